@@ -1,0 +1,128 @@
+"""Synthetic THC-RR-CCSD systems shaped like the paper's workloads.
+
+The paper's molecules, basis sets and integrals are not available, so every
+input is drawn from a seeded generator:
+
+* occupied orbital energies  eps_o ~ U[-1.5, -0.3] Eh, sorted ascending;
+* virtual orbital energies   eps_v ~ U[ 0.1,  3.0] Eh, sorted ascending;
+* ERI grid collocation       x ~ N(0,1)/sqrt(G), shape (n, G);
+* grid metric factor          A = |N(0,1)| * sqrt(gamma / (K * 2/pi)), shape (G, K);
+* amplitude collocation      Y ~ N(0,1)/sqrt(P), shape (n, P);
+  drawn in that order from ``numpy.random.default_rng(seed)``.
+
+The generator's text leaves the scale and sign of A open.  A non-negative A
+makes the grid kernel z elementwise positive, like the Coulomb kernel 1/r12
+it stands for, and the scale puts Coulomb-type integrals (pp|qq) near
+``gamma`` (default 0.3 Eh) while ovov integrals stay of order gamma / G, so
+the amplitude equations are well conditioned at every size.
+
+Derived inputs (input construction, not the method):
+
+* ERI-THC core  z = A A^T + 1e-3 I   (G x G, the THC form of Eq. 17);
+* R = first K columns of a diagonally pivoted Cholesky factor of z (G x K);
+* Cholesky vectors  L[K, p, q] = sum_I x[p, I] x[q, I] R[I, K]   (Eq. 24).
+
+With ``consistent=True`` the Cholesky rank is the full grid size (K = G) and
+the Cholesky and THC ovov integrals agree exactly; the invariant tests use it.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class System:
+    """One synthetic closed-shell system (all arrays float64, C order)."""
+    o: int
+    v: int
+    P: int
+    G: int
+    K: int
+    seed: int
+    eps_o: np.ndarray   # (o,)
+    eps_v: np.ndarray   # (v,)
+    Y: np.ndarray       # (n, P) occupied rows first
+    x: np.ndarray       # (n, G)
+    z: np.ndarray       # (G, G) symmetric
+    L: np.ndarray       # (K, n, n) symmetric in the last two indices
+
+    @property
+    def n(self) -> int:
+        return self.o + self.v
+
+
+def _pivoted_cholesky(V: np.ndarray, rank: int) -> np.ndarray:
+    """Diagonally pivoted (outer-product) Cholesky: V ~= R R^T, R is G x rank.
+
+    Columns come in pivot order (largest remaining diagonal first).
+    """
+    G = V.shape[0]
+    R = np.zeros((G, rank))
+    d = np.diag(V).astype(np.float64).copy()
+    for k in range(rank):
+        p = int(np.argmax(d))
+        piv = d[p]
+        if piv <= 0.0:
+            break
+        col = V[:, p] - R[:, :k] @ R[p, :k]
+        col /= np.sqrt(piv)
+        R[:, k] = col
+        d -= col * col
+        d[p] = 0.0
+    return R
+
+
+def make_system(o: int, v: int, P: int, G: int, K: int, seed: int,
+                consistent: bool = False, gamma: float = 0.3) -> System:
+    """Draw one synthetic system.  ``consistent`` forces K = G."""
+    if consistent:
+        K = G
+    rng = np.random.default_rng(seed)
+    eps_o = np.sort(rng.uniform(-1.5, -0.3, o))
+    eps_v = np.sort(rng.uniform(0.1, 3.0, v))
+    n = o + v
+    x = rng.standard_normal((n, G)) / np.sqrt(G)
+    A = np.abs(rng.standard_normal((G, K))) * np.sqrt(gamma / (K * 2.0 / np.pi))
+    Y = rng.standard_normal((n, P)) / np.sqrt(P)
+    z = A @ A.T + 1e-3 * np.eye(G)
+    z = 0.5 * (z + z.T)
+    R = _pivoted_cholesky(z, K)
+    # L[K, p, q] = sum_I x[p, I] x[q, I] R[I, K], built one Cholesky vector
+    # at a time to bound the temporary.
+    L = np.empty((K, n, n))
+    for k in range(K):
+        L[k] = (x * R[:, k]) @ x.T
+    L = 0.5 * (L + L.transpose(0, 2, 1))
+    return System(o, v, P, G, K, seed, eps_o, eps_v,
+                  np.ascontiguousarray(Y), np.ascontiguousarray(x),
+                  np.ascontiguousarray(z), np.ascontiguousarray(L))
+
+
+def random_amplitudes(P: int, o: int, v: int, seed: int,
+                      t2_scale: float = 1e-2, t1_scale: float = 1e-2):
+    """A symmetric THC core Zc (P x P) and singles t1 (o x v).
+
+    Zc has entries of size ``t2_scale * P`` so that the doubles amplitudes it
+    encodes are of size ``t2_scale`` when Y ~ N(0,1)/sqrt(P).
+    """
+    rng = np.random.default_rng(seed)
+    Zc = rng.standard_normal((P, P)) * (t2_scale * P)
+    Zc = 0.5 * (Zc + Zc.T)
+    t1 = rng.standard_normal((o, v)) * t1_scale
+    return np.ascontiguousarray(Zc), np.ascontiguousarray(t1)
+
+
+# The workloads: (o, v, P, G, K, seed).
+CONFIGS = {
+    "c1": (5, 20, 60, 120, 60, 0),
+    "c2": (40, 200, 400, 1200, 600, 1),
+    "c3": (100, 600, 1000, 3500, 1500, 2),
+    "c5": (60, 300, 600, 1800, 900, 200),
+}
+
+
+def config_system(name: str) -> System:
+    o, v, P, G, K, seed = CONFIGS[name]
+    return make_system(o, v, P, G, K, seed)
