@@ -1,0 +1,172 @@
+/*
+ * thc.h - C ABI of the GB300 THC-RR-CCSD residual library (libthc.so).
+ *
+ * The library evaluates the residual of rank-reduced coupled-cluster singles
+ * and doubles with tensor-hypercontracted doubles amplitudes (Hohenstein,
+ * Fales, Parrish, Martinez, "Rank-reduced coupled-cluster III", Sec. II-III):
+ *
+ *   t_ij^ab = sum_WX y_i^W y_a^W Zc^WX y_j^X y_b^X                    (Eq. 23)
+ *   (pq^|rs) = sum_A L^_pq^A L^_rs^A, L^ = T1-dressed Cholesky vectors (Eqs. 24-27)
+ *   (ia|jb)  = sum_IJ x_i^I x_a^I z^IJ x_j^J x_b^J                    (Eq. 17)
+ *
+ * and returns the doubles residual projected onto the amplitude factors,
+ *   sigma^WX = sum_ijab y_i^W y_a^W y_j^X y_b^X Omega_ij^ab       (Eq. 6, Eq. 14)
+ * (the sum of Eqs. 28, 29, 31, 34, 35 and 41), the singles residual
+ * Omega_i^a (Eqs. 38 and 42), and the closed-shell CCSD energy.
+ *
+ * Conventions shared by every entry point
+ *   - All arrays are row-major IEEE float64 (C order), whatever the internal
+ *     precision policy.
+ *   - Orbitals: o occupied then v virtual, n = o + v.  Y is n x P with the
+ *     occupied rows first; x is n x G likewise; L is K x n x n.
+ *   - Pointers may be host or device memory (the kind is detected per
+ *     pointer); outputs are written into the caller's buffer in its own
+ *     memory kind.  Every call is synchronous on the context's stream: when it
+ *     returns, outputs are complete and inputs may be reused.
+ *   - Every call returns a thc_status; nothing throws across the ABI.  On
+ *     failure thc_last_error() describes the first error on that context.
+ *   - A context belongs to one GPU and one stream and is not thread-safe;
+ *     separate contexts are independent.
+ */
+#ifndef THC_H
+#define THC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct thc_ctx thc_ctx;
+
+typedef enum {
+    THC_OK = 0,
+    THC_ERR_ARG = 1,            /* bad dimension, null pointer, asymmetric input */
+    THC_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    THC_ERR_OOM = 3,            /* device workspace could not be allocated */
+    THC_ERR_NUMERIC = 4,        /* non-finite input/output, metric not positive */
+    THC_ERR_NOT_CONVERGED = 5,  /* thc_solve hit max_iter */
+    THC_ERR_TIMEOUT = 6,        /* a bounded device wait expired */
+    THC_ERR_UNSUPPORTED = 7     /* feature not available on this device */
+} thc_status;
+
+/* Arithmetic policy for the bulk contractions.  FP64: every step in float64.
+ * MIXED: operands stored in float32, tensor-core GEMMs with split (hi/lo)
+ * bf16 products and float32 accumulation, float32 CUDA-core triangle kernel;
+ * the sigma accumulation, energy, least squares and DIIS stay float64. */
+typedef enum { THC_PREC_FP64 = 0, THC_PREC_MIXED = 1 } thc_precision;
+
+typedef struct {
+    int n_occ;               /* o > 0 */
+    int n_vir;               /* v > 0 */
+    int n_p;                 /* P: amplitude THC rank (columns of Y) */
+    int n_g;                 /* G: ERI-THC grid size (columns of x) */
+    int n_k;                 /* K: number of Cholesky vectors */
+    int precision;           /* thc_precision */
+    int k_slab;              /* Cholesky vectors per fused slab, 0 = auto */
+    int i_chunk;             /* grid points per Alg. 6 chunk, 0 = auto */
+    int x_block;             /* amplitude-THC columns per Alg. 7 block, 0 = auto */
+    size_t workspace_bytes;  /* device workspace limit, 0 = auto */
+    double lsq_rel_cutoff;   /* drop metric eigenvalues below cutoff*max (1e-10) */
+} thc_config;
+
+/* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */
+thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p,
+                              int n_g, int n_k);
+
+/*
+ * thc_init - copy the system to the device and precompute the fixed parts.
+ *
+ *   eps_occ  o      occupied orbital energies (canonical Hartree-Fock: the
+ *                   Fock matrix is diag(eps); the core Hamiltonian is
+ *                   recovered from it and the Cholesky integrals)
+ *   eps_vir  v      virtual orbital energies
+ *   Y        n x P  amplitude collocation factors y_p^W (Eq. 7, Eq. 23)
+ *   L        K x n x n  Cholesky vectors L_pq^A, symmetric in pq (Eq. 24)
+ *   x        n x G  ERI-THC collocation x_p^I (Eq. 17)
+ *   z        G x G  ERI-THC core z^IJ, symmetric (Eq. 17)
+ *   stream   cudaStream_t to run on, or NULL for the legacy default stream
+ *
+ * Precomputes o^XY, v^XY (Alg. 1 lines 1-2), the metric S = o*v (Eq. 10)
+ * and the orthonormal working basis of Eq. 22 (generalised eigenbasis of
+ * the orbital-energy Fock block in the metric).  Inputs are copied; the
+ * caller keeps ownership.  Errors: THC_ERR_ARG for non-positive sizes or
+ * asymmetric z, THC_ERR_OOM, THC_ERR_CUDA, THC_ERR_NUMERIC if the metric has
+ * no positive eigenvalue.  On failure *out is NULL.
+ */
+thc_status thc_init(const thc_config* cfg, const double* eps_occ,
+                    const double* eps_vir, const double* Y, const double* L,
+                    const double* x, const double* z, void* stream,
+                    thc_ctx** out);
+
+/*
+ * thc_residual - one evaluation of the projected residual (Algs. 1-10).
+ *
+ *   Zc      P x P  symmetric THC core T^WX (Eq. 22-23), input
+ *   t1      o x v  singles t_i^a, input
+ *   sigmaZ  P x P  sigma^WX, output (y basis, as produced by Algs. 1-9)
+ *   sigma1  o x v  Omega_i^a, output (Algs. 8 and 10)
+ *   energy  scalar closed-shell CCSD energy at (Zc, t1); may be NULL
+ *
+ * Errors: THC_ERR_ARG for NULL required pointers, THC_ERR_NUMERIC if an
+ * output is not finite.
+ */
+thc_status thc_residual(thc_ctx* ctx, const double* Zc, const double* t1,
+                        double* sigmaZ, double* sigma1, double* energy);
+
+/*
+ * thc_energy - closed-shell CCSD energy
+ *   E = sum_iajb [2(ia|jb) - (ib|ja)] (t_ij^ab + t_i^a t_j^b)
+ * with Cholesky integrals (Sec. II.a: the energy is the usual CCSD one),
+ * evaluated in O(K P^2) from the THC core.
+ */
+thc_status thc_energy(thc_ctx* ctx, const double* Zc, const double* t1,
+                      double* energy);
+
+typedef struct {
+    double r_tol;        /* stop when |residual| < r_tol (1e-8) */
+    double e_tol;        /* and |dE| < e_tol (0 = not used) */
+    int max_iter;        /* iteration cap (100) */
+    int diis_n;          /* DIIS subspace size (8), 0 = plain Jacobi */
+    int use_mlp;         /* 1 = learned preconditioner proposals */
+    int verbose;         /* 1 = one line per iteration on stderr */
+} thc_solve_opts;
+
+typedef struct {
+    int iters;
+    int mlp_accepted;
+    int mlp_rejected;
+    double energy;
+    double r_norm;
+    double wall_s;
+} thc_report;
+
+/* Fill *opts with the defaults listed above. */
+thc_status thc_solve_opts_default(thc_solve_opts* opts);
+
+/*
+ * thc_solve - solve the projected amplitude equations from (Zc, t1).
+ *
+ * Works in the orthonormal basis of Eq. 22 (T^PQ, Zc = C T C^T): Jacobi
+ * step -sigma_q/(e_P+e_Q) on the doubles and -Omega_i^a/(eps_a-eps_i) on
+ * the singles, Pulay DIIS, float64 throughout the update.  The residual norm
+ * is sqrt(|Omega1|^2 + |C^T sigma C|^2).  Zc_inout and t1_inout hold the
+ * start point on entry and the solution on return.  Returns
+ * THC_ERR_NOT_CONVERGED (with the last iterate written back) at max_iter.
+ */
+thc_status thc_solve(thc_ctx* ctx, const thc_solve_opts* opts,
+                     double* Zc_inout, double* t1_inout, thc_report* report);
+
+/* Text of the first error recorded on ctx ("" if none).  The pointer stays
+ * valid until the next call on ctx or thc_destroy.  ctx may be NULL, which
+ * returns the last error of a failed thc_init on this thread. */
+const char* thc_last_error(const thc_ctx* ctx);
+
+/* Release every device buffer of ctx.  NULL is accepted. */
+void thc_destroy(thc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THC_H */

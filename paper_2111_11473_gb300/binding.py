@@ -1,0 +1,226 @@
+"""ctypes binding of the C ABI in include/thc.h (marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libthc.so")
+
+THC_PREC_FP64 = 0
+THC_PREC_MIXED = 1
+
+STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_CUDA", 3: "THC_ERR_OOM",
+          4: "THC_ERR_NUMERIC", 5: "THC_ERR_NOT_CONVERGED", 6: "THC_ERR_TIMEOUT",
+          7: "THC_ERR_UNSUPPORTED"}
+
+
+class ThcConfig(C.Structure):
+    _fields_ = [("n_occ", C.c_int), ("n_vir", C.c_int), ("n_p", C.c_int),
+                ("n_g", C.c_int), ("n_k", C.c_int), ("precision", C.c_int),
+                ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
+                ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double)]
+
+
+class ThcSolveOpts(C.Structure):
+    _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
+                ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int)]
+
+
+class ThcReport(C.Structure):
+    _fields_ = [("iters", C.c_int), ("mlp_accepted", C.c_int), ("mlp_rejected", C.c_int),
+                ("energy", C.c_double), ("r_norm", C.c_double), ("wall_s", C.c_double)]
+
+
+@dataclass
+class Report:
+    status: str
+    iters: int
+    energy: float
+    r_norm: float
+    wall_s: float
+    mlp_accepted: int
+    mlp_rejected: int
+
+
+class ThcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+_LIB = None
+_VP = C.c_void_p
+_DP = C.c_void_p   # double* (host or device); passed as raw addresses
+
+_SIGNATURES = {
+    "thc_config_default": (C.c_int, [C.POINTER(ThcConfig), C.c_int, C.c_int, C.c_int,
+                                     C.c_int, C.c_int]),
+    "thc_solve_opts_default": (C.c_int, [C.POINTER(ThcSolveOpts)]),
+    "thc_init": (C.c_int, [C.POINTER(ThcConfig), _DP, _DP, _DP, _DP, _DP, _DP, _VP,
+                           C.POINTER(_VP)]),
+    "thc_residual": (C.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
+    "thc_energy": (C.c_int, [_VP, _DP, _DP, _DP]),
+    "thc_solve": (C.c_int, [_VP, C.POINTER(ThcSolveOpts), _DP, _DP, C.POINTER(ThcReport)]),
+    "thc_last_error": (C.c_char_p, [_VP]),
+    "thc_destroy": (None, [_VP]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libthc.so and declare the C ABI.  Raises if it is not built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def _is_torch(a):
+    return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+
+
+class _Arg:
+    """A float64 C-contiguous buffer and its address (numpy or torch)."""
+
+    def __init__(self, a, shape, writable=False):
+        if _is_torch(a):
+            import torch
+            if a.dtype != torch.float64:
+                raise TypeError("expected a float64 tensor")
+            if tuple(a.shape) != tuple(shape):
+                raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+            if not a.is_contiguous():
+                if writable:
+                    raise ValueError("output tensor must be contiguous")
+                a = a.contiguous()
+            self.obj = a
+            self.ptr = a.data_ptr()
+        else:
+            arr = np.asarray(a)
+            if arr.shape != tuple(shape):
+                raise ValueError(f"expected shape {shape}, got {arr.shape}")
+            if writable:
+                if arr.dtype != np.float64 or not arr.flags.c_contiguous:
+                    raise ValueError("output array must be C-contiguous float64")
+            else:
+                arr = np.ascontiguousarray(arr, dtype=np.float64)
+            self.obj = arr
+            self.ptr = arr.ctypes.data
+
+
+class Context:
+    """One THC-RR-CCSD system resident on the GPU (wraps thc_ctx*)."""
+
+    def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
+                 k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10):
+        lib = load_library()
+        o, v = len(eps_o), len(eps_v)
+        n = o + v
+        P = Y.shape[1]
+        G = x.shape[1]
+        K = L.shape[0]
+        cfg = ThcConfig()
+        st = lib.thc_config_default(C.byref(cfg), o, v, P, G, K)
+        if st != 0:
+            raise ThcError(st, "bad dimensions")
+        cfg.precision = int(precision)
+        cfg.k_slab, cfg.i_chunk, cfg.x_block = k_slab, i_chunk, x_block
+        cfg.workspace_bytes = workspace_bytes
+        cfg.lsq_rel_cutoff = lsq_rel_cutoff
+        args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)), _Arg(L, (K, n, n)),
+                _Arg(x, (n, G)), _Arg(z, (G, G))]
+        handle = _VP()
+        stream_ptr = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        st = lib.thc_init(C.byref(cfg), *[a.ptr for a in args], _VP(stream_ptr),
+                          C.byref(handle))
+        if st != 0:
+            raise ThcError(st, lib.thc_last_error(None).decode())
+        self._lib = lib
+        self._h = handle
+        self.o, self.v, self.P, self.G, self.K = o, v, P, G, K
+        self.precision = precision
+
+    def _check(self, st):
+        if st != 0:
+            raise ThcError(st, self._lib.thc_last_error(self._h).decode())
+
+    def _out(self, like, shape):
+        if _is_torch(like):
+            import torch
+            return torch.empty(shape, dtype=torch.float64, device=like.device)
+        return np.empty(shape)
+
+    def residual(self, Zc, t1, out=None, want_energy=True):
+        """(sigma^WX, Omega_i^a, E) at (Zc, t1); outputs in the inputs' memory."""
+        zc = _Arg(Zc, (self.P, self.P))
+        tt = _Arg(t1, (self.o, self.v))
+        if out is None:
+            out = (self._out(Zc, (self.P, self.P)), self._out(Zc, (self.o, self.v)))
+        s = _Arg(out[0], (self.P, self.P), writable=True)
+        s1 = _Arg(out[1], (self.o, self.v), writable=True)
+        e = C.c_double(0.0)
+        eptr = C.addressof(e) if want_energy else None
+        self._check(self._lib.thc_residual(self._h, zc.ptr, tt.ptr, s.ptr, s1.ptr, eptr))
+        return out[0], out[1], (e.value if want_energy else None)
+
+    def energy(self, Zc, t1):
+        zc = _Arg(Zc, (self.P, self.P))
+        tt = _Arg(t1, (self.o, self.v))
+        e = C.c_double(0.0)
+        self._check(self._lib.thc_energy(self._h, zc.ptr, tt.ptr, C.addressof(e)))
+        return e.value
+
+    def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
+              use_mlp=False, verbose=False, raise_on_failure=True):
+        """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero."""
+        if Zc is None:
+            Zc = np.zeros((self.P, self.P))
+        if t1 is None:
+            t1 = np.zeros((self.o, self.v))
+        zc = _Arg(Zc, (self.P, self.P), writable=True)
+        tt = _Arg(t1, (self.o, self.v), writable=True)
+        opts = ThcSolveOpts()
+        self._lib.thc_solve_opts_default(C.byref(opts))
+        opts.r_tol, opts.e_tol, opts.max_iter = r_tol, e_tol, max_iter
+        opts.diis_n, opts.use_mlp, opts.verbose = diis_n, int(use_mlp), int(verbose)
+        rep = ThcReport()
+        st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
+        report = Report(STATUS.get(st, str(st)), rep.iters, rep.energy, rep.r_norm, rep.wall_s,
+                        rep.mlp_accepted, rep.mlp_rejected)
+        if st != 0 and raise_on_failure:
+            self._check(st)
+        return Zc, t1, report
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.thc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,153 @@
+// C ABI of the THC-RR-CCSD library (declared in include/thc.h).
+#include <chrono>
+#include <cmath>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "engine.cuh"
+#include "solver.cuh"
+
+struct thc_ctx {
+    thc_config cfg{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    std::unique_ptr<thc::Engine<double>> e64;
+    std::unique_ptr<thc::Engine<float>> e32;
+    std::unique_ptr<thc::Solver> solver;
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+thc_status fail(thc_ctx* c, const thc::Err& e) {
+    if (c && c->err.empty()) c->err = e.msg;
+    return e.code;
+}
+
+thc::Err check_config(const thc_config* cfg) {
+    if (!cfg) return {THC_ERR_ARG, "cfg is NULL"};
+    if (cfg->n_occ <= 0 || cfg->n_vir <= 0 || cfg->n_p <= 0 || cfg->n_g <= 0 || cfg->n_k <= 0)
+        return {THC_ERR_ARG, "every dimension must be positive"};
+    if (cfg->precision != THC_PREC_FP64 && cfg->precision != THC_PREC_MIXED)
+        return {THC_ERR_ARG, "unknown precision policy"};
+    if (cfg->k_slab < 0 || cfg->i_chunk < 0 || cfg->x_block < 0)
+        return {THC_ERR_ARG, "blocking sizes must be >= 0"};
+    return {};
+}
+
+}  // namespace
+
+extern "C" {
+
+thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p, int n_g,
+                              int n_k) {
+    if (!cfg) return THC_ERR_ARG;
+    *cfg = thc_config{};
+    cfg->n_occ = n_occ;
+    cfg->n_vir = n_vir;
+    cfg->n_p = n_p;
+    cfg->n_g = n_g;
+    cfg->n_k = n_k;
+    cfg->precision = THC_PREC_FP64;
+    cfg->lsq_rel_cutoff = 1e-10;
+    return check_config(cfg).code;
+}
+
+thc_status thc_solve_opts_default(thc_solve_opts* opts) {
+    if (!opts) return THC_ERR_ARG;
+    opts->r_tol = 1e-8;
+    opts->e_tol = 0.0;
+    opts->max_iter = 100;
+    opts->diis_n = 8;
+    opts->use_mlp = 0;
+    opts->verbose = 0;
+    return THC_OK;
+}
+
+thc_status thc_init(const thc_config* cfg, const double* eps_occ, const double* eps_vir,
+                    const double* Y, const double* L, const double* x, const double* z,
+                    void* stream, thc_ctx** out) {
+    g_init_error.clear();
+    if (!out) { g_init_error = "out is NULL"; return THC_ERR_ARG; }
+    *out = nullptr;
+    thc::Err e = check_config(cfg);
+    if (e.ok() && (!eps_occ || !eps_vir || !Y || !L || !x || !z))
+        e = {THC_ERR_ARG, "an input pointer is NULL"};
+    if (!e.ok()) { g_init_error = e.msg; return e.code; }
+    thc_ctx* c = new (std::nothrow) thc_ctx;
+    if (!c) { g_init_error = "host allocation failed"; return THC_ERR_OOM; }
+    c->cfg = *cfg;
+    if (c->cfg.lsq_rel_cutoff <= 0) c->cfg.lsq_rel_cutoff = 1e-10;
+    c->st = (cudaStream_t)stream;
+    {
+        if (cfg->precision == THC_PREC_FP64) {
+            c->e64.reset(new thc::Engine<double>());
+            e = c->e64->init(c->cfg, eps_occ, eps_vir, Y, L, x, z, c->st);
+        } else {
+            c->e32.reset(new thc::Engine<float>());
+            e = c->e32->init(c->cfg, eps_occ, eps_vir, Y, L, x, z, c->st);
+        }
+    }
+    if (!e.ok()) {
+        g_init_error = e.msg;
+        delete c;
+        return e.code;
+    }
+    *out = c;
+    return THC_OK;
+}
+
+thc_status thc_residual(thc_ctx* c, const double* Zc, const double* t1, double* sigmaZ,
+                        double* sigma1, double* energy) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (!Zc || !t1 || !sigmaZ || !sigma1) return fail(c, {THC_ERR_ARG, "NULL argument"});
+    thc::Err e = c->e64 ? c->e64->residual(Zc, t1, sigmaZ, sigma1, energy)
+               : c->e32->residual(Zc, t1, sigmaZ, sigma1, energy);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+thc_status thc_energy(thc_ctx* c, const double* Zc, const double* t1, double* energy) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (!Zc || !t1 || !energy) return fail(c, {THC_ERR_ARG, "NULL argument"});
+    thc::Err e = c->e64 ? c->e64->energy(Zc, t1, energy) : c->e32->energy(Zc, t1, energy);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
+                     double* t1_inout, thc_report* report) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (!opts || !Zc_inout || !t1_inout) return fail(c, {THC_ERR_ARG, "NULL argument"});
+    if (!c->solver) {
+        c->solver.reset(new thc::Solver());
+        thc::Err e = c->e64 ? c->solver->setup(*c->e64, c->cfg.lsq_rel_cutoff)
+                            : c->solver->setup(*c->e32, c->cfg.lsq_rel_cutoff);
+        if (!e.ok()) { c->solver.reset(); return fail(c, e); }
+    }
+    thc_report rep{};
+    thc::Err e = c->e64 ? c->solver->run(*c->e64, *opts, Zc_inout, t1_inout, &rep)
+                        : c->solver->run(*c->e32, *opts, Zc_inout, t1_inout, &rep);
+    if (report) *report = rep;
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+const char* thc_last_error(const thc_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+void thc_destroy(thc_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Shared definitions of the THC-RR-CCSD CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/thc.h"
+
+namespace thc {
+
+// Status carrier used inside the library; converted to thc_status at the ABI.
+struct Err {
+    thc_status code = THC_OK;
+    std::string msg;
+    bool ok() const { return code == THC_OK; }
+};
+
+#define THC_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            return ::thc::Err{e_ == cudaErrorMemoryAllocation ? THC_ERR_OOM    \
+                                                              : THC_ERR_CUDA,  \
+                              std::string(#call) + ": " +                      \
+                                  cudaGetErrorString(e_)};                     \
+        }                                                                      \
+    } while (0)
+
+#define THC_TRY(expr)                                                          \
+    do {                                                                       \
+        ::thc::Err e_ = (expr);                                                \
+        if (!e_.ok()) return e_;                                               \
+    } while (0)
+
+// A strided view of a matrix: element (r, c) lives at p[r*rs + c*cs].
+template <typename T>
+struct View {
+    const T* p;
+    long long rs, cs;
+    View t() const { return View{p, cs, rs}; }
+};
+
+template <typename T>
+View<T> rowmajor(const T* p, long long ld) { return View<T>{p, ld, 1}; }
+
+// One (batched) matrix product  C_b = alpha * A_b B_b + beta * C_b, with
+// A_b = A + b*sAb etc.  With reduce = true every batch is summed into a
+// single C (a long inner dimension running over the batch).
+template <typename T>
+struct Gemm {
+    int M = 0, N = 0, K = 0, batch = 1;
+    View<T> A{}, B{};
+    long long sAb = 0, sBb = 0;
+    T* C = nullptr;
+    long long ldc = 0, sCb = 0;
+    double alpha = 1.0, beta = 0.0;
+    bool reduce = false;
+    // Optional split-K workspace (partials are summed deterministically).
+    T* ws = nullptr;
+    size_t ws_elems = 0;
+    int splits = 1;        // set by the launcher
+};
+
+cudaError_t gemm_simt(const Gemm<double>& g, cudaStream_t s);
+cudaError_t gemm_simt(const Gemm<float>& g, cudaStream_t s);
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace thc

@@ -1,0 +1,632 @@
+// Residual engine: factorised evaluation of the projected THC-RR-CCSD
+// residual (Algorithms 1-10 of the paper) on one GPU.
+//
+// Notation: y_o = Y[0:o], y_v = Y[o:n] (amplitude collocation, Eq. 23),
+// x_o, x_v likewise for the ERI grid (Eq. 17), T = Zc the THC core,
+// o^XY = y_o^T y_o, v^XY = y_v^T y_v (Alg. 1 lines 1-2), S = o * v (Eq. 10).
+// Dressed Cholesky blocks per vector A (Eqs. 25-27, C = 1 in the MO basis):
+//   L^_oo = L_oo + L_ov t1^T,  L^_vv = L_vv - t1^T L_ov,
+//   L^_vo = L_vo + L_vv t1^T - t1^T L^_oo,  L^_ov = L_ov.
+#include <cstring>
+#include <type_traits>
+
+#include "engine.cuh"
+
+namespace thc {
+
+namespace {
+
+template <typename T>
+__global__ void k_wen_acc(const T* E, int P, int nb, double* acc) {
+    const long long PP = (long long)P * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < PP;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int Y = (int)(idx / P), Z = (int)(idx % P);
+        double s = 0;
+        for (int a = 0; a < nb; ++a)
+            s += (double)E[a * PP + (long long)Z * P + Y] * (double)E[a * PP + idx];
+        acc[idx] -= s;
+    }
+}
+
+template <typename T>
+__global__ void k_outer_acc(const T* Acols, int P, int K, double* acc, double scale) {
+    const long long PP = (long long)P * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < PP;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(idx / P), Y = (int)(idx % P);
+        double s = 0;
+        for (int a = 0; a < K; ++a)
+            s += (double)Acols[(long long)X * K + a] * (double)Acols[(long long)Y * K + a];
+        acc[idx] += scale * s;
+    }
+}
+
+__global__ void k_asym(const double* a, int n, unsigned long long* out) {
+    // out[0] = bits of max |a - a^T|, out[1] = bits of max |a|, out[2] = # non-finite
+    const long long nn = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        const double x = a[idx];
+        if (!isfinite(x)) { atomicAdd(&out[2], 1ULL); continue; }
+        const double d = fabs(x - a[(long long)j * n + i]);
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(isfinite(d) ? d : 0.0));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(fabs(x)));
+    }
+}
+
+}  // namespace
+
+template <typename T>
+Err Engine<T>::check_sym(const double* a, int nn_, double rel, const char* what) {
+    unsigned long long h[3];
+    THC_CUDA(cudaMemsetAsync(chk.p, 0, 3 * sizeof(unsigned long long), st));
+    const long long tot = (long long)nn_ * nn_;
+    k_asym<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, st>>>(a, nn_, chk.p);
+    THC_CUDA(cudaGetLastError());
+    THC_CUDA(cudaMemcpyAsync(h, chk.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (h[2]) return Err{THC_ERR_NUMERIC, std::string(what) + " has non-finite entries"};
+    double asym, amax;
+    memcpy(&asym, &h[0], 8);
+    memcpy(&amax, &h[1], 8);
+    if (asym > rel * amax) return Err{THC_ERR_ARG, std::string(what) + " is not symmetric"};
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::check_finite(const double* a, long long count, const char* what) {
+    int bad = 0;
+    THC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    THC_CUDA(any_nonfinite(a, count, flag.p, st));
+    THC_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (bad) return Err{THC_ERR_NUMERIC, std::string(what) + " has non-finite entries"};
+    return Err{};
+}
+
+template <typename T>
+static View<T> rm(const T* p, long long ld) { return View<T>{p, ld, 1}; }
+template <typename T>
+static View<T> tr(const T* p, long long ld) { return View<T>{p, 1, ld}; }
+
+template <typename T>
+Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ldc,
+                  double alpha, double beta, int batch, long long sAb, long long sBb,
+                  long long sCb, bool reduce) {
+    Gemm<T> g;
+    g.M = M; g.N = N; g.K = Kd; g.batch = batch;
+    g.A = A; g.B = B; g.sAb = sAb; g.sBb = sBb;
+    g.C = C; g.ldc = ldc; g.sCb = sCb;
+    g.alpha = alpha; g.beta = beta; g.reduce = reduce;
+    g.ws = splitk.p; g.ws_elems = splitk.n;
+    THC_CUDA(gemm_simt(g, st));
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::dress(const T* oo_, const T* ov_, const T* vv_, int nb, T* out_oo,
+                     T* out_vv, T* out_vo) {
+    const T* tp = t1.p;
+    // L^_oo = L_oo + L_ov t1^T
+    THC_CUDA(cudaMemcpyAsync(out_oo, oo_, sizeof(T) * nb * o * o, cudaMemcpyDeviceToDevice, st));
+    THC_TRY(mm(o, o, v, rm(ov_, v), tr(tp, v), out_oo, o, 1, 1, nb, (long long)o * v, 0,
+               (long long)o * o));
+    // L^_vv = L_vv - t1^T L_ov
+    THC_CUDA(cudaMemcpyAsync(out_vv, vv_, sizeof(T) * nb * v * v, cudaMemcpyDeviceToDevice, st));
+    THC_TRY(mm(v, v, o, tr(tp, v), rm(ov_, v), out_vv, v, -1, 1, nb, 0, (long long)o * v,
+               (long long)v * v));
+    // L^_vo = L_ov^T + L_vv t1^T - t1^T L^_oo
+    THC_CUDA(transpose_batched(ov_, out_vo, nb, o, v, st));
+    THC_TRY(mm(v, o, v, rm(vv_, v), tr(tp, v), out_vo, o, 1, 1, nb, (long long)v * v, 0,
+               (long long)v * o));
+    THC_TRY(mm(v, o, o, tr(tp, v), rm(out_oo, o), out_vo, o, -1, 1, nb, 0, (long long)o * o,
+               (long long)v * o));
+    return Err{};
+}
+
+// Coulomb (J) and exchange (X) parts of the Fock matrix from nb vectors:
+// J_pq += sum_A tr(L^_oo^A) L^_pq^A,  X_pq += sum_A sum_k L^_pk^A L^_kq^A.
+template <typename T>
+Err Engine<T>::fock_slab(int nb, bool, T* Jo, T* Jov_, T* Jvo_, T* Jv, T* Xo, T* Xov_,
+                         T* Xvo_, T* Xv, const T* Loo_, const T* Lov_, const T* Lvo_,
+                         const T* Lvv_) {
+    THC_CUDA(traces(Loo_, o, nb, dtr.p, st));
+    View<T> d{dtr.p, 0, 1};
+    const long long oo2 = (long long)o * o, ov = (long long)o * v, vv2 = (long long)v * v;
+    THC_TRY(mm(1, (int)oo2, nb, d, rm(Loo_, oo2), Jo, oo2, 1, 1));
+    THC_TRY(mm(1, (int)ov, nb, d, rm(Lov_, ov), Jov_, ov, 1, 1));
+    THC_TRY(mm(1, (int)ov, nb, d, rm(Lvo_, ov), Jvo_, ov, 1, 1));
+    THC_TRY(mm(1, (int)vv2, nb, d, rm(Lvv_, vv2), Jv, vv2, 1, 1));
+    THC_TRY(mm(o, o, o, rm(Loo_, o), rm(Loo_, o), Xo, o, 1, 1, nb, oo2, oo2, 0, true));
+    THC_TRY(mm(o, v, o, rm(Loo_, o), rm(Lov_, v), Xov_, v, 1, 1, nb, oo2, ov, 0, true));
+    THC_TRY(mm(v, o, o, rm(Lvo_, o), rm(Loo_, o), Xvo_, o, 1, 1, nb, ov, oo2, 0, true));
+    THC_TRY(mm(v, v, o, rm(Lvo_, o), rm(Lov_, v), Xv, v, 1, 1, nb, ov, ov, 0, true));
+    return Err{};
+}
+
+// D_ia = sum_kc (2 t_ik^ac - t_ik^ca) M_kc for nb matrices M (o x v):
+// D = y_o (2 diag(T a) - T o E) y_v^T,  a^X = sum_ia y_i^X y_a^X M_ia,
+// E^YZ = sum_kc y_c^Y y_k^Z M_kc   (Alg. 8 lines 6-9, Alg. 10 lines 1-8).
+template <typename T>
+Err Engine<T>::d_operator(const T* Mv, int nb, T* Dout) {
+    const long long ov = (long long)o * v, oP = (long long)o * P, PP = (long long)P * P;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    THC_TRY(mm(o, P, v, rm(Mv, v), rm(yv, P), M3.p, P, 1, 0, nb, ov, 0, oP));
+    THC_CUDA(diag_reduce(yo, M3.p, o, P, nb, Ta0.p, nb, 0, st));
+    THC_TRY(mm(P, nb, P, rm(Tc.p, P), rm(Ta0.p, nb), TA.p, nb, 1, 0));
+    THC_TRY(mm(P, P, o, tr(M3.p, P), rm(yo, P), E.p, P, 1, 0, nb, oP, 0, PP));
+    THC_CUDA(w_single(TA.p, nb, Tc.p, E.p, W.p, P, nb, st));
+    THC_TRY(mm(o, P, P, rm(yo, P), rm(W.p, P), M4.p, P, 1, 0, nb, 0, PP, oP));
+    THC_TRY(mm(o, v, P, rm(M4.p, P), tr(yv, P), Dout, v, 1, 0, nb, oP, 0, ov));
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* eps_v,
+                    const double* Yh, const double* Lh, const double* xh, const double* zh,
+                    cudaStream_t s) {
+    st = s;
+    o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
+    kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, K) : std::min(K, 64);
+    ic = cfg.i_chunk > 0 ? std::min(cfg.i_chunk, G) : std::min(G, 64);
+    xb = cfg.x_block > 0 ? std::min(cfg.x_block, P) : std::min(P, 32);
+    const long long ov = (long long)o * v, PP = (long long)P * P, nn = (long long)n * n;
+
+    THC_TRY(flag.alloc(1));
+    THC_TRY(chk.alloc(3));
+    {
+        DBuf<double> zd, ed;
+        THC_TRY(zd.alloc((size_t)G * G));
+        THC_CUDA(cudaMemcpyAsync(zd.p, zh, sizeof(double) * G * G, cudaMemcpyDefault, st));
+        THC_TRY(check_sym(zd.p, G, 1e-12, "z"));
+        THC_TRY(ed.alloc((size_t)n));
+        THC_CUDA(cudaMemcpyAsync(ed.p, eps_o, sizeof(double) * o, cudaMemcpyDefault, st));
+        THC_CUDA(cudaMemcpyAsync(ed.p + o, eps_v, sizeof(double) * v, cudaMemcpyDefault, st));
+        THC_TRY(check_finite(ed.p, n, "orbital energies"));
+    }
+    // ---- fixed inputs
+    THC_TRY(y.alloc((size_t)n * P));
+    THC_TRY(x.alloc((size_t)n * G));
+    THC_TRY(z.alloc((size_t)G * G));
+    THC_TRY(load(Yh, y.p, (long long)n * P));
+    THC_TRY(load(xh, x.p, (long long)n * G));
+    THC_TRY(load(zh, z.p, (long long)G * G));
+    THC_TRY(Loo.alloc((size_t)K * o * o));
+    THC_TRY(Lov.alloc((size_t)K * ov));
+    THC_TRY(Lvv.alloc((size_t)K * v * v));
+    {
+        // Stage L in slabs of kb vectors and split it into its blocks.
+        DBuf<double> stage;
+        DBuf<T> stageT;
+        THC_TRY(stage.alloc((size_t)kb * nn));
+        if (!std::is_same<T, double>::value) THC_TRY(stageT.alloc((size_t)kb * nn));
+        for (int A0 = 0; A0 < K; A0 += kb) {
+            int nb = std::min(kb, K - A0);
+            THC_CUDA(cudaMemcpyAsync(stage.p, Lh + (long long)A0 * nn,
+                                     sizeof(double) * nb * nn, cudaMemcpyDefault, st));
+            const T* src;
+            if constexpr (std::is_same<T, double>::value) {
+                src = stage.p;
+            } else {
+                THC_CUDA(convert(stage.p, stageT.p, nb * nn, st));
+                src = stageT.p;
+            }
+            Blocks<T> b{Loo.p + (long long)A0 * o * o, Lov.p + (long long)A0 * ov, nullptr,
+                        Lvv.p + (long long)A0 * v * v};
+            THC_CUDA(split_blocks(src, nb, o, v, b, st));
+        }
+        THC_CUDA(cudaStreamSynchronize(st));
+    }
+
+    // ---- scratch
+    const long long kbl = kb;
+    THC_TRY(splitk.alloc((size_t)std::max<long long>(4 * PP, 1 << 22)));
+    THC_TRY(Tc.alloc(PP));
+    THC_TRY(Tcd.alloc(PP));
+    THC_TRY(t1.alloc(ov));
+    THC_TRY(t1d.alloc(ov));
+    THC_TRY(sig.alloc(PP));
+    THC_TRY(sig1.alloc(ov));
+    THC_TRY(en.alloc(4));
+    if (!std::is_same<T, double>::value) {
+        THC_TRY(sigT.alloc(PP));
+        THC_TRY(sig1T.alloc(ov));
+    }
+    THC_TRY(xoo.alloc((size_t)o * o));
+    THC_TRY(xvv.alloc((size_t)v * v));
+    THC_TRY(Ccross.alloc(PP));
+    THC_TRY(Abar.alloc((size_t)P * K));
+    THC_TRY(Q.alloc((size_t)P * K));
+    THC_TRY(Wq.alloc((size_t)P * K));
+    for (DBuf<T>* b : {&Joo, &Xoo, &Foo, &hh_oo}) THC_TRY(b->alloc((size_t)o * o));
+    for (DBuf<T>* b : {&Jov, &Xov, &Fov, &Jvo, &Xvo, &Fvo, &hh_vo}) THC_TRY(b->alloc(ov));
+    for (DBuf<T>* b : {&Jvv, &Xvv, &Fvv, &hh_vv}) THC_TRY(b->alloc((size_t)v * v));
+    for (DBuf<T>* b : {&ST, &E9, &V9, &O9}) THC_TRY(b->alloc(PP));
+    THC_TRY(M9.alloc((size_t)n * P));
+    THC_TRY(FvoT.alloc(ov));
+    THC_TRY(red.alloc(std::max(1024, K + 16)));
+    THC_TRY(Lh_oo.alloc(kbl * o * o));
+    THC_TRY(Lh_vv.alloc(kbl * v * v));
+    THC_TRY(Lh_vo.alloc(kbl * ov));
+    THC_TRY(dtr.alloc(kbl));
+    THC_TRY(M1.alloc(kbl * o * P));
+    THC_TRY(N1.alloc(kbl * v * P));
+    THC_TRY(M2.alloc(kbl * v * P));
+    THC_TRY(M3.alloc(kbl * o * P));
+    THC_TRY(M4.alloc(kbl * o * P));
+    THC_TRY(M5.alloc(kbl * o * P));
+    for (DBuf<T>* b : {&Bbar, &Btil, &C1, &D1, &E, &W}) THC_TRY(b->alloc(kbl * PP));
+    THC_TRY(TA.alloc(kbl * P));
+    THC_TRY(Ta0.alloc(kbl * P));
+    THC_TRY(D8.alloc(kbl * ov));
+    THC_TRY(Mo.alloc((size_t)K * o * o));
+
+    // ---- core Hamiltonian  h = diag(eps) - (2 J - X)  from undressed blocks
+    THC_TRY(h.alloc(nn));
+    THC_TRY(hoo.alloc((size_t)o * o));
+    THC_TRY(hov.alloc(ov));
+    THC_TRY(hvo.alloc(ov));
+    THC_TRY(hvv.alloc((size_t)v * v));
+    for (DBuf<T>* b : {&Joo, &Jov, &Jvo, &Jvv, &Xoo, &Xov, &Xvo, &Xvv})
+        THC_CUDA(cudaMemsetAsync(b->p, 0, b->n * sizeof(T), st));
+    for (int A0 = 0; A0 < K; A0 += kb) {
+        int nb = std::min(kb, K - A0);
+        THC_CUDA(transpose_batched(Lov.p + A0 * ov, Lh_vo.p, nb, o, v, st));
+        THC_TRY(fock_slab(nb, false, Joo.p, Jov.p, Jvo.p, Jvv.p, Xoo.p, Xov.p, Xvo.p, Xvv.p,
+                          Loo.p + (long long)A0 * o * o, Lov.p + A0 * ov, Lh_vo.p,
+                          Lvv.p + (long long)A0 * v * v));
+    }
+    {
+        std::vector<double> eps(n);
+        THC_CUDA(cudaMemcpy(eps.data(), eps_o, sizeof(double) * o, cudaMemcpyDefault));
+        THC_CUDA(cudaMemcpy(eps.data() + o, eps_v, sizeof(double) * v, cudaMemcpyDefault));
+        eps_h = eps;
+        std::vector<T> foo((size_t)o * o, T(0)), fvv((size_t)v * v, T(0));
+        for (int i = 0; i < o; ++i) foo[(size_t)i * o + i] = (T)eps[i];
+        for (int a = 0; a < v; ++a) fvv[(size_t)a * v + a] = (T)eps[o + a];
+        THC_CUDA(cudaMemcpyAsync(hoo.p, foo.data(), sizeof(T) * o * o, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(hvv.p, fvv.data(), sizeof(T) * v * v, cudaMemcpyHostToDevice, st));
+        THC_CUDA(lincomb(hoo.p, (long long)o * o, 1, hoo.p, -2, Joo.p, 1, Xoo.p, st));
+        THC_CUDA(lincomb(hvv.p, (long long)v * v, 1, hvv.p, -2, Jvv.p, 1, Xvv.p, st));
+        THC_CUDA(lincomb(hov.p, ov, -2, Jov.p, 1, Xov.p, 0, (const T*)nullptr, st));
+        THC_CUDA(lincomb(hvo.p, ov, -2, Jvo.p, 1, Xvo.p, 0, (const T*)nullptr, st));
+        THC_CUDA(cudaStreamSynchronize(st));
+    }
+
+    // ---- amplitude-factor products
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    const T* xo = x.p;
+    const T* xv = x.p + (long long)o * G;
+    THC_TRY(oo.alloc(PP));
+    THC_TRY(vv.alloc(PP));
+    THC_TRY(S.alloc(PP));
+    THC_TRY(mm(P, P, o, tr(yo, P), rm(yo, P), oo.p, P, 1, 0));
+    THC_TRY(mm(P, P, v, tr(yv, P), rm(yv, P), vv.p, P, 1, 0));
+    THC_CUDA(hadamard2(S.p, PP, oo.p, vv.p, (const T*)nullptr, (const T*)nullptr, st));
+    THC_TRY(KRy.alloc(ov * P));
+    THC_TRY(KRx.alloc(ov * G));
+    THC_CUDA(khatri_rao(yo, yv, o, v, P, KRy.p, st));
+    THC_CUDA(khatri_rao(xo, xv, o, v, G, KRx.p, st));
+
+    // ---- energy weight  Wen = 2 sum_A a_A a_A^T - sum_A E_A^T o E_A   (float64)
+    THC_TRY(Atil.alloc((size_t)P * K));
+    THC_TRY(Wen.alloc(PP));
+    THC_CUDA(cudaMemsetAsync(Wen.p, 0, PP * sizeof(double), st));
+    for (int A0 = 0; A0 < K; A0 += kb) {
+        int nb = std::min(kb, K - A0);
+        THC_TRY(mm(o, P, v, rm(Lov.p + A0 * ov, v), rm(yv, P), M3.p, P, 1, 0, nb, ov, 0,
+                   (long long)o * P));
+        THC_CUDA(diag_reduce(yo, M3.p, o, P, nb, Atil.p, K, A0, st));
+        THC_TRY(mm(P, P, o, tr(M3.p, P), rm(yo, P), E.p, P, 1, 0, nb, (long long)o * P, 0, PP));
+        k_wen_acc<T><<<cdiv(PP, 256), 256, 0, st>>>(E.p, P, nb, Wen.p);
+        THC_CUDA(cudaGetLastError());
+    }
+    k_outer_acc<T><<<cdiv(PP, 256), 256, 0, st>>>(Atil.p, P, K, Wen.p, 2.0);
+    THC_CUDA(cudaGetLastError());
+
+    // ---- Alg. 6 fixed parts: B_ia^I = sum_J x_i^J x_a^J z^IJ (line 2),
+    //      U[i][I][Z] = sum_a B_ia^I y_a^Z, G_I^YZ = sum_i y_i^Y U[i][I][Z] (line 10)
+    THC_TRY(B6.alloc(ov * G));
+    THC_TRY(mm((int)ov, G, G, rm(KRx.p, G), rm(z.p, G), B6.p, G, 1, 0));
+    THC_TRY(U6.alloc((size_t)o * G * P));
+    THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p, P, 1, 0, o, (long long)v * G, 0,
+               (long long)G * P));
+    const size_t gall_bytes = (size_t)G * PP * sizeof(T);
+    gall_resident = cfg.workspace_bytes == 0 ? gall_bytes <= (size_t)48 << 30
+                                             : gall_bytes <= cfg.workspace_bytes / 4;
+    if (gall_resident) {
+        THC_TRY(Gall.alloc((size_t)G * PP));
+        THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0, G,
+                   0, P, PP));
+    } else {
+        THC_TRY(Gch.alloc((size_t)ic * PP));
+    }
+    THC_TRY(A6.alloc(ov * P));
+    THC_TRY(C6.alloc((size_t)o * PP));
+    THC_TRY(D6.alloc((size_t)v * PP));
+    THC_TRY(Ech.alloc((size_t)ic * PP));
+    THC_TRY(Fch.alloc((size_t)ic * PP));
+    THC_TRY(H.alloc((size_t)P * PP));
+    THC_TRY(M6.alloc((size_t)P * o * P));
+    THC_TRY(I6.alloc((size_t)P * ov));
+    // ---- Alg. 7 scratch
+    THC_TRY(R7.alloc((size_t)P * ov));
+    THC_TRY(S7.alloc((size_t)P * ov));
+    THC_TRY(C7.alloc((size_t)P * G));
+    THC_TRY(D7.alloc((size_t)P * G));
+    THC_TRY(Yv.alloc((size_t)xb * o * P));
+    THC_TRY(M7.alloc((size_t)xb * o * P));
+    THC_TRY(Yo.alloc((size_t)xb * v * P));
+    THC_TRY(N7.alloc((size_t)xb * o * G));
+    THC_TRY(E7.alloc((size_t)xb * G * G));
+    THC_TRY(P7.alloc((size_t)xb * o * G));
+    THC_TRY(G7.alloc((size_t)xb * ov));
+    THC_CUDA(cudaStreamSynchronize(st));
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::load(const double* src, T* dst, long long count) {
+    if constexpr (std::is_same<T, double>::value) {
+        THC_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDefault, st));
+    } else {
+        DBuf<double> tmp;
+        THC_TRY(tmp.alloc(count));
+        THC_CUDA(cudaMemcpyAsync(tmp.p, src, sizeof(double) * count, cudaMemcpyDefault, st));
+        THC_CUDA(convert(tmp.p, dst, count, st));
+        THC_CUDA(cudaStreamSynchronize(st));
+    }
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::set_state(const double* Zc, const double* t1in) {
+    const long long PP = (long long)P * P, ov = (long long)o * v;
+    THC_CUDA(cudaMemcpyAsync(Tcd.p, Zc, sizeof(double) * PP, cudaMemcpyDefault, st));
+    THC_CUDA(cudaMemcpyAsync(t1d.p, t1in, sizeof(double) * ov, cudaMemcpyDefault, st));
+    THC_TRY(check_sym(Tcd.p, P, 1e-12, "Zc"));
+    THC_TRY(check_finite(t1d.p, ov, "t1"));
+    if constexpr (std::is_same<T, double>::value) {
+        THC_CUDA(cudaMemcpyAsync(Tc.p, Tcd.p, sizeof(double) * PP, cudaMemcpyDeviceToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(t1.p, t1d.p, sizeof(double) * ov, cudaMemcpyDeviceToDevice, st));
+    } else {
+        THC_CUDA(convert(Tcd.p, Tc.p, PP, st));
+        THC_CUDA(convert(t1d.p, t1.p, ov, st));
+    }
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::alg6(T* sgm) {
+    const long long ov = (long long)o * v, PP = (long long)P * P;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    // A_ia^X = sum_Y y_i^Y y_a^Y T^XY  (line 1), C_i^XY (line 4), D_a^XY (line 5)
+    THC_TRY(mm((int)ov, P, P, rm(KRy.p, P), rm(Tc.p, P), A6.p, P, 1, 0));
+    THC_TRY(mm(P, P, v, tr(yv, P), rm(A6.p, P), C6.p, P, 1, 0, o, 0, (long long)v * P, PP));
+    THC_TRY(mm(P, P, o, tr(yo, P), View<T>{A6.p, (long long)v * P, 1}, D6.p, P, 1, 0, v, 0, P,
+               PP));
+    THC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(T) * P * PP, st));
+    for (int I0 = 0; I0 < G; I0 += ic) {
+        const int nI = std::min(ic, G - I0);
+        // E^XY = sum_i C_i^XY x_i^I (line 8), F^XZ = sum_a D_a^XZ x_a^I (line 9)
+        THC_TRY(mm(nI, (int)PP, o, View<T>{x.p + I0, 1, G}, rm(C6.p, PP), Ech.p, PP, 1, 0));
+        THC_TRY(mm(nI, (int)PP, v, View<T>{x.p + (long long)o * G + I0, 1, G}, rm(D6.p, PP),
+                   Fch.p, PP, 1, 0));
+        const T* Gp;
+        if (gall_resident) {
+            Gp = Gall.p + (long long)I0 * PP;
+        } else {
+            THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p + (long long)I0 * P, (long long)G * P, 1},
+                       Gch.p, P, 1, 0, nI, 0, P, PP));
+            Gp = Gch.p;
+        }
+        // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
+        THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st));
+    }
+    // I_ia = sum_YZ y_i^Z y_a^Y H^XYZ (line 14); sigma^XX' += sum_ia y_i^X' y_a^X' I_ia
+    THC_TRY(mm(o, P, P, rm(yo, P), View<T>{H.p, 1, P}, M6.p, P, 1, 0, P, 0, PP,
+               (long long)o * P));
+    THC_TRY(mm(o, v, P, rm(M6.p, P), tr(yv, P), I6.p, v, 1, 0, P, (long long)o * P, 0, ov));
+    THC_TRY(mm(P, P, (int)ov, rm(I6.p, ov), rm(KRy.p, P), sgm, P, 1, 1));
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::alg7(T* sgm) {
+    const long long ov = (long long)o * v, PP = (long long)P * P, GG = (long long)G * G;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    const T* xo = x.p;
+    const T* xv = x.p + (long long)o * G;
+    // R_ia^X = 2 sum_Y y_i^Y y_a^Y (S T)^XY + S_ia^X   (lines 3-8)
+    THC_TRY(mm(P, (int)ov, P, rm(ST.p, P), tr(KRy.p, P), R7.p, ov, 2, 0));
+    for (int X0 = 0; X0 < P; X0 += xb) {
+        const int nx = std::min(xb, P - X0);
+        THC_CUDA(scale_rows(yo, o, P, vv.p, X0, nx, Yv.p, st));
+        THC_TRY(mm(o, P, P, rm(Yv.p, P), rm(Tc.p, P), M7.p, P, 1, 0, nx, (long long)o * P, 0,
+                   (long long)o * P));
+        THC_CUDA(scale_rows(yv, v, P, oo.p, X0, nx, Yo.p, st));
+        THC_TRY(mm(o, v, P, rm(M7.p, P), View<T>{Yo.p, 1, P}, S7.p + (long long)X0 * ov, v, -1,
+                   0, nx, (long long)o * P, (long long)v * P, ov));
+    }
+    THC_CUDA(lincomb(R7.p, (long long)P * ov, 1, R7.p, 1, S7.p, 0, (const T*)nullptr, st));
+    // Coulomb part: C^XI = sum_ia x_i^I x_a^I R_ia^X, D = C z (lines 9-10)
+    THC_TRY(mm(P, G, (int)ov, rm(R7.p, ov), rm(KRx.p, G), C7.p, G, 1, 0));
+    THC_TRY(mm(P, G, G, rm(C7.p, G), rm(z.p, G), D7.p, G, 1, 0));
+    THC_TRY(mm(P, P, G, rm(C7.p, G), tr(D7.p, G), sgm, P, 1, 1));
+    // Exchange parts (lines 12-21), blocked over X
+    for (int pass = 0; pass < 2; ++pass) {
+        const T* src = pass == 0 ? R7.p : S7.p;
+        const double sign = pass == 0 ? -0.5 : 0.5;
+        for (int X0 = 0; X0 < P; X0 += xb) {
+            const int nx = std::min(xb, P - X0);
+            THC_TRY(mm(o, G, v, rm(src + (long long)X0 * ov, v), rm(xv, G), N7.p, G, 1, 0, nx,
+                       ov, 0, (long long)o * G));
+            THC_TRY(mm(G, G, o, tr(xo, G), rm(N7.p, G), E7.p, G, 1, 0, nx, 0, (long long)o * G,
+                       GG));
+            THC_CUDA(hadamard_batched(E7.p, z.p, GG, nx, st));
+            THC_TRY(mm(o, G, G, rm(xo, G), tr(E7.p, G), P7.p, G, 1, 0, nx, 0, GG,
+                       (long long)o * G));
+            THC_TRY(mm(o, v, G, rm(P7.p, G), tr(xv, G), G7.p, v, 1, 0, nx, (long long)o * G, 0,
+                       ov));
+            THC_TRY(mm(nx, P, (int)ov, rm(G7.p, ov), tr(src, ov), sgm + (long long)X0 * P, P,
+                       sign, 1));
+        }
+    }
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::residual_dev(bool want_energy) {
+    const long long ov = (long long)o * v, PP = (long long)P * P;
+    const long long oo2 = (long long)o * o, vv2 = (long long)v * v;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    T* sgm;
+    T* sg1;
+    if constexpr (std::is_same<T, double>::value) {
+        sgm = sig.p;
+        sg1 = sig1.p;
+    } else {
+        sgm = sigT.p;
+        sg1 = sig1T.p;
+    }
+    THC_CUDA(cudaMemsetAsync(sgm, 0, sizeof(T) * PP, st));
+    THC_CUDA(cudaMemsetAsync(sg1, 0, sizeof(T) * ov, st));
+    for (DBuf<T>* b : {&xoo, &xvv, &Ccross, &Joo, &Jov, &Jvo, &Jvv, &Xoo, &Xov, &Xvo, &Xvv})
+        THC_CUDA(cudaMemsetAsync(b->p, 0, b->n * sizeof(T), st));
+
+    // Dressed core Hamiltonian (one "vector" of the dressing routine).
+    THC_TRY(dress(hoo.p, hov.p, hvv.p, 1, hh_oo.p, hh_vv.p, hh_vo.p));
+
+    // ---- fused Cholesky-slab pass: Algs. 1, 2, 3, 8 and the Fock matrix
+    for (int A0 = 0; A0 < K; A0 += kb) {
+        const int nb = std::min(kb, K - A0);
+        const T* Lov_s = Lov.p + A0 * ov;
+        THC_TRY(dress(Loo.p + A0 * oo2, Lov_s, Lvv.p + A0 * vv2, nb, Lh_oo.p, Lh_vv.p, Lh_vo.p));
+        THC_TRY(fock_slab(nb, true, Joo.p, Jov.p, Jvo.p, Jvv.p, Xoo.p, Xov.p, Xvo.p, Xvv.p,
+                          Lh_oo.p, Lov_s, Lh_vo.p, Lh_vv.p));
+        // Alg. 1: Bbar^XY = sum_ik y_i^X l_ki y_k^Y, Btil^XY = sum_ac y_a^X l_ac y_c^Y,
+        // C = v o Bbar - o o Btil, sigma += C T C^T.  Alg. 3: Ccross += Bbar o Btil.
+        THC_TRY(mm(o, P, o, rm(Lh_oo.p, o), rm(yo, P), M1.p, P, 1, 0, nb, oo2, 0, (long long)o * P));
+        THC_TRY(mm(P, P, o, tr(M1.p, P), rm(yo, P), Bbar.p, P, 1, 0, nb, (long long)o * P, 0, PP));
+        THC_TRY(mm(v, P, v, rm(Lh_vv.p, v), rm(yv, P), N1.p, P, 1, 0, nb, vv2, 0, (long long)v * P));
+        THC_TRY(mm(P, P, v, tr(yv, P), rm(N1.p, P), Btil.p, P, 1, 0, nb, 0, (long long)v * P, PP));
+        THC_CUDA(alg1_combine(Bbar.p, Btil.p, oo.p, vv.p, C1.p, Ccross.p, P, nb, st));
+        THC_TRY(mm(P * nb, P, P, rm(C1.p, P), rm(Tc.p, P), D1.p, P, 1, 0));
+        THC_TRY(mm(P, P, nb * P, rm(D1.p, (long long)nb * P), tr(C1.p, (long long)nb * P), sgm,
+                   P, 1, 1));
+        // Alg. 2 line 5: Abar^X = sum_ai y_a^X y_i^X l_ai
+        THC_TRY(mm(v, P, o, rm(Lh_vo.p, o), rm(yo, P), M2.p, P, 1, 0, nb, ov, 0, (long long)v * P));
+        THC_CUDA(diag_reduce(yv, M2.p, v, P, nb, Abar.p, K, A0, st));
+        // Alg. 8 lines 6-9: D_ia = sum_kc u_ik^ac l_kc; Alg. 2: Q^X = (2 Dtil - H)^X
+        THC_TRY(d_operator(Lov_s, nb, D8.p));
+        THC_TRY(mm(o, P, v, rm(D8.p, v), rm(yv, P), M5.p, P, 1, 0, nb, ov, 0, (long long)o * P));
+        THC_CUDA(diag_reduce(yo, M5.p, o, P, nb, Q.p, K, A0, st));
+        // Alg. 8 lines 10-13
+        THC_TRY(mm(o, o, v, rm(Lov_s, v), tr(D8.p, v), xoo.p, o, 1, 1, nb, ov, ov, 0, true));
+        THC_TRY(mm(v, v, o, tr(D8.p, v), rm(Lov_s, v), xvv.p, v, -1, 1, nb, ov, ov, 0, true));
+        THC_TRY(mm(o, v, v, rm(D8.p, v), tr(Lh_vv.p, v), sg1, v, 1, 1, nb, ov, vv2, 0, true));
+        THC_TRY(mm(o, v, o, tr(Lh_oo.p, o), rm(D8.p, v), sg1, v, -1, 1, nb, oo2, ov, 0, true));
+    }
+
+    // Alg. 2 line 14: sigma += Abar Abar^T + Q Abar^T + Abar Q^T
+    THC_CUDA(lincomb(Wq.p, (long long)P * K, 1, Abar.p, 1, Q.p, 0, (const T*)nullptr, st));
+    THC_TRY(mm(P, P, K, rm(Wq.p, K), tr(Abar.p, K), sgm, P, 1, 1));
+    THC_TRY(mm(P, P, K, rm(Abar.p, K), tr(Q.p, K), sgm, P, 1, 1));
+    // Alg. 3 lines 11-12: sigma -= (S T) Ccross^T + Ccross (S T)^T
+    THC_TRY(mm(P, P, P, rm(S.p, P), rm(Tc.p, P), ST.p, P, 1, 0));
+    THC_TRY(mm(P, P, P, rm(ST.p, P), tr(Ccross.p, P), sgm, P, -1, 1));
+    THC_TRY(mm(P, P, P, rm(Ccross.p, P), tr(ST.p, P), sgm, P, -1, 1));
+
+    // Dressed Fock matrix  F^ = h^ + 2 J - X
+    THC_CUDA(lincomb(Foo.p, oo2, 1, hh_oo.p, 2, Joo.p, -1, Xoo.p, st));
+    THC_CUDA(lincomb(Fov.p, ov, 1, hov.p, 2, Jov.p, -1, Xov.p, st));
+    THC_CUDA(lincomb(Fvo.p, ov, 1, hh_vo.p, 2, Jvo.p, -1, Xvo.p, st));
+    THC_CUDA(lincomb(Fvv.p, vv2, 1, hh_vv.p, 2, Jvv.p, -1, Xvv.p, st));
+
+    // Alg. 9: E = o o (y_v^T Fb_vv y_v) - v o (y_o^T Fb_oo^T y_o), sigma += E B^T + B E^T
+    THC_CUDA(lincomb(xoo.p, oo2, 1, Foo.p, 1, xoo.p, 0, (const T*)nullptr, st));
+    THC_CUDA(lincomb(xvv.p, vv2, 1, Fvv.p, 1, xvv.p, 0, (const T*)nullptr, st));
+    THC_TRY(mm(v, P, v, rm(xvv.p, v), rm(yv, P), M9.p, P, 1, 0));
+    THC_TRY(mm(P, P, v, tr(yv, P), rm(M9.p, P), V9.p, P, 1, 0));
+    THC_TRY(mm(o, P, o, tr(xoo.p, o), rm(yo, P), M9.p, P, 1, 0));
+    THC_TRY(mm(P, P, o, tr(yo, P), rm(M9.p, P), O9.p, P, 1, 0));
+    THC_CUDA(hadamard2(E9.p, PP, oo.p, V9.p, vv.p, O9.p, st));
+    THC_TRY(mm(P, P, P, rm(E9.p, P), tr(ST.p, P), sgm, P, 1, 1));
+    THC_TRY(mm(P, P, P, rm(ST.p, P), tr(E9.p, P), sgm, P, 1, 1));
+
+    // Alg. 10: sigma_ia += F^_ai + sum_kc u_ik^ac F^_kc
+    THC_TRY(d_operator(Fov.p, 1, D8.p));
+    THC_CUDA(transpose_batched(Fvo.p, FvoT.p, 1, v, o, st));
+    THC_CUDA(lincomb(sg1, ov, 1, sg1, 1, D8.p, 1, FvoT.p, st));
+
+    // Algs. 6 and 7 (T2^2 terms through the THC ovov integrals)
+    THC_TRY(alg6(sgm));
+    THC_TRY(alg7(sgm));
+
+    if constexpr (!std::is_same<T, double>::value) {
+        THC_CUDA(cudaMemsetAsync(sig.p, 0, sizeof(double) * PP, st));
+        THC_CUDA(cudaMemsetAsync(sig1.p, 0, sizeof(double) * ov, st));
+        THC_CUDA(accumulate(sig.p, sgm, PP, 1.0, st));
+        THC_CUDA(accumulate(sig1.p, sg1, ov, 1.0, st));
+    }
+    if (want_energy) THC_TRY(energy_dev());
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::energy_dev() {
+    const long long PP = (long long)P * P, ov = (long long)o * v, oo2 = (long long)o * o;
+    // doubles: <Zc, Wen>;  singles: sum_A [2 (L_A . t1)^2 - tr((L_A t1^T)^2)]
+    THC_CUDA(dot(Tcd.p, Wen.p, PP, red.p, en.p, st));
+    THC_TRY(mm(o, o, v, rm(Lov.p, v), tr(t1.p, v), Mo.p, o, 1, 0, K, ov, 0, oo2));
+    THC_CUDA(singles_energy(Lov.p, Mo.p, t1.p, K, o, v, red.p, en.p + 1, st));
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::residual(const double* Zc, const double* t1in, double* sigmaZ,
+                        double* sigma1, double* energy_out) {
+    THC_TRY(set_state(Zc, t1in));
+    THC_TRY(residual_dev(energy_out != nullptr));
+    const long long PP = (long long)P * P, ov = (long long)o * v;
+    THC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    THC_CUDA(any_nonfinite(sig.p, PP, flag.p, st));
+    THC_CUDA(any_nonfinite(sig1.p, ov, flag.p, st));
+    THC_CUDA(cudaMemcpyAsync(sigmaZ, sig.p, sizeof(double) * PP, cudaMemcpyDefault, st));
+    THC_CUDA(cudaMemcpyAsync(sigma1, sig1.p, sizeof(double) * ov, cudaMemcpyDefault, st));
+    int bad = 0;
+    double e[2] = {0, 0};
+    THC_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (energy_out) THC_CUDA(cudaMemcpyAsync(e, en.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (energy_out) {
+        const double etot = e[0] + e[1];
+        THC_CUDA(cudaMemcpy(energy_out, &etot, sizeof(double), cudaMemcpyDefault));
+    }
+    if (bad) return Err{THC_ERR_NUMERIC, "residual has non-finite entries"};
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::energy(const double* Zc, const double* t1in, double* e_out) {
+    THC_TRY(set_state(Zc, t1in));
+    THC_TRY(energy_dev());
+    double e[2];
+    THC_CUDA(cudaMemcpyAsync(e, en.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    const double etot = e[0] + e[1];
+    THC_CUDA(cudaMemcpy(e_out, &etot, sizeof(double), cudaMemcpyDefault));
+    return Err{};
+}
+
+template struct Engine<double>;
+template struct Engine<float>;
+
+}  // namespace thc

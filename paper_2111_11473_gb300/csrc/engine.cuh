@@ -1,0 +1,111 @@
+// Residual engine of the THC-RR-CCSD library: device buffers and the
+// factorised evaluation of Algorithms 1-10.
+#pragma once
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace thc {
+
+// Owned device allocation.
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    Err alloc(size_t count) {
+        n = count;
+        if (count == 0) return Err{};
+        THC_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        return Err{};
+    }
+    ~DBuf() { if (p) cudaFree(p); }
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+};
+
+// Matrix-product policy: which kernel family runs the contractions.
+enum class MMKind { SIMT, TC_BF16X3 };
+
+template <typename T>
+struct Engine {
+    int o = 0, v = 0, n = 0, P = 0, G = 0, K = 0;
+    int kb = 0, ic = 0, xb = 0;
+    bool gall_resident = false;
+    MMKind mm_kind = MMKind::SIMT;
+    cudaStream_t st = nullptr;
+    size_t bytes = 0;
+
+    // Fixed data (storage type T unless noted).
+    DBuf<T> y, x, z;                        // n x P, n x G, G x G
+    DBuf<T> Loo, Lov, Lvv;                  // K x o x o, K x o x v, K x v x v (undressed)
+    DBuf<T> h;                              // n x n core Hamiltonian (blocks below)
+    DBuf<T> hoo, hov, hvo, hvv;
+    DBuf<T> oo, vv, S;                      // P x P
+    DBuf<T> KRy, KRx;                       // (o v) x P, (o v) x G
+    DBuf<T> Atil;                           // P x K   (Alg. 2 line 6 / Alg. 8 line 6)
+    DBuf<double> Wen;                       // P x P   energy weight of the core
+    DBuf<T> Gall;                           // G x P x P (Alg. 6 line 10), if resident
+    DBuf<T> B6;                             // (o v) x G (Alg. 6 line 2)
+    DBuf<T> U6;                             // o x G x P  sum_a B_ia^I y_a^Z
+
+    // Per-residual state and accumulators.
+    DBuf<T> Tc, t1;                         // P x P, o x v
+    DBuf<double> Tcd, t1d;                  // float64 copies of the state
+    DBuf<double> sig, sig1, en;             // P x P, o x v, energy scalars
+    DBuf<T> sigT, sig1T;                    // partial sums in T (float engine)
+    DBuf<T> splitk;                         // split-K partials of the GEMMs
+    std::vector<double> eps_h;              // orbital energies (host copy)
+    DBuf<T> xoo, xvv, Ccross, Abar, Q;      // o x o, v x v, P x P, P x K, P x K
+    DBuf<T> Joo, Jov, Jvo, Jvv, Xoo, Xov, Xvo, Xvv;  // Coulomb / exchange Fock parts
+    DBuf<T> Foo, Fov, Fvo, Fvv;             // dressed Fock blocks
+    DBuf<T> hh_oo, hh_vo, hh_vv;            // dressed core Hamiltonian blocks
+    DBuf<T> ST, E9, V9, O9, M9, Wq;         // P x P and n x P work
+    DBuf<T> FvoT, Ta0;
+    DBuf<double> red;                       // reduction scratch
+    DBuf<int> flag;
+    DBuf<unsigned long long> chk;           // symmetry / finiteness check results
+
+    // Slab scratch.
+    DBuf<T> Lh_oo, Lh_vv, Lh_vo, dtr;
+    DBuf<T> M1, Bbar, N1, Btil, C1, D1, M2, M3, E, TA, W, M4, D8, M5, Mo;
+
+    // Alg. 6 scratch.
+    DBuf<T> A6, C6, D6, Ech, Fch, Gch, H, M6, I6;
+    // Alg. 7 scratch.
+    DBuf<T> R7, S7, C7, D7, Yv, M7, Yo, N7, E7, P7, G7;
+
+    Err init(const thc_config& cfg, const double* eps_o, const double* eps_v,
+             const double* Y, const double* L, const double* xin, const double* zin,
+             cudaStream_t s);
+    Err residual(const double* Zc, const double* t1in, double* sigmaZ, double* sigma1,
+                 double* energy);
+    Err energy(const double* Zc, const double* t1in, double* e);
+
+    // Device-resident variant used by the solver: Tc and t1 already loaded.
+    Err residual_dev(bool want_energy);
+    Err energy_dev();
+
+    Err load(const double* src, T* dst, long long count);
+    // THC_ERR_ARG if |a - a^T| > rel max|a|, THC_ERR_NUMERIC if a is not finite
+    // (a: n x n float64 in device memory).
+    Err check_sym(const double* a, int n, double rel, const char* what);
+    Err check_finite(const double* a, long long count, const char* what);
+    Err set_state(const double* Zc, const double* t1in);
+    Err mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ldc,
+           double alpha, double beta, int batch = 1, long long sAb = 0,
+           long long sBb = 0, long long sCb = 0, bool reduce = false);
+    Err dress(const T* oo_, const T* ov_, const T* vv_, int nb, T* out_oo, T* out_vv,
+              T* out_vo);
+    Err fock_slab(int nb, bool dressed, T* Jo, T* Jov_, T* Jvo_, T* Jv, T* Xo, T* Xov_,
+                  T* Xvo_, T* Xv, const T* Loo_, const T* Lov_, const T* Lvo_,
+                  const T* Lvv_);
+    Err d_operator(const T* M, int nb, T* Dout);
+    Err alg6(T* sgm);
+    Err alg7(T* sgm);
+};
+
+}  // namespace thc

@@ -1,0 +1,479 @@
+// Element-wise, reduction and triangle kernels of the residual engine.
+#include "kernels.cuh"
+
+namespace thc {
+namespace {
+
+constexpr int NT = 256;
+
+inline unsigned nblocks(long long n) {
+    long long b = (n + NT - 1) / NT;
+    if (b > 152LL * 64) b = 152LL * 64;   // grid-stride beyond 64 blocks per SM
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__global__ void k_split(const T* full, int nb, int o, int v, Blocks<T> out) {
+    const int n = o + v;
+    const long long total = (long long)nb * n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long a = idx / ((long long)n * n);
+        int r = (int)(idx / n % n), c = (int)(idx % n);
+        T val = full[idx];
+        if (r < o && c < o) out.oo[(a * o + r) * o + c] = val;
+        else if (r < o) { if (out.ov) out.ov[(a * o + r) * v + (c - o)] = val; }
+        else if (c < o) { if (out.vo) out.vo[(a * v + (r - o)) * o + c] = val; }
+        else out.vv[(a * v + (r - o)) * v + (c - o)] = val;
+    }
+}
+
+template <typename T>
+__global__ void k_transpose(const T* in, T* out, int nb, int rows, int cols) {
+    __shared__ T tile[32][33];
+    const int a = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const T* src = in + (long long)a * rows * cols;
+    T* dst = out + (long long)a * rows * cols;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        int r = r0 + j, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[j][threadIdx.x] = src[(long long)r * cols + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        int c = c0 + j, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(long long)c * rows + r] = tile[threadIdx.x][j];
+    }
+}
+
+template <typename T>
+__global__ void k_convert(const double* in, T* out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+template <typename T>
+__global__ void k_to_double(const T* in, double* out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+template <typename T>
+__global__ void k_alg1(const T* Bbar, const T* Btil, const T* oo, const T* vv,
+                       T* C1, T* Ccross, int P, int nb) {
+    const long long PP = (long long)P * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < PP;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(idx / P), Y = (int)(idx % P);
+        const T wo = oo[idx], wv = vv[idx];
+        T cross = Ccross[idx];
+        for (int a = 0; a < nb; ++a) {
+            const T bb = Bbar[a * PP + idx], bt = Btil[a * PP + idx];
+            C1[((long long)X * nb + a) * P + Y] = wv * bb - wo * bt;
+            cross += bb * bt;
+        }
+        Ccross[idx] = cross;
+    }
+}
+
+template <typename T>
+__global__ void k_diag_reduce(const T* y, const T* M, int R, int P, int nb, T* out,
+                              int ldo, int col0) {
+    const long long total = (long long)nb * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / P), X = (int)(idx % P);
+        const T* m = M + (long long)a * R * P + X;
+        T acc = 0;
+        for (int r = 0; r < R; ++r) acc += y[(long long)r * P + X] * m[(long long)r * P];
+        out[(long long)X * ldo + col0 + a] = acc;
+    }
+}
+
+template <typename T>
+__global__ void k_w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P,
+                           int nb) {
+    const long long PP = (long long)P * P, total = PP * nb;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / PP);
+        const long long e = idx % PP;
+        const int Y = (int)(e / P), Z = (int)(e % P);
+        T w = -Tc[e] * E[idx];
+        if (Y == Z) w += T(2) * TA[(long long)Y * ldta + a];
+        W[idx] = w;
+    }
+}
+
+template <typename T>
+__global__ void k_traces(const T* M, int n, int nb, T* d) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nb) return;
+    const T* m = M + (long long)a * n * n;
+    T acc = 0;
+    for (int k = 0; k < n; ++k) acc += m[(long long)k * n + k];
+    d[a] = acc;
+}
+
+template <typename T>
+__global__ void k_lincomb(T* out, long long n, double a, const T* x, double b,
+                          const T* y, double c, const T* z) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T r = T(a) * x[i];
+        if (y) r += T(b) * y[i];
+        if (z) r += T(c) * z[i];
+        out[i] = r;
+    }
+}
+
+template <typename T>
+__global__ void k_hadamard2(T* out, long long n, const T* a, const T* b, const T* c,
+                            const T* d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = c ? a[i] * b[i] - c[i] * d[i] : a[i] * b[i];
+}
+
+template <typename T>
+__global__ void k_hadamard_batched(T* M, const T* z, long long per, int nb) {
+    const long long total = per * nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        M[i] *= z[i % per];
+}
+
+template <typename T>
+__global__ void k_kr(const T* A, const T* B, int na, int nbr, int P, T* out) {
+    const long long total = (long long)na * nbr * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(idx % P);
+        const long long ia = idx / P;
+        const int i = (int)(ia / nbr), a = (int)(ia % nbr);
+        out[idx] = A[(long long)i * P + X] * B[(long long)a * P + X];
+    }
+}
+
+template <typename T>
+__global__ void k_scale_rows(const T* y, int R, int P, const T* w, int x0, int nx,
+                             T* out) {
+    const long long per = (long long)R * P, total = per * nx;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(idx / per);
+        const long long e = idx % per;
+        const int Y = (int)(e % P);
+        out[idx] = y[e] * w[(long long)(x0 + x) * P + Y];
+    }
+}
+
+// Register-tiled triangle kernel: a block owns TXB amplitude indices X and a
+// 32 x 32 (Y, Z) tile of H; per grid point I it stages G_I^{YZ} and the E, F
+// rows of its X's in shared memory, 4 grid points per stage.
+constexpr int TXB = 4, TYZ = 32, IST = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_triangle(T* H, const T* E, const T* F,
+                                                  const T* G, int P, int nI) {
+    __shared__ T sG[IST][TYZ][TYZ + 1];
+    __shared__ T sEy[IST][TXB][TYZ], sEz[IST][TXB][TYZ];
+    __shared__ T sFy[IST][TXB][TYZ], sFz[IST][TXB][TYZ];
+    const int Z0 = blockIdx.x * TYZ, Y0 = blockIdx.y * TYZ, X0 = blockIdx.z * TXB;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long PP = (long long)P * P;
+    T acc[TXB][2][2];
+#pragma unroll
+    for (int x = 0; x < TXB; ++x)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) acc[x][i][j] = 0;
+    for (int I0 = 0; I0 < nI; I0 += IST) {
+        for (int e = tid; e < IST * TYZ * TYZ; e += 256) {
+            int s = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
+            int I = I0 + s, Y = Y0 + r, Z = Z0 + c;
+            sG[s][r][c] = (I < nI && Y < P && Z < P) ? G[I * PP + (long long)Y * P + Z] : T(0);
+        }
+        for (int e = tid; e < IST * TXB * TYZ; e += 256) {
+            int s = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
+            int I = I0 + s, X = X0 + x;
+            bool okx = (I < nI && X < P);
+            long long base = I * PP + (long long)X * P;
+            sEy[s][x][c] = (okx && Y0 + c < P) ? E[base + Y0 + c] : T(0);
+            sEz[s][x][c] = (okx && Z0 + c < P) ? E[base + Z0 + c] : T(0);
+            sFy[s][x][c] = (okx && Y0 + c < P) ? F[base + Y0 + c] : T(0);
+            sFz[s][x][c] = (okx && Z0 + c < P) ? F[base + Z0 + c] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < IST; ++s) {
+            T g[2][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) g[i][j] = sG[s][ty + 16 * i][tx + 16 * j];
+#pragma unroll
+            for (int x = 0; x < TXB; ++x) {
+                T ey[2], fy[2], ez[2], fz[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    ey[i] = sEy[s][x][ty + 16 * i];
+                    fy[i] = sFy[s][x][ty + 16 * i];
+                    ez[i] = sEz[s][x][tx + 16 * i];
+                    fz[i] = sFz[s][x][tx + 16 * i];
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        T t = ey[i] * fz[j];
+                        t = fma(ez[j], fy[i], t);
+                        acc[x][i][j] = fma(t, g[i][j], acc[x][i][j]);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < TXB; ++x) {
+        int X = X0 + x;
+        if (X >= P) continue;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            int Y = Y0 + ty + 16 * i;
+            if (Y >= P) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                int Z = Z0 + tx + 16 * j;
+                if (Z >= P) continue;
+                H[((long long)X * P + Y) * P + Z] += acc[x][i][j];
+            }
+        }
+    }
+}
+
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int NPART = 512;
+
+template <typename T>
+__global__ void k_dot_part(const T* a, const T* b, long long n, double* part) {
+    double acc = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_parts(const double* part, int n, double* out) {
+    double acc = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+template <typename T>
+__global__ void k_singles_energy(const T* Lov, const T* Mo, const T* t1, int o, int v,
+                                 double* part) {
+    const int k = blockIdx.x;
+    const T* L = Lov + (long long)k * o * v;
+    const T* M = Mo + (long long)k * o * o;
+    double s = 0, q = 0;
+    for (int e = threadIdx.x; e < o * v; e += blockDim.x) s += (double)L[e] * (double)t1[e];
+    for (int e = threadIdx.x; e < o * o; e += blockDim.x) {
+        int i = e / o, j = e % o;
+        q += (double)M[e] * (double)M[j * o + i];
+    }
+    s = block_sum(s);
+    __syncthreads();
+    q = block_sum(q);
+    if (threadIdx.x == 0) part[k] = 2.0 * s * s - q;
+}
+
+__global__ void k_nonfinite(const double* a, long long n, int* flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicOr(flag, 1);
+}
+
+template <typename T>
+__global__ void k_accumulate(double* acc, const T* part, long long n, double scale) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc[i] += scale * (double)part[i];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t split_blocks(const T* full, int nb, int o, int v, Blocks<T> out,
+                         cudaStream_t s) {
+    long long n = (long long)nb * (o + v) * (o + v);
+    k_split<T><<<nblocks(n), NT, 0, s>>>(full, nb, o, v, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t transpose_batched(const T* in, T* out, int nb, int rows, int cols,
+                              cudaStream_t s) {
+    dim3 grid(cdiv(cols, 32), cdiv(rows, 32), nb);
+    k_transpose<T><<<grid, dim3(32, 8), 0, s>>>(in, out, nb, rows, cols);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t convert(const double* in, T* out, long long n, cudaStream_t s) {
+    k_convert<T><<<nblocks(n), NT, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t to_double(const T* in, double* out, long long n, cudaStream_t s) {
+    k_to_double<T><<<nblocks(n), NT, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t alg1_combine(const T* Bbar, const T* Btil, const T* oo, const T* vv,
+                         T* C1, T* Ccross, int P, int nb, cudaStream_t s) {
+    k_alg1<T><<<nblocks((long long)P * P), NT, 0, s>>>(Bbar, Btil, oo, vv, C1, Ccross, P, nb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t diag_reduce(const T* y, const T* M, int R, int P, int nb, T* out, int ldo,
+                        int col0, cudaStream_t s) {
+    k_diag_reduce<T><<<nblocks((long long)nb * P), NT, 0, s>>>(y, M, R, P, nb, out, ldo, col0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P, int nb,
+                     cudaStream_t s) {
+    k_w_single<T><<<nblocks((long long)nb * P * P), NT, 0, s>>>(TA, ldta, Tc, E, W, P, nb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s) {
+    k_traces<T><<<cdiv(nb, 128), 128, 0, s>>>(M, n, nb, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lincomb(T* out, long long n, double a, const T* x, double b, const T* y,
+                    double c, const T* z, cudaStream_t s) {
+    k_lincomb<T><<<nblocks(n), NT, 0, s>>>(out, n, a, x, b, y, c, z);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hadamard2(T* out, long long n, const T* a, const T* b, const T* c,
+                      const T* d, cudaStream_t s) {
+    k_hadamard2<T><<<nblocks(n), NT, 0, s>>>(out, n, a, b, c, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t hadamard_batched(T* M, const T* z, long long per, int nb, cudaStream_t s) {
+    k_hadamard_batched<T><<<nblocks(per * nb), NT, 0, s>>>(M, z, per, nb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t khatri_rao(const T* A, const T* B, int na, int nbr, int P, T* out,
+                       cudaStream_t s) {
+    k_kr<T><<<nblocks((long long)na * nbr * P), NT, 0, s>>>(A, B, na, nbr, P, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* out,
+                       cudaStream_t s) {
+    k_scale_rows<T><<<nblocks((long long)R * P * nx), NT, 0, s>>>(y, R, P, w, x0, nx, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
+                     cudaStream_t s) {
+    dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
+    k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dot(const T* a, const T* b, long long n, double* scratch, double* out,
+                cudaStream_t s) {
+    k_dot_part<T><<<NPART, NT, 0, s>>>(a, b, n, scratch);
+    k_sum_parts<<<1, NT, 0, s>>>(scratch, NPART, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t singles_energy(const T* Lov, const T* Mo, const T* t1, int K, int o, int v,
+                           double* scratch, double* out, cudaStream_t s) {
+    k_singles_energy<T><<<K, NT, 0, s>>>(Lov, Mo, t1, o, v, scratch);
+    k_sum_parts<<<1, NT, 0, s>>>(scratch, K, out);
+    return cudaGetLastError();
+}
+
+cudaError_t any_nonfinite(const double* a, long long n, int* flag, cudaStream_t s) {
+    k_nonfinite<<<nblocks(n), NT, 0, s>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
+                       cudaStream_t s) {
+    k_accumulate<T><<<nblocks(n), NT, 0, s>>>(acc, part, n, scale);
+    return cudaGetLastError();
+}
+
+#define THC_INSTANTIATE(T)                                                              \
+    template cudaError_t split_blocks<T>(const T*, int, int, int, Blocks<T>, cudaStream_t); \
+    template cudaError_t transpose_batched<T>(const T*, T*, int, int, int, cudaStream_t); \
+    template cudaError_t convert<T>(const double*, T*, long long, cudaStream_t);        \
+    template cudaError_t to_double<T>(const T*, double*, long long, cudaStream_t);      \
+    template cudaError_t alg1_combine<T>(const T*, const T*, const T*, const T*, T*, T*, \
+                                         int, int, cudaStream_t);                       \
+    template cudaError_t diag_reduce<T>(const T*, const T*, int, int, int, T*, int, int, \
+                                        cudaStream_t);                                  \
+    template cudaError_t w_single<T>(const T*, int, const T*, const T*, T*, int, int,  \
+                                     cudaStream_t);                                     \
+    template cudaError_t traces<T>(const T*, int, int, T*, cudaStream_t);               \
+    template cudaError_t lincomb<T>(T*, long long, double, const T*, double, const T*, \
+                                    double, const T*, cudaStream_t);                    \
+    template cudaError_t hadamard2<T>(T*, long long, const T*, const T*, const T*,     \
+                                      const T*, cudaStream_t);                          \
+    template cudaError_t hadamard_batched<T>(T*, const T*, long long, int, cudaStream_t); \
+    template cudaError_t khatri_rao<T>(const T*, const T*, int, int, int, T*, cudaStream_t); \
+    template cudaError_t scale_rows<T>(const T*, int, int, const T*, int, int, T*,     \
+                                       cudaStream_t);                                   \
+    template cudaError_t triangle<T>(T*, const T*, const T*, const T*, int, int,       \
+                                     cudaStream_t);                                     \
+    template cudaError_t dot<T>(const T*, const T*, long long, double*, double*,       \
+                                cudaStream_t);                                          \
+    template cudaError_t singles_energy<T>(const T*, const T*, const T*, int, int, int, \
+                                           double*, double*, cudaStream_t);             \
+    template cudaError_t accumulate<T>(double*, const T*, long long, double, cudaStream_t);
+
+THC_INSTANTIATE(double)
+THC_INSTANTIATE(float)
+
+}  // namespace thc

@@ -1,0 +1,397 @@
+// Jacobi + DIIS solver of the projected THC-RR-CCSD amplitude equations.
+//
+// The paper states only that the residual is converged to 1e-8 (Fig. 3); the
+// update is the orbital-energy Jacobi step in the orthonormal basis of Eq. 22
+// (the working variable T^PQ the paper recommends) with Pulay DIIS, all in
+// float64 on the device.  The only host arithmetic is the (m+1) x (m+1) DIIS
+// system.
+#include <cusolverDn.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+
+#include "solver.cuh"
+
+namespace thc {
+
+namespace {
+
+using View64 = View<double>;
+View64 rm64(const double* p, long long ld) { return View64{p, ld, 1}; }
+View64 tr64(const double* p, long long ld) { return View64{p, 1, ld}; }
+
+__global__ void k_scale_diag(const double* y, const double* eps, int R, int P, double* out) {
+    const long long total = (long long)R * P;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = y[i] * eps[i / P];
+}
+
+__global__ void k_metric(const double* oo, const double* vv, const double* oe,
+                         const double* ve, double* S, double* F, long long nn) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * blockDim.x) {
+        S[i] = oo[i] * vv[i];
+        F[i] = oo[i] * ve[i] - oe[i] * vv[i];
+    }
+}
+
+// X[i][k] = V[(k0 + k) * P + i] / sqrt(s[k0 + k])   (cuSOLVER returns V column-major)
+__global__ void k_half_inverse(const double* V, const double* s, int P, int k0, int r,
+                               double* X) {
+    const long long total = (long long)P * r;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / r), k = (int)(idx % r);
+        X[idx] = V[(long long)(k0 + k) * P + i] / sqrt(s[k0 + k]);
+    }
+}
+
+// row-major W[i][k] from column-major eigenvectors
+__global__ void k_colmajor_to_rowmajor(const double* V, int r, double* W) {
+    const long long total = (long long)r * r;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / r), k = (int)(idx % r);
+        W[idx] = V[(long long)k * r + i];
+    }
+}
+
+__global__ void k_symmetrize(double* A, int n) {
+    const long long total = (long long)n * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        if (i < j) {
+            const double m = 0.5 * (A[idx] + A[(long long)j * n + i]);
+            A[idx] = m;
+            A[(long long)j * n + i] = m;
+        }
+    }
+}
+
+// step = [-sigma1 / (eps_a - eps_i) | -sigma_q / (e_P + e_Q)];  xnew = x + step
+__global__ void k_jacobi(const double* sig1, const double* sq, const double* eps,
+                         const double* e, int o, int v, int r, const double* x, double* step,
+                         double* xnew) {
+    const long long ov = (long long)o * v, total = ov + (long long)r * r;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double s;
+        if (idx < ov) {
+            const int i = (int)(idx / v), a = (int)(idx % v);
+            s = -sig1[idx] / (eps[o + a] - eps[i]);
+        } else {
+            const long long q = idx - ov;
+            const int p = (int)(q / r), qq = (int)(q % r);
+            s = -sq[q] / (e[p] + e[qq]);
+        }
+        step[idx] = s;
+        xnew[idx] = x[idx] + s;
+    }
+}
+
+__global__ void k_combine(const double* hx, const double* c, int m, long long len,
+                          double* out) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < len;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int k = 0; k < m; ++k) s += c[k] * hx[(long long)k * len + idx];
+        out[idx] = s;
+    }
+}
+
+__device__ double block_sum64(double v) {
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// out[k] = <a_k, b> for m vectors a_k (stride len), one block per k.
+__global__ void k_multidot(const double* A, const double* b, long long len, double* out) {
+    const double* a = A + (long long)blockIdx.x * len;
+    double s = 0;
+    for (long long i = threadIdx.x; i < len; i += blockDim.x) s += a[i] * b[i];
+    s = block_sum64(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+unsigned nb(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152 * 32); }
+
+// Solve the bordered DIIS system; returns false if it is singular.
+bool diis_coefficients(const std::vector<double>& Bm, int m, std::vector<double>& c) {
+    const int N = m + 1;
+    std::vector<double> A((size_t)N * N, 0.0), rhs(N, 0.0);
+    double scale = 0;
+    for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(Bm[(size_t)i * m + i]));
+    if (scale <= 0) return false;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) A[(size_t)i * N + j] = Bm[(size_t)i * m + j] / scale;
+    for (int i = 0; i < m; ++i) A[(size_t)i * N + m] = A[(size_t)m * N + i] = -1.0;
+    rhs[m] = -1.0;
+    // Gaussian elimination with partial pivoting.
+    for (int k = 0; k < N; ++k) {
+        int p = k;
+        for (int i = k + 1; i < N; ++i)
+            if (std::fabs(A[(size_t)i * N + k]) > std::fabs(A[(size_t)p * N + k])) p = i;
+        if (std::fabs(A[(size_t)p * N + k]) < 1e-300) return false;
+        if (p != k) {
+            for (int j = 0; j < N; ++j) std::swap(A[(size_t)k * N + j], A[(size_t)p * N + j]);
+            std::swap(rhs[k], rhs[p]);
+        }
+        for (int i = k + 1; i < N; ++i) {
+            const double f = A[(size_t)i * N + k] / A[(size_t)k * N + k];
+            for (int j = k; j < N; ++j) A[(size_t)i * N + j] -= f * A[(size_t)k * N + j];
+            rhs[i] -= f * rhs[k];
+        }
+    }
+    std::vector<double> sol(N);
+    for (int i = N - 1; i >= 0; --i) {
+        double s = rhs[i];
+        for (int j = i + 1; j < N; ++j) s -= A[(size_t)i * N + j] * sol[j];
+        sol[i] = s / A[(size_t)i * N + i];
+    }
+    c.assign(sol.begin(), sol.begin() + m);
+    for (double ci : c)
+        if (!std::isfinite(ci)) return false;
+    return true;
+}
+
+struct Cusolver {
+    cusolverDnHandle_t h = nullptr;
+    ~Cusolver() { if (h) cusolverDnDestroy(h); }
+};
+
+Err syevd(cudaStream_t st, double* A, int N, double* w) {
+    Cusolver cs;
+    if (cusolverDnCreate(&cs.h) != CUSOLVER_STATUS_SUCCESS)
+        return Err{THC_ERR_CUDA, "cusolverDnCreate failed"};
+    cusolverDnSetStream(cs.h, st);
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(cs.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, N, A,
+                                    N, w, &lwork) != CUSOLVER_STATUS_SUCCESS)
+        return Err{THC_ERR_CUDA, "syevd buffer size failed"};
+    DBuf<double> work;
+    DBuf<int> info;
+    THC_TRY(work.alloc((size_t)std::max(lwork, 1)));
+    THC_TRY(info.alloc(1));
+    if (cusolverDnDsyevd(cs.h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, N, A, N, w,
+                         work.p, lwork, info.p) != CUSOLVER_STATUS_SUCCESS)
+        return Err{THC_ERR_CUDA, "syevd failed"};
+    int hinfo = 0;
+    THC_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (hinfo != 0) return Err{THC_ERR_NUMERIC, "metric eigensolver did not converge"};
+    return Err{};
+}
+
+}  // namespace
+
+Err Solver::mm(cudaStream_t st, int M, int N, int K, View<double> A, View<double> Bv,
+               double* Cp, long long ldc, double alpha, double beta) {
+    Gemm<double> g;
+    g.M = M; g.N = N; g.K = K; g.A = A; g.B = Bv; g.C = Cp; g.ldc = ldc;
+    g.alpha = alpha; g.beta = beta;
+    g.ws = ws.p; g.ws_elems = ws.n;
+    THC_CUDA(gemm_simt(g, st));
+    return Err{};
+}
+
+template <typename T>
+Err Solver::setup(Engine<T>& eng, double cutoff) {
+    cudaStream_t st = eng.st;
+    P = eng.P; o = eng.o; v = eng.v;
+    const int n = o + v;
+    const long long PP = (long long)P * P;
+    THC_TRY(ws.alloc((size_t)std::max<long long>(4 * PP, 1 << 20)));
+    THC_TRY(epsd.alloc(n));
+    THC_CUDA(cudaMemcpyAsync(epsd.p, eng.eps_h.data(), sizeof(double) * n,
+                             cudaMemcpyHostToDevice, st));
+    DBuf<double> yd, yo_e, yv_e, oo, vv, oe, ve, F, Wm, sv;
+    THC_TRY(yd.alloc((size_t)n * P));
+    if constexpr (std::is_same<T, double>::value) {
+        THC_CUDA(cudaMemcpyAsync(yd.p, eng.y.p, sizeof(double) * n * P, cudaMemcpyDeviceToDevice, st));
+    } else {
+        THC_CUDA(to_double(eng.y.p, yd.p, (long long)n * P, st));
+    }
+    const double* yo = yd.p;
+    const double* yv = yd.p + (long long)o * P;
+    THC_TRY(yo_e.alloc((size_t)o * P));
+    THC_TRY(yv_e.alloc((size_t)v * P));
+    k_scale_diag<<<nb((long long)o * P), 256, 0, st>>>(yo, epsd.p, o, P, yo_e.p);
+    k_scale_diag<<<nb((long long)v * P), 256, 0, st>>>(yv, epsd.p + o, v, P, yv_e.p);
+    THC_CUDA(cudaGetLastError());
+    for (DBuf<double>* b : {&oo, &vv, &oe, &ve, &F}) THC_TRY(b->alloc(PP));
+    THC_TRY(Sd.alloc(PP));
+    THC_TRY(mm(st, P, P, o, tr64(yo, P), rm64(yo, P), oo.p, P, 1, 0));
+    THC_TRY(mm(st, P, P, v, tr64(yv, P), rm64(yv, P), vv.p, P, 1, 0));
+    THC_TRY(mm(st, P, P, o, tr64(yo, P), rm64(yo_e.p, P), oe.p, P, 1, 0));
+    THC_TRY(mm(st, P, P, v, tr64(yv, P), rm64(yv_e.p, P), ve.p, P, 1, 0));
+    k_metric<<<nb(PP), 256, 0, st>>>(oo.p, vv.p, oe.p, ve.p, Sd.p, F.p, PP);
+    THC_CUDA(cudaGetLastError());
+    k_symmetrize<<<nb(PP), 256, 0, st>>>(F.p, P);
+    // S = V diag(s) V^T
+    THC_TRY(Wm.alloc(PP));
+    THC_TRY(sv.alloc(P));
+    THC_CUDA(cudaMemcpyAsync(Wm.p, Sd.p, sizeof(double) * PP, cudaMemcpyDeviceToDevice, st));
+    THC_TRY(syevd(st, Wm.p, P, sv.p));
+    std::vector<double> s(P);
+    THC_CUDA(cudaMemcpy(s.data(), sv.p, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    const double smax = s[P - 1];
+    if (!(smax > 0)) return Err{THC_ERR_NUMERIC, "metric S has no positive eigenvalue"};
+    int k0 = 0;
+    while (k0 < P && !(s[k0] > cutoff * smax)) ++k0;
+    r = P - k0;
+    DBuf<double> X, M, tmpPr;
+    THC_TRY(X.alloc((size_t)P * r));
+    k_half_inverse<<<nb((long long)P * r), 256, 0, st>>>(Wm.p, sv.p, P, k0, r, X.p);
+    THC_CUDA(cudaGetLastError());
+    // M = X^T F X, eigenvectors W:  C = X W
+    THC_TRY(tmpPr.alloc((size_t)P * r));
+    THC_TRY(M.alloc((size_t)r * r));
+    THC_TRY(mm(st, P, r, P, rm64(F.p, P), rm64(X.p, r), tmpPr.p, r, 1, 0));
+    THC_TRY(mm(st, r, r, P, tr64(X.p, r), rm64(tmpPr.p, r), M.p, r, 1, 0));
+    k_symmetrize<<<nb((long long)r * r), 256, 0, st>>>(M.p, r);
+    THC_TRY(e.alloc(r));
+    THC_TRY(syevd(st, M.p, r, e.p));
+    DBuf<double> W;
+    THC_TRY(W.alloc((size_t)r * r));
+    k_colmajor_to_rowmajor<<<nb((long long)r * r), 256, 0, st>>>(M.p, r, W.p);
+    THC_TRY(C.alloc((size_t)P * r));
+    THC_TRY(mm(st, P, r, r, rm64(X.p, r), rm64(W.p, r), C.p, r, 1, 0));
+    THC_TRY(SC.alloc((size_t)P * r));
+    THC_TRY(mm(st, P, r, P, rm64(Sd.p, P), rm64(C.p, r), SC.p, r, 1, 0));
+    len = (long long)o * v + (long long)r * r;
+    THC_TRY(Zc.alloc(PP));
+    THC_TRY(tmp.alloc((size_t)P * r));
+    THC_TRY(sq.alloc((size_t)r * r));
+    THC_TRY(x.alloc(len));
+    THC_TRY(xnew.alloc(len));
+    THC_TRY(step.alloc(len));
+    THC_TRY(red.alloc(1024));
+    THC_TRY(dots.alloc(64));
+    THC_CUDA(cudaStreamSynchronize(st));
+    return Err{};
+}
+
+template <typename T>
+Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, double* t1_io,
+                thc_report* rep) {
+    cudaStream_t st = eng.st;
+    const auto t0 = std::chrono::steady_clock::now();
+    const long long PP = (long long)P * P, ov = (long long)o * v, rr = (long long)r * r;
+    const int m = std::max(0, std::min(opts.diis_n, 32));
+    if (m > 0 && hx.n < (size_t)m * len) {
+        THC_TRY(hx.alloc((size_t)m * len));
+        THC_TRY(he.alloc((size_t)m * len));
+    }
+    nhist = 0;
+    head = 0;
+    B.assign((size_t)std::max(m, 1) * std::max(m, 1), 0.0);
+    // Start point: t1 and T = (S C)^T Zc (S C).
+    THC_CUDA(cudaMemcpyAsync(x.p, t1_io, sizeof(double) * ov, cudaMemcpyDefault, st));
+    THC_CUDA(cudaMemcpyAsync(Zc.p, Zc_io, sizeof(double) * PP, cudaMemcpyDefault, st));
+    THC_TRY(eng.check_sym(Zc.p, P, 1e-12, "Zc"));
+    THC_TRY(mm(st, P, r, P, rm64(Zc.p, P), rm64(SC.p, r), tmp.p, r, 1, 0));
+    THC_TRY(mm(st, r, r, P, tr64(SC.p, r), rm64(tmp.p, r), x.p + ov, r, 1, 0));
+    k_symmetrize<<<nb(rr), 256, 0, st>>>(x.p + ov, r);
+    double energy = 0, norm = 0, e_prev = 0;
+    bool converged = false;
+    int it = 0;
+    const int max_iter = opts.max_iter > 0 ? opts.max_iter : 100;
+    for (it = 1; it <= max_iter; ++it) {
+        // Zc = C T C^T
+        THC_TRY(mm(st, P, r, r, rm64(C.p, r), rm64(x.p + ov, r), tmp.p, r, 1, 0));
+        THC_TRY(mm(st, P, P, r, rm64(tmp.p, r), tr64(C.p, r), Zc.p, P, 1, 0));
+        k_symmetrize<<<nb(PP), 256, 0, st>>>(Zc.p, P);
+        THC_CUDA(cudaGetLastError());
+        THC_TRY(eng.set_state(Zc.p, x.p));
+        THC_TRY(eng.residual_dev(true));
+        // sigma_q = C^T sigma C
+        THC_TRY(mm(st, P, r, P, rm64(eng.sig.p, P), rm64(C.p, r), tmp.p, r, 1, 0));
+        THC_TRY(mm(st, r, r, P, tr64(C.p, r), rm64(tmp.p, r), sq.p, r, 1, 0));
+        k_multidot<<<1, 256, 0, st>>>(eng.sig1.p, eng.sig1.p, ov, dots.p);
+        k_multidot<<<1, 256, 0, st>>>(sq.p, sq.p, rr, dots.p + 1);
+        THC_CUDA(cudaGetLastError());
+        double h[4];
+        THC_CUDA(cudaMemcpyAsync(h, dots.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        THC_CUDA(cudaMemcpyAsync(h + 2, eng.en.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        THC_CUDA(cudaStreamSynchronize(st));
+        norm = std::sqrt(h[0] + h[1]);
+        energy = h[2] + h[3];
+        if (!std::isfinite(norm) || !std::isfinite(energy))
+            return Err{THC_ERR_NUMERIC, "solver diverged (non-finite residual)"};
+        if (opts.verbose)
+            fprintf(stderr, "thc_solve it %3d  E = %.12f  |r| = %.3e\n", it, energy, norm);
+        const bool de_ok = opts.e_tol <= 0 || (it > 1 && std::fabs(energy - e_prev) < opts.e_tol);
+        e_prev = energy;
+        if (norm < opts.r_tol && de_ok) {
+            converged = true;
+            break;
+        }
+        k_jacobi<<<nb(len), 256, 0, st>>>(eng.sig1.p, sq.p, epsd.p, e.p, o, v, r, x.p,
+                                           step.p, xnew.p);
+        THC_CUDA(cudaGetLastError());
+        if (m > 0) {
+            const int slot = head;
+            head = (head + 1) % m;
+            nhist = std::min(nhist + 1, m);
+            THC_CUDA(cudaMemcpyAsync(hx.p + (long long)slot * len, xnew.p, sizeof(double) * len,
+                                     cudaMemcpyDeviceToDevice, st));
+            THC_CUDA(cudaMemcpyAsync(he.p + (long long)slot * len, step.p, sizeof(double) * len,
+                                     cudaMemcpyDeviceToDevice, st));
+            k_multidot<<<m, 256, 0, st>>>(he.p, step.p, len, dots.p);
+            THC_CUDA(cudaGetLastError());
+            std::vector<double> row(m);
+            THC_CUDA(cudaMemcpyAsync(row.data(), dots.p, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            THC_CUDA(cudaStreamSynchronize(st));
+            for (int k = 0; k < nhist; ++k) {
+                B[(size_t)slot * m + k] = row[k];
+                B[(size_t)k * m + slot] = row[k];
+            }
+            std::vector<double> c;
+            std::vector<double> Bsub((size_t)nhist * nhist);
+            for (int i = 0; i < nhist; ++i)
+                for (int j = 0; j < nhist; ++j) Bsub[(size_t)i * nhist + j] = B[(size_t)i * m + j];
+            if (nhist >= 2 && diis_coefficients(Bsub, nhist, c)) {
+                THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
+                                         cudaMemcpyHostToDevice, st));
+                k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
+                THC_CUDA(cudaGetLastError());
+            } else {
+                THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+            }
+        } else {
+            THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    // Write back the last evaluated point.
+    THC_CUDA(cudaMemcpyAsync(Zc_io, Zc.p, sizeof(double) * PP, cudaMemcpyDefault, st));
+    THC_CUDA(cudaMemcpyAsync(t1_io, eng.t1d.p, sizeof(double) * ov, cudaMemcpyDefault, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    rep->iters = converged ? it : max_iter;
+    rep->energy = energy;
+    rep->r_norm = norm;
+    rep->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (!converged) return Err{THC_ERR_NOT_CONVERGED, "thc_solve reached max_iter"};
+    return Err{};
+}
+
+template Err Solver::setup<double>(Engine<double>&, double);
+template Err Solver::setup<float>(Engine<float>&, double);
+template Err Solver::run<double>(Engine<double>&, const thc_solve_opts&, double*, double*,
+                                 thc_report*);
+template Err Solver::run<float>(Engine<float>&, const thc_solve_opts&, double*, double*,
+                                thc_report*);
+
+}  // namespace thc
