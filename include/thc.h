@@ -130,6 +130,9 @@ typedef struct {
     int diis_n;          /* DIIS subspace size (8), 0 = plain Jacobi */
     int use_mlp;         /* 1 = learned preconditioner proposals */
     int verbose;         /* 1 = one line per iteration on stderr */
+    double* history;     /* nullable host array of max_iter x 3 doubles: per
+                            iteration (energy, residual norm, seconds since
+                            the call started) */
 } thc_solve_opts;
 
 typedef struct {
@@ -156,6 +159,42 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts);
  */
 thc_status thc_solve(thc_ctx* ctx, const thc_solve_opts* opts,
                      double* Zc_inout, double* t1_inout, thc_report* report);
+
+/*
+ * Per-step device timing (CUDA events recorded on the context's stream
+ * around every step of thc_residual while profiling is on).  flops counts
+ * the algorithmic floating-point operations the step issued (2 per
+ * multiply-add of every contraction; 5 per (I,X,Y,Z) term of the triangle
+ * kernel), so flops / ms is the achieved rate of that step.
+ */
+enum {
+    THC_STEP_DRESS = 0,      /* T1 dressing of the Cholesky vectors (Eqs. 25-27) */
+    THC_STEP_FOCK = 1,       /* Coulomb/exchange parts of the dressed Fock matrix */
+    THC_STEP_ALG1 = 2,       /* ladders, Alg. 1 (+ Alg. 3 intermediate) */
+    THC_STEP_ALG2_8 = 3,     /* Alg. 2 and Alg. 8 per Cholesky vector */
+    THC_STEP_POST = 4,       /* Alg. 2/3 closing products, Algs. 9 and 10 */
+    THC_STEP_ALG6_GEMM = 5,  /* Alg. 6 lines 1-10 (contractions) */
+    THC_STEP_TRIANGLE = 6,   /* Alg. 6 line 11 (triangle kernel) */
+    THC_STEP_ALG6_POST = 7,  /* Alg. 6 lines 13-16 */
+    THC_STEP_ALG7 = 8,       /* Alg. 7 */
+    THC_STEP_ENERGY = 9,     /* energy */
+    THC_N_STEPS = 10
+};
+
+typedef struct {
+    double ms[THC_N_STEPS];         /* accumulated device time per step */
+    double flops[THC_N_STEPS];      /* accumulated algorithmic flops per step */
+    long long launches[THC_N_STEPS];/* timed segments (kernel launches for the triangle) */
+    long long residuals;            /* residual evaluations profiled */
+    long long kernel_launches;      /* library kernels launched while profiling */
+} thc_profile;
+
+/* Switch profiling on (1) or off (0); switching on clears the counters. */
+thc_status thc_profile_enable(thc_ctx* ctx, int on);
+/* Copy the accumulated counters into *out. */
+thc_status thc_profile_read(thc_ctx* ctx, thc_profile* out);
+/* Name of a step ("dress", "fock", ...), or NULL if out of range. */
+const char* thc_step_name(int step);
 
 /* Text of the first error recorded on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx or thc_destroy.  ctx may be NULL, which

@@ -27,12 +27,22 @@ class ThcConfig(C.Structure):
 
 class ThcSolveOpts(C.Structure):
     _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
-                ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int)]
+                ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int),
+                ("history", C.c_void_p)]
 
 
 class ThcReport(C.Structure):
     _fields_ = [("iters", C.c_int), ("mlp_accepted", C.c_int), ("mlp_rejected", C.c_int),
                 ("energy", C.c_double), ("r_norm", C.c_double), ("wall_s", C.c_double)]
+
+
+N_STEPS = 10
+
+
+class ThcProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * N_STEPS), ("flops", C.c_double * N_STEPS),
+                ("launches", C.c_longlong * N_STEPS), ("residuals", C.c_longlong),
+                ("kernel_launches", C.c_longlong)]
 
 
 @dataclass
@@ -66,6 +76,9 @@ _SIGNATURES = {
     "thc_residual": (C.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
     "thc_energy": (C.c_int, [_VP, _DP, _DP, _DP]),
     "thc_solve": (C.c_int, [_VP, C.POINTER(ThcSolveOpts), _DP, _DP, C.POINTER(ThcReport)]),
+    "thc_profile_enable": (C.c_int, [_VP, C.c_int]),
+    "thc_profile_read": (C.c_int, [_VP, C.POINTER(ThcProfile)]),
+    "thc_step_name": (C.c_char_p, [C.c_int]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }
@@ -188,8 +201,11 @@ class Context:
         return e.value
 
     def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
-              use_mlp=False, verbose=False, raise_on_failure=True):
-        """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero."""
+              use_mlp=False, verbose=False, raise_on_failure=True, history=None):
+        """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero.
+
+        If ``history`` is a list, (energy, |r|, seconds) per iteration is
+        appended to it."""
         if Zc is None:
             Zc = np.zeros((self.P, self.P))
         if t1 is None:
@@ -200,13 +216,32 @@ class Context:
         self._lib.thc_solve_opts_default(C.byref(opts))
         opts.r_tol, opts.e_tol, opts.max_iter = r_tol, e_tol, max_iter
         opts.diis_n, opts.use_mlp, opts.verbose = diis_n, int(use_mlp), int(verbose)
+        hbuf = np.zeros((max(1, max_iter), 3))
+        opts.history = hbuf.ctypes.data
         rep = ThcReport()
         st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
+        if history is not None:
+            history.extend(tuple(r) for r in hbuf[:rep.iters])
         report = Report(STATUS.get(st, str(st)), rep.iters, rep.energy, rep.r_norm, rep.wall_s,
                         rep.mlp_accepted, rep.mlp_rejected)
         if st != 0 and raise_on_failure:
             self._check(st)
         return Zc, t1, report
+
+    def profile(self, on=True):
+        """Switch per-step device timing on (clears counters) or off."""
+        self._check(self._lib.thc_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        """{step name: (ms, flops, launches)} accumulated since profile(True)."""
+        p = ThcProfile()
+        self._check(self._lib.thc_profile_read(self._h, C.byref(p)))
+        out = {}
+        for i in range(N_STEPS):
+            out[self._lib.thc_step_name(i).decode()] = (p.ms[i], p.flops[i], p.launches[i])
+        out["residuals"] = p.residuals
+        out["kernel_launches"] = p.kernel_launches
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

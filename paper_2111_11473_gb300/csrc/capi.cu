@@ -138,6 +138,38 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
     return THC_OK;
 }
 
+thc_status thc_profile_enable(thc_ctx* c, int on) {
+    if (!c) return THC_ERR_ARG;
+    thc::Profiler& p = c->e64 ? c->e64->prof : c->e32->prof;
+    p.on = on != 0;
+    p.reset();
+    p.marks.clear();
+    p.used = 0;
+    p.cur = -1;
+    return THC_OK;
+}
+
+thc_status thc_profile_read(thc_ctx* c, thc_profile* out) {
+    if (!c || !out) return THC_ERR_ARG;
+    const thc::Profiler& p = c->e64 ? c->e64->prof : c->e32->prof;
+    for (int i = 0; i < THC_N_STEPS; ++i) {
+        out->ms[i] = p.ms[i];
+        out->flops[i] = p.flops[i];
+        out->launches[i] = p.launches[i];
+    }
+    out->residuals = p.residuals;
+    out->kernel_launches = p.kernel_launches;
+    return THC_OK;
+}
+
+const char* thc_step_name(int step) {
+    static const char* names[THC_N_STEPS] = {"dress", "fock", "alg1", "alg2_8", "post",
+                                             "alg6_gemm", "triangle", "alg6_post", "alg7",
+                                             "energy"};
+    if (step < 0 || step >= THC_N_STEPS) return nullptr;
+    return names[step];
+}
+
 const char* thc_last_error(const thc_ctx* c) {
     if (!c) return g_init_error.c_str();
     return c->err.c_str();

@@ -63,6 +63,10 @@ struct Gemm {
     int splits = 1;        // set by the launcher
 };
 
+// Number of kernels this library has launched (all threads, all contexts).
+long long launches();
+void count_launches(int n);
+
 cudaError_t gemm_simt(const Gemm<double>& g, cudaStream_t s);
 cudaError_t gemm_simt(const Gemm<float>& g, cudaStream_t s);
 

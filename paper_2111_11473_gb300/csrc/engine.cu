@@ -64,6 +64,7 @@ Err Engine<T>::check_sym(const double* a, int nn_, double rel, const char* what)
     THC_CUDA(cudaMemsetAsync(chk.p, 0, 3 * sizeof(unsigned long long), st));
     const long long tot = (long long)nn_ * nn_;
     k_asym<<<(unsigned)std::min<long long>((tot + 255) / 256, 152 * 32), 256, 0, st>>>(a, nn_, chk.p);
+    count_launches(1);
     THC_CUDA(cudaGetLastError());
     THC_CUDA(cudaMemcpyAsync(h, chk.p, sizeof(h), cudaMemcpyDeviceToHost, st));
     THC_CUDA(cudaStreamSynchronize(st));
@@ -87,6 +88,44 @@ Err Engine<T>::check_finite(const double* a, long long count, const char* what) 
 }
 
 template <typename T>
+void Engine<T>::seg_begin(int step) {
+    if (!prof.on) return;
+    if (prof.cur >= 0) seg_end();
+    cudaEvent_t e = prof.next_event();
+    cudaEventRecord(e, st);
+    prof.marks.push_back({step, {prof.used - 1, -1}});
+    prof.cur = step;
+}
+
+template <typename T>
+void Engine<T>::seg_end() {
+    if (!prof.on || prof.cur < 0) return;
+    cudaEvent_t e = prof.next_event();
+    cudaEventRecord(e, st);
+    prof.marks.back().second.second = prof.used - 1;
+    prof.cur = -1;
+}
+
+template <typename T>
+Err Engine<T>::prof_collect() {
+    if (!prof.on) return Err{};
+    seg_end();
+    THC_CUDA(cudaStreamSynchronize(st));
+    for (auto& m : prof.marks) {
+        if (m.second.second < 0) continue;
+        float t = 0;
+        THC_CUDA(cudaEventElapsedTime(&t, prof.pool[m.second.first], prof.pool[m.second.second]));
+        prof.ms[m.first] += t;
+        prof.launches[m.first] += 1;
+    }
+    prof.marks.clear();
+    prof.used = 0;
+    prof.residuals += 1;
+    prof.kernel_launches = launches() - prof.launch_base;
+    return Err{};
+}
+
+template <typename T>
 static View<T> rm(const T* p, long long ld) { return View<T>{p, ld, 1}; }
 template <typename T>
 static View<T> tr(const T* p, long long ld) { return View<T>{p, 1, ld}; }
@@ -101,6 +140,7 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     g.C = C; g.ldc = ldc; g.sCb = sCb;
     g.alpha = alpha; g.beta = beta; g.reduce = reduce;
     g.ws = splitk.p; g.ws_elems = splitk.n;
+    if (prof.on && prof.cur >= 0) prof.flops[prof.cur] += 2.0 * M * N * (double)Kd * batch;
     THC_CUDA(gemm_simt(g, st));
     return Err{};
 }
@@ -323,9 +363,11 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         THC_CUDA(diag_reduce(yo, M3.p, o, P, nb, Atil.p, K, A0, st));
         THC_TRY(mm(P, P, o, tr(M3.p, P), rm(yo, P), E.p, P, 1, 0, nb, (long long)o * P, 0, PP));
         k_wen_acc<T><<<cdiv(PP, 256), 256, 0, st>>>(E.p, P, nb, Wen.p);
+        count_launches(1);
         THC_CUDA(cudaGetLastError());
     }
     k_outer_acc<T><<<cdiv(PP, 256), 256, 0, st>>>(Atil.p, P, K, Wen.p, 2.0);
+    count_launches(1);
     THC_CUDA(cudaGetLastError());
 
     // ---- Alg. 6 fixed parts: B_ia^I = sum_J x_i^J x_a^J z^IJ (line 2),
@@ -405,6 +447,7 @@ Err Engine<T>::alg6(T* sgm) {
     const long long ov = (long long)o * v, PP = (long long)P * P;
     const T* yo = y.p;
     const T* yv = y.p + (long long)o * P;
+    seg_begin(THC_STEP_ALG6_GEMM);
     // A_ia^X = sum_Y y_i^Y y_a^Y T^XY  (line 1), C_i^XY (line 4), D_a^XY (line 5)
     THC_TRY(mm((int)ov, P, P, rm(KRy.p, P), rm(Tc.p, P), A6.p, P, 1, 0));
     THC_TRY(mm(P, P, v, tr(yv, P), rm(A6.p, P), C6.p, P, 1, 0, o, 0, (long long)v * P, PP));
@@ -413,6 +456,7 @@ Err Engine<T>::alg6(T* sgm) {
     THC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(T) * P * PP, st));
     for (int I0 = 0; I0 < G; I0 += ic) {
         const int nI = std::min(ic, G - I0);
+        seg_begin(THC_STEP_ALG6_GEMM);
         // E^XY = sum_i C_i^XY x_i^I (line 8), F^XZ = sum_a D_a^XZ x_a^I (line 9)
         THC_TRY(mm(nI, (int)PP, o, View<T>{x.p + I0, 1, G}, rm(C6.p, PP), Ech.p, PP, 1, 0));
         THC_TRY(mm(nI, (int)PP, v, View<T>{x.p + (long long)o * G + I0, 1, G}, rm(D6.p, PP),
@@ -426,8 +470,12 @@ Err Engine<T>::alg6(T* sgm) {
             Gp = Gch.p;
         }
         // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
+        seg_begin(THC_STEP_TRIANGLE);
+        if (prof.on) prof.flops[THC_STEP_TRIANGLE] += 5.0 * nI * (double)P * P * P;
         THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st));
+        seg_end();
     }
+    seg_begin(THC_STEP_ALG6_POST);
     // I_ia = sum_YZ y_i^Z y_a^Y H^XYZ (line 14); sigma^XX' += sum_ia y_i^X' y_a^X' I_ia
     THC_TRY(mm(o, P, P, rm(yo, P), View<T>{H.p, 1, P}, M6.p, P, 1, 0, P, 0, PP,
                (long long)o * P));
@@ -443,6 +491,7 @@ Err Engine<T>::alg7(T* sgm) {
     const T* yv = y.p + (long long)o * P;
     const T* xo = x.p;
     const T* xv = x.p + (long long)o * G;
+    seg_begin(THC_STEP_ALG7);
     // R_ia^X = 2 sum_Y y_i^Y y_a^Y (S T)^XY + S_ia^X   (lines 3-8)
     THC_TRY(mm(P, (int)ov, P, rm(ST.p, P), tr(KRy.p, P), R7.p, ov, 2, 0));
     for (int X0 = 0; X0 < P; X0 += xb) {
@@ -502,15 +551,19 @@ Err Engine<T>::residual_dev(bool want_energy) {
         THC_CUDA(cudaMemsetAsync(b->p, 0, b->n * sizeof(T), st));
 
     // Dressed core Hamiltonian (one "vector" of the dressing routine).
+    seg_begin(THC_STEP_DRESS);
     THC_TRY(dress(hoo.p, hov.p, hvv.p, 1, hh_oo.p, hh_vv.p, hh_vo.p));
 
     // ---- fused Cholesky-slab pass: Algs. 1, 2, 3, 8 and the Fock matrix
     for (int A0 = 0; A0 < K; A0 += kb) {
         const int nb = std::min(kb, K - A0);
         const T* Lov_s = Lov.p + A0 * ov;
+        seg_begin(THC_STEP_DRESS);
         THC_TRY(dress(Loo.p + A0 * oo2, Lov_s, Lvv.p + A0 * vv2, nb, Lh_oo.p, Lh_vv.p, Lh_vo.p));
+        seg_begin(THC_STEP_FOCK);
         THC_TRY(fock_slab(nb, true, Joo.p, Jov.p, Jvo.p, Jvv.p, Xoo.p, Xov.p, Xvo.p, Xvv.p,
                           Lh_oo.p, Lov_s, Lh_vo.p, Lh_vv.p));
+        seg_begin(THC_STEP_ALG1);
         // Alg. 1: Bbar^XY = sum_ik y_i^X l_ki y_k^Y, Btil^XY = sum_ac y_a^X l_ac y_c^Y,
         // C = v o Bbar - o o Btil, sigma += C T C^T.  Alg. 3: Ccross += Bbar o Btil.
         THC_TRY(mm(o, P, o, rm(Lh_oo.p, o), rm(yo, P), M1.p, P, 1, 0, nb, oo2, 0, (long long)o * P));
@@ -521,6 +574,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
         THC_TRY(mm(P * nb, P, P, rm(C1.p, P), rm(Tc.p, P), D1.p, P, 1, 0));
         THC_TRY(mm(P, P, nb * P, rm(D1.p, (long long)nb * P), tr(C1.p, (long long)nb * P), sgm,
                    P, 1, 1));
+        seg_begin(THC_STEP_ALG2_8);
         // Alg. 2 line 5: Abar^X = sum_ai y_a^X y_i^X l_ai
         THC_TRY(mm(v, P, o, rm(Lh_vo.p, o), rm(yo, P), M2.p, P, 1, 0, nb, ov, 0, (long long)v * P));
         THC_CUDA(diag_reduce(yv, M2.p, v, P, nb, Abar.p, K, A0, st));
@@ -535,6 +589,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
         THC_TRY(mm(o, v, o, tr(Lh_oo.p, o), rm(D8.p, v), sg1, v, -1, 1, nb, oo2, ov, 0, true));
     }
 
+    seg_begin(THC_STEP_POST);
     // Alg. 2 line 14: sigma += Abar Abar^T + Q Abar^T + Abar Q^T
     THC_CUDA(lincomb(Wq.p, (long long)P * K, 1, Abar.p, 1, Q.p, 0, (const T*)nullptr, st));
     THC_TRY(mm(P, P, K, rm(Wq.p, K), tr(Abar.p, K), sgm, P, 1, 1));
@@ -570,6 +625,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
     THC_TRY(alg6(sgm));
     THC_TRY(alg7(sgm));
 
+    seg_begin(THC_STEP_POST);
     if constexpr (!std::is_same<T, double>::value) {
         THC_CUDA(cudaMemsetAsync(sig.p, 0, sizeof(double) * PP, st));
         THC_CUDA(cudaMemsetAsync(sig1.p, 0, sizeof(double) * ov, st));
@@ -577,6 +633,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
         THC_CUDA(accumulate(sig1.p, sg1, ov, 1.0, st));
     }
     if (want_energy) THC_TRY(energy_dev());
+    seg_end();
     return Err{};
 }
 
@@ -584,6 +641,7 @@ template <typename T>
 Err Engine<T>::energy_dev() {
     const long long PP = (long long)P * P, ov = (long long)o * v, oo2 = (long long)o * o;
     // doubles: <Zc, Wen>;  singles: sum_A [2 (L_A . t1)^2 - tr((L_A t1^T)^2)]
+    seg_begin(THC_STEP_ENERGY);
     THC_CUDA(dot(Tcd.p, Wen.p, PP, red.p, en.p, st));
     THC_TRY(mm(o, o, v, rm(Lov.p, v), tr(t1.p, v), Mo.p, o, 1, 0, K, ov, 0, oo2));
     THC_CUDA(singles_energy(Lov.p, Mo.p, t1.p, K, o, v, red.p, en.p + 1, st));
@@ -595,6 +653,7 @@ Err Engine<T>::residual(const double* Zc, const double* t1in, double* sigmaZ,
                         double* sigma1, double* energy_out) {
     THC_TRY(set_state(Zc, t1in));
     THC_TRY(residual_dev(energy_out != nullptr));
+    THC_TRY(prof_collect());
     const long long PP = (long long)P * P, ov = (long long)o * v;
     THC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
     THC_CUDA(any_nonfinite(sig.p, PP, flag.p, st));

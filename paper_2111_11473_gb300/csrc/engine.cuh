@@ -27,6 +27,37 @@ struct DBuf {
     DBuf& operator=(const DBuf&) = delete;
 };
 
+long long launches();
+
+// Per-step device timing with CUDA events on the engine's stream.
+struct Profiler {
+    bool on = false;
+    int cur = -1;
+    double ms[THC_N_STEPS] = {};
+    double flops[THC_N_STEPS] = {};
+    long long launches[THC_N_STEPS] = {};
+    long long residuals = 0;
+    long long launch_base = 0, kernel_launches = 0;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<int, int>>> marks;   // (step, (ev0, ev1))
+    int used = 0;
+    cudaEvent_t next_event() {
+        if (used == (int)pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void reset() {
+        for (int i = 0; i < THC_N_STEPS; ++i) ms[i] = flops[i] = 0, launches[i] = 0;
+        residuals = 0;
+        launch_base = thc::launches();
+        kernel_launches = 0;
+    }
+    ~Profiler() { for (auto e : pool) cudaEventDestroy(e); }
+};
+
 // Matrix-product policy: which kernel family runs the contractions.
 enum class MMKind { SIMT, TC_BF16X3 };
 
@@ -38,6 +69,11 @@ struct Engine {
     MMKind mm_kind = MMKind::SIMT;
     cudaStream_t st = nullptr;
     size_t bytes = 0;
+    Profiler prof;
+    // Open / close a timed segment of step `step` (no-ops when profiling is off).
+    void seg_begin(int step);
+    void seg_end();
+    Err prof_collect();
 
     // Fixed data (storage type T unless noted).
     DBuf<T> y, x, z;                        // n x P, n x G, G x G

@@ -7,9 +7,18 @@
 // register tile per thread, double-buffered shared memory.
 #include <algorithm>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace thc {
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+long long launches() { return g_launches.load(); }
+void count_launches(int n) { g_launches += n; }
+
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
@@ -193,6 +202,7 @@ cudaError_t launch(Gemm<T> g, cudaStream_t s) {
     dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), (g.reduce ? 1 : g.batch) * splits);
     if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidValue;
     gemm_kernel<T><<<grid, NT, 0, s>>>(g);
+    count_launches(splits > 1 ? 2 : 1);
     if (splits > 1) {
         long long total = (long long)g.M * g.N * (g.reduce ? 1 : g.batch);
         unsigned nbk = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 32);

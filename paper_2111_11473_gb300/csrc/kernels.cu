@@ -325,6 +325,7 @@ cudaError_t split_blocks(const T* full, int nb, int o, int v, Blocks<T> out,
                          cudaStream_t s) {
     long long n = (long long)nb * (o + v) * (o + v);
     k_split<T><<<nblocks(n), NT, 0, s>>>(full, nb, o, v, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -333,18 +334,21 @@ cudaError_t transpose_batched(const T* in, T* out, int nb, int rows, int cols,
                               cudaStream_t s) {
     dim3 grid(cdiv(cols, 32), cdiv(rows, 32), nb);
     k_transpose<T><<<grid, dim3(32, 8), 0, s>>>(in, out, nb, rows, cols);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t convert(const double* in, T* out, long long n, cudaStream_t s) {
     k_convert<T><<<nblocks(n), NT, 0, s>>>(in, out, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t to_double(const T* in, double* out, long long n, cudaStream_t s) {
     k_to_double<T><<<nblocks(n), NT, 0, s>>>(in, out, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -352,6 +356,7 @@ template <typename T>
 cudaError_t alg1_combine(const T* Bbar, const T* Btil, const T* oo, const T* vv,
                          T* C1, T* Ccross, int P, int nb, cudaStream_t s) {
     k_alg1<T><<<nblocks((long long)P * P), NT, 0, s>>>(Bbar, Btil, oo, vv, C1, Ccross, P, nb);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -359,6 +364,7 @@ template <typename T>
 cudaError_t diag_reduce(const T* y, const T* M, int R, int P, int nb, T* out, int ldo,
                         int col0, cudaStream_t s) {
     k_diag_reduce<T><<<nblocks((long long)nb * P), NT, 0, s>>>(y, M, R, P, nb, out, ldo, col0);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -366,12 +372,14 @@ template <typename T>
 cudaError_t w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P, int nb,
                      cudaStream_t s) {
     k_w_single<T><<<nblocks((long long)nb * P * P), NT, 0, s>>>(TA, ldta, Tc, E, W, P, nb);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s) {
     k_traces<T><<<cdiv(nb, 128), 128, 0, s>>>(M, n, nb, d);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -379,6 +387,7 @@ template <typename T>
 cudaError_t lincomb(T* out, long long n, double a, const T* x, double b, const T* y,
                     double c, const T* z, cudaStream_t s) {
     k_lincomb<T><<<nblocks(n), NT, 0, s>>>(out, n, a, x, b, y, c, z);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -386,12 +395,14 @@ template <typename T>
 cudaError_t hadamard2(T* out, long long n, const T* a, const T* b, const T* c,
                       const T* d, cudaStream_t s) {
     k_hadamard2<T><<<nblocks(n), NT, 0, s>>>(out, n, a, b, c, d);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t hadamard_batched(T* M, const T* z, long long per, int nb, cudaStream_t s) {
     k_hadamard_batched<T><<<nblocks(per * nb), NT, 0, s>>>(M, z, per, nb);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -399,6 +410,7 @@ template <typename T>
 cudaError_t khatri_rao(const T* A, const T* B, int na, int nbr, int P, T* out,
                        cudaStream_t s) {
     k_kr<T><<<nblocks((long long)na * nbr * P), NT, 0, s>>>(A, B, na, nbr, P, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -406,6 +418,7 @@ template <typename T>
 cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* out,
                        cudaStream_t s) {
     k_scale_rows<T><<<nblocks((long long)R * P * nx), NT, 0, s>>>(y, R, P, w, x0, nx, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -414,6 +427,7 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
                      cudaStream_t s) {
     dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
     k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -421,6 +435,7 @@ template <typename T>
 cudaError_t dot(const T* a, const T* b, long long n, double* scratch, double* out,
                 cudaStream_t s) {
     k_dot_part<T><<<NPART, NT, 0, s>>>(a, b, n, scratch);
+    count_launches(1);
     k_sum_parts<<<1, NT, 0, s>>>(scratch, NPART, out);
     return cudaGetLastError();
 }
@@ -429,12 +444,14 @@ template <typename T>
 cudaError_t singles_energy(const T* Lov, const T* Mo, const T* t1, int K, int o, int v,
                            double* scratch, double* out, cudaStream_t s) {
     k_singles_energy<T><<<K, NT, 0, s>>>(Lov, Mo, t1, o, v, scratch);
+    count_launches(1);
     k_sum_parts<<<1, NT, 0, s>>>(scratch, K, out);
     return cudaGetLastError();
 }
 
 cudaError_t any_nonfinite(const double* a, long long n, int* flag, cudaStream_t s) {
     k_nonfinite<<<nblocks(n), NT, 0, s>>>(a, n, flag);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -442,6 +459,7 @@ template <typename T>
 cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
                        cudaStream_t s) {
     k_accumulate<T><<<nblocks(n), NT, 0, s>>>(acc, part, n, scale);
+    count_launches(1);
     return cudaGetLastError();
 }
 

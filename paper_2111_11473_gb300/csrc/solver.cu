@@ -229,6 +229,7 @@ Err Solver::setup(Engine<T>& eng, double cutoff) {
     THC_TRY(yo_e.alloc((size_t)o * P));
     THC_TRY(yv_e.alloc((size_t)v * P));
     k_scale_diag<<<nb((long long)o * P), 256, 0, st>>>(yo, epsd.p, o, P, yo_e.p);
+    count_launches(1);
     k_scale_diag<<<nb((long long)v * P), 256, 0, st>>>(yv, epsd.p + o, v, P, yv_e.p);
     THC_CUDA(cudaGetLastError());
     for (DBuf<double>* b : {&oo, &vv, &oe, &ve, &F}) THC_TRY(b->alloc(PP));
@@ -238,8 +239,10 @@ Err Solver::setup(Engine<T>& eng, double cutoff) {
     THC_TRY(mm(st, P, P, o, tr64(yo, P), rm64(yo_e.p, P), oe.p, P, 1, 0));
     THC_TRY(mm(st, P, P, v, tr64(yv, P), rm64(yv_e.p, P), ve.p, P, 1, 0));
     k_metric<<<nb(PP), 256, 0, st>>>(oo.p, vv.p, oe.p, ve.p, Sd.p, F.p, PP);
+    count_launches(1);
     THC_CUDA(cudaGetLastError());
     k_symmetrize<<<nb(PP), 256, 0, st>>>(F.p, P);
+    count_launches(1);
     // S = V diag(s) V^T
     THC_TRY(Wm.alloc(PP));
     THC_TRY(sv.alloc(P));
@@ -255,6 +258,7 @@ Err Solver::setup(Engine<T>& eng, double cutoff) {
     DBuf<double> X, M, tmpPr;
     THC_TRY(X.alloc((size_t)P * r));
     k_half_inverse<<<nb((long long)P * r), 256, 0, st>>>(Wm.p, sv.p, P, k0, r, X.p);
+    count_launches(1);
     THC_CUDA(cudaGetLastError());
     // M = X^T F X, eigenvectors W:  C = X W
     THC_TRY(tmpPr.alloc((size_t)P * r));
@@ -262,11 +266,13 @@ Err Solver::setup(Engine<T>& eng, double cutoff) {
     THC_TRY(mm(st, P, r, P, rm64(F.p, P), rm64(X.p, r), tmpPr.p, r, 1, 0));
     THC_TRY(mm(st, r, r, P, tr64(X.p, r), rm64(tmpPr.p, r), M.p, r, 1, 0));
     k_symmetrize<<<nb((long long)r * r), 256, 0, st>>>(M.p, r);
+    count_launches(1);
     THC_TRY(e.alloc(r));
     THC_TRY(syevd(st, M.p, r, e.p));
     DBuf<double> W;
     THC_TRY(W.alloc((size_t)r * r));
     k_colmajor_to_rowmajor<<<nb((long long)r * r), 256, 0, st>>>(M.p, r, W.p);
+    count_launches(1);
     THC_TRY(C.alloc((size_t)P * r));
     THC_TRY(mm(st, P, r, r, rm64(X.p, r), rm64(W.p, r), C.p, r, 1, 0));
     THC_TRY(SC.alloc((size_t)P * r));
@@ -305,6 +311,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     THC_TRY(mm(st, P, r, P, rm64(Zc.p, P), rm64(SC.p, r), tmp.p, r, 1, 0));
     THC_TRY(mm(st, r, r, P, tr64(SC.p, r), rm64(tmp.p, r), x.p + ov, r, 1, 0));
     k_symmetrize<<<nb(rr), 256, 0, st>>>(x.p + ov, r);
+    count_launches(1);
     double energy = 0, norm = 0, e_prev = 0;
     bool converged = false;
     int it = 0;
@@ -314,13 +321,16 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         THC_TRY(mm(st, P, r, r, rm64(C.p, r), rm64(x.p + ov, r), tmp.p, r, 1, 0));
         THC_TRY(mm(st, P, P, r, rm64(tmp.p, r), tr64(C.p, r), Zc.p, P, 1, 0));
         k_symmetrize<<<nb(PP), 256, 0, st>>>(Zc.p, P);
+        count_launches(1);
         THC_CUDA(cudaGetLastError());
         THC_TRY(eng.set_state(Zc.p, x.p));
         THC_TRY(eng.residual_dev(true));
+        THC_TRY(eng.prof_collect());
         // sigma_q = C^T sigma C
         THC_TRY(mm(st, P, r, P, rm64(eng.sig.p, P), rm64(C.p, r), tmp.p, r, 1, 0));
         THC_TRY(mm(st, r, r, P, tr64(C.p, r), rm64(tmp.p, r), sq.p, r, 1, 0));
         k_multidot<<<1, 256, 0, st>>>(eng.sig1.p, eng.sig1.p, ov, dots.p);
+        count_launches(1);
         k_multidot<<<1, 256, 0, st>>>(sq.p, sq.p, rr, dots.p + 1);
         THC_CUDA(cudaGetLastError());
         double h[4];
@@ -331,6 +341,12 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         energy = h[2] + h[3];
         if (!std::isfinite(norm) || !std::isfinite(energy))
             return Err{THC_ERR_NUMERIC, "solver diverged (non-finite residual)"};
+        if (opts.history) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            opts.history[3 * (it - 1) + 0] = energy;
+            opts.history[3 * (it - 1) + 1] = norm;
+            opts.history[3 * (it - 1) + 2] = el;
+        }
         if (opts.verbose)
             fprintf(stderr, "thc_solve it %3d  E = %.12f  |r| = %.3e\n", it, energy, norm);
         const bool de_ok = opts.e_tol <= 0 || (it > 1 && std::fabs(energy - e_prev) < opts.e_tol);
@@ -341,6 +357,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         }
         k_jacobi<<<nb(len), 256, 0, st>>>(eng.sig1.p, sq.p, epsd.p, e.p, o, v, r, x.p,
                                            step.p, xnew.p);
+        count_launches(1);
         THC_CUDA(cudaGetLastError());
         if (m > 0) {
             const int slot = head;
@@ -351,6 +368,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             THC_CUDA(cudaMemcpyAsync(he.p + (long long)slot * len, step.p, sizeof(double) * len,
                                      cudaMemcpyDeviceToDevice, st));
             k_multidot<<<m, 256, 0, st>>>(he.p, step.p, len, dots.p);
+            count_launches(1);
             THC_CUDA(cudaGetLastError());
             std::vector<double> row(m);
             THC_CUDA(cudaMemcpyAsync(row.data(), dots.p, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
@@ -367,6 +385,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
                 THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
                                          cudaMemcpyHostToDevice, st));
                 k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
+                count_launches(1);
                 THC_CUDA(cudaGetLastError());
             } else {
                 THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));

@@ -25,8 +25,9 @@ def lib():
 
 def test_header_declares_the_abi():
     assert _declared() == ["thc_config_default", "thc_destroy", "thc_energy", "thc_init",
-                           "thc_last_error", "thc_residual", "thc_solve",
-                           "thc_solve_opts_default"]
+                           "thc_last_error", "thc_profile_enable", "thc_profile_read",
+                           "thc_residual", "thc_solve", "thc_solve_opts_default",
+                           "thc_step_name"]
 
 
 def test_library_exports_every_declared_symbol(lib):
