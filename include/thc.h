@@ -196,9 +196,43 @@ thc_status thc_profile_read(thc_ctx* ctx, thc_profile* out);
 /* Name of a step ("dress", "fock", ...), or NULL if out of range. */
 const char* thc_step_name(int step);
 
+/*
+ * thc_energy_noalloc - the CCSD energy of thc_energy, for callers that may
+ * not allocate device memory.  No counterpart in the paper.
+ *
+ * Some callers cannot call cudaMalloc: a process whose device memory is
+ * already reserved by another runtime's pool (a framework's caching
+ * allocator holding nearly all of HBM), or a latency-critical loop that
+ * must not take an allocation's cost or its risk of failing.  This entry
+ * point allocates nothing and needs no context: the caller passes device
+ * inputs and an output, and the scratch is a fixed, file-scope device array
+ * of THC_NOALLOC_SCRATCH doubles (16 MiB) that every GPU which loads the
+ * library holds until the process exits.
+ *
+ *   Y       n x P  device, amplitude collocation factors (occupied rows first)
+ *   Lov     K x o x v  device, occupied-virtual blocks of the Cholesky vectors
+ *   Zc      P x P  device, THC core;  t1  o x v  device, singles
+ *   energy  host or device scalar, output
+ *   stream  cudaStream_t or NULL
+ *
+ * Needs o*P + P*P + P + o*o + K + 1 <= THC_NOALLOC_SCRATCH; larger sizes
+ * return THC_ERR_ARG with the reason in thc_last_error(NULL).  The first call
+ * on a device looks up the scratch array's device address (with that device
+ * current), so make it before any stream capture.  Every call on a device
+ * shares the one array and leaves its contents behind: calls whose work
+ * overlaps on the GPU (other streams, other threads) race, so serialise them.
+ * Synchronous on `stream`.  Agrees with thc_energy to rounding.
+ */
+#define THC_NOALLOC_SCRATCH (1 << 21)
+thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
+                              const double* Y, const double* Lov,
+                              const double* Zc, const double* t1,
+                              double* energy, void* stream);
+
 /* Text of the first error recorded on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx or thc_destroy.  ctx may be NULL, which
- * returns the last error of a failed thc_init on this thread. */
+ * returns the last error of a failed thc_init or thc_energy_noalloc on this
+ * thread. */
 const char* thc_last_error(const thc_ctx* ctx);
 
 /* Release every device buffer of ctx.  NULL is accepted. */

@@ -79,6 +79,8 @@ _SIGNATURES = {
     "thc_profile_enable": (C.c_int, [_VP, C.c_int]),
     "thc_profile_read": (C.c_int, [_VP, C.POINTER(ThcProfile)]),
     "thc_step_name": (C.c_char_p, [C.c_int]),
+    "thc_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP,
+                                     _DP, _DP, _VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }

@@ -39,6 +39,10 @@ thc::Err check_config(const thc_config* cfg) {
 
 }  // namespace
 
+namespace thc {
+void set_thread_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace thc
+
 extern "C" {
 
 thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p, int n_g,

@@ -24,7 +24,8 @@ def lib():
 
 
 def test_header_declares_the_abi():
-    assert _declared() == ["thc_config_default", "thc_destroy", "thc_energy", "thc_init",
+    assert _declared() == ["thc_config_default", "thc_destroy", "thc_energy",
+                           "thc_energy_noalloc", "thc_init",
                            "thc_last_error", "thc_profile_enable", "thc_profile_read",
                            "thc_residual", "thc_solve", "thc_solve_opts_default",
                            "thc_step_name"]
