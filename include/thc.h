@@ -68,6 +68,9 @@ typedef struct {
     int x_block;             /* amplitude-THC columns per Alg. 7 block, 0 = auto */
     size_t workspace_bytes;  /* device workspace limit, 0 = auto */
     double lsq_rel_cutoff;   /* drop metric eigenvalues below cutoff*max (1e-10) */
+    int tc_products;         /* MIXED only: tensor-core products per contraction,
+                                3 = bf16 hi*hi + hi*lo + lo*hi (default),
+                                1 = bf16 hi*hi, 0 = float32 CUDA cores */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */

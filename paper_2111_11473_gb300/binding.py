@@ -22,7 +22,8 @@ class ThcConfig(C.Structure):
     _fields_ = [("n_occ", C.c_int), ("n_vir", C.c_int), ("n_p", C.c_int),
                 ("n_g", C.c_int), ("n_k", C.c_int), ("precision", C.c_int),
                 ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
-                ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double)]
+                ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double),
+                ("tc_products", C.c_int)]
 
 
 class ThcSolveOpts(C.Structure):
@@ -144,7 +145,8 @@ class Context:
     """One THC-RR-CCSD system resident on the GPU (wraps thc_ctx*)."""
 
     def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
-                 k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10):
+                 k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10,
+                 tc_products=3):
         lib = load_library()
         o, v = len(eps_o), len(eps_v)
         n = o + v
@@ -159,6 +161,7 @@ class Context:
         cfg.k_slab, cfg.i_chunk, cfg.x_block = k_slab, i_chunk, x_block
         cfg.workspace_bytes = workspace_bytes
         cfg.lsq_rel_cutoff = lsq_rel_cutoff
+        cfg.tc_products = tc_products
         args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)), _Arg(L, (K, n, n)),
                 _Arg(x, (n, G)), _Arg(z, (G, G))]
         handle = _VP()

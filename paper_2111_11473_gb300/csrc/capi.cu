@@ -34,6 +34,8 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "unknown precision policy"};
     if (cfg->k_slab < 0 || cfg->i_chunk < 0 || cfg->x_block < 0)
         return {THC_ERR_ARG, "blocking sizes must be >= 0"};
+    if (cfg->tc_products != 0 && cfg->tc_products != 1 && cfg->tc_products != 3)
+        return {THC_ERR_ARG, "tc_products must be 0, 1 or 3"};
     return {};
 }
 
@@ -56,6 +58,7 @@ thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p, in
     cfg->n_k = n_k;
     cfg->precision = THC_PREC_FP64;
     cfg->lsq_rel_cutoff = 1e-10;
+    cfg->tc_products = 3;
     return check_config(cfg).code;
 }
 

@@ -59,6 +59,19 @@ __global__ void k_asym(const double* a, int n, unsigned long long* out) {
 }  // namespace
 
 template <typename T>
+Err Engine<T>::check_timeout() {
+    if (!tcerr.p) return Err{};
+    int h = 0;
+    THC_CUDA(cudaMemcpyAsync(&h, tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
+        return Err{THC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait expired"};
+    }
+    return Err{};
+}
+
+template <typename T>
 Err Engine<T>::check_sym(const double* a, int nn_, double rel, const char* what) {
     unsigned long long h[3];
     THC_CUDA(cudaMemsetAsync(chk.p, 0, 3 * sizeof(unsigned long long), st));
@@ -140,7 +153,17 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     g.C = C; g.ldc = ldc; g.sCb = sCb;
     g.alpha = alpha; g.beta = beta; g.reduce = reduce;
     g.ws = splitk.p; g.ws_elems = splitk.n;
-    if (prof.on && prof.cur >= 0) prof.flops[prof.cur] += 2.0 * M * N * (double)Kd * batch;
+    const double fl = 2.0 * M * N * (double)Kd * batch;
+    if (prof.on && prof.cur >= 0) prof.flops[prof.cur] += fl;
+    if constexpr (std::is_same<T, float>::value) {
+        // Large products go to the tensor cores; the rest stays on the CUDA
+        // cores (also if the packed operands do not fit the workspace).
+        if (tc_products > 0 && fl >= 3.0e7 && Kd >= 16) {
+            cudaError_t e = gemm_tc(g, tcws, tc_products, st);
+            if (e == cudaSuccess) return Err{};
+            if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
+        }
+    }
     THC_CUDA(gemm_simt(g, st));
     return Err{};
 }
@@ -211,7 +234,12 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     st = s;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
     kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, K) : std::min(K, 64);
-    ic = cfg.i_chunk > 0 ? std::min(cfg.i_chunk, G) : std::min(G, 64);
+    // Alg. 6 grid chunk: as many grid points as 4 GB of E/F chunk buffers hold,
+    // so that H is read and written once per chunk.
+    ic = cfg.i_chunk > 0
+             ? std::min(cfg.i_chunk, G)
+             : (int)std::max<long long>(1, std::min<long long>(
+                   G, (4LL << 30) / (2LL * P * P * (long long)sizeof(T))));
     xb = cfg.x_block > 0 ? std::min(cfg.x_block, P) : std::min(P, 32);
     const long long ov = (long long)o * v, PP = (long long)P * P, nn = (long long)n * n;
 
@@ -407,6 +435,33 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(E7.alloc((size_t)xb * G * G));
     THC_TRY(P7.alloc((size_t)xb * o * G));
     THC_TRY(G7.alloc((size_t)xb * ov));
+    if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
+        // Packed-operand workspace: the largest product of the residual.
+        struct Shape { long long M, N, K, b; };
+        const long long PP2 = (long long)P * P;
+        const Shape shapes[] = {
+            {P, P, (long long)kb * P, 1}, {(long long)P * kb, P, P, 1}, {P, P, o, kb},
+            {P, P, v, kb}, {v, P, v, kb}, {o, G, v, xb}, {G, G, o, xb}, {o, G, G, xb},
+            {o, v, G, xb}, {xb, P, ov, 1}, {P, G, ov, 1}, {P, G, G, 1}, {P, P, G, 1},
+            {P, ov, P, 1}, {o, P, P, xb}, {o, v, P, xb}, {ov, P, P, 1}, {P, P, v, o},
+            {P, P, o, v}, {ic, PP2, o, 1}, {ic, PP2, v, 1}, {o, P, P, P}, {o, v, P, P},
+            {P, P, ov, 1}, {P, P, K, 1}};
+        size_t need = 0;
+        for (const Shape& sh : shapes)
+            need = std::max(need, gemm_tc_pack_elems((int)std::min<long long>(sh.M, INT32_MAX),
+                                                     (int)std::min<long long>(sh.N, INT32_MAX),
+                                                     (int)sh.K, (int)sh.b, false));
+        tc_products = cfg.tc_products;
+        THC_TRY(tcpack.alloc(need));
+        THC_TRY(tcpart.alloc((size_t)std::max<long long>(8 * PP, 1 << 22)));
+        THC_TRY(tcerr.alloc(1));
+        THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
+        tcws.buf = tcpack.p;
+        tcws.elems = tcpack.n;
+        tcws.partial = tcpart.p;
+        tcws.partial_elems = tcpart.n;
+        tcws.err = tcerr.p;
+    }
     THC_CUDA(cudaStreamSynchronize(st));
     return Err{};
 }
@@ -654,6 +709,7 @@ Err Engine<T>::residual(const double* Zc, const double* t1in, double* sigmaZ,
     THC_TRY(set_state(Zc, t1in));
     THC_TRY(residual_dev(energy_out != nullptr));
     THC_TRY(prof_collect());
+    THC_TRY(check_timeout());
     const long long PP = (long long)P * P, ov = (long long)o * v;
     THC_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
     THC_CUDA(any_nonfinite(sig.p, PP, flag.p, st));

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gemm_tc.cuh"
 #include "kernels.cuh"
 
 namespace thc {
@@ -94,6 +95,12 @@ struct Engine {
     DBuf<double> sig, sig1, en;             // P x P, o x v, energy scalars
     DBuf<T> sigT, sig1T;                    // partial sums in T (float engine)
     DBuf<T> splitk;                         // split-K partials of the GEMMs
+    int tc_products = 0;                    // tensor-core products (float engine)
+    DBuf<__nv_bfloat16> tcpack;             // packed bf16 hi/lo operands
+    DBuf<float> tcpart;                     // tensor-core split-K partials
+    DBuf<int> tcerr;                        // bounded-wait expiry flag
+    TcWorkspace tcws;
+    Err check_timeout();
     std::vector<double> eps_h;              // orbital energies (host copy)
     DBuf<T> xoo, xvv, Ccross, Abar, Q;      // o x o, v x v, P x P, P x K, P x K
     DBuf<T> Joo, Jov, Jvo, Jvv, Xoo, Xov, Xvo, Xvv;  // Coulomb / exchange Fock parts

@@ -1,4 +1,6 @@
 // Element-wise, reduction and triangle kernels of the residual engine.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace thc {
@@ -255,6 +257,120 @@ __global__ void __launch_bounds__(256) k_triangle(T* H, const T* E, const T* F,
     }
 }
 
+// Float32 triangle kernel.  A block owns a 32 x 32 x 32 (X, Y, Z) tile of H;
+// lane = X, and the 16 warps form a 4 x 4 grid of 8 x 8 (Y, Z) register tiles.
+// Per grid point I the block stages E_I[X][Y-tile | Z-tile], F_I likewise and
+// G_I[Y-tile][Z-tile] in shared memory through a 3-stage cp.async pipeline.
+// Each thread issues 3 FMA-pipe instructions per (I, X, Y, Z); G is read by
+// warp-wide broadcast, E and F by conflict-free 128-bit loads (row pad 4).
+constexpr int TT = 32, TROW = 2 * TT + 4, TGROW = TT + 4, TSTAGES = 3;
+
+struct TriStage {
+    float e[TT][TROW];
+    float f[TT][TROW];
+    float g[TT][TGROW];
+};
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = ok ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+
+__device__ __forceinline__ void tri_load(TriStage& st, const float* E, const float* F,
+                                         const float* G, int I, int P, int X0, int Y0, int Z0) {
+    const long long PP = (long long)P * P;
+    const float* Ei = E + I * PP;
+    const float* Fi = F + I * PP;
+    const float* Gi = G + I * PP;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int e = t + 512 * k;
+        const int r = e >> 6, c = e & 63;
+        const int X = X0 + r;
+        const int col = c < TT ? Y0 + c : Z0 + (c - TT);
+        const bool ok = X < P && col < P;
+        const long long off = ok ? (long long)X * P + col : 0;
+        cp_async4(&st.e[r][c], Ei + off, ok);
+        cp_async4(&st.f[r][c], Fi + off, ok);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int e = t + 512 * k;
+        const int r = e >> 5, c = e & 31;
+        const bool ok = Y0 + r < P && Z0 + c < P;
+        const long long off = ok ? (long long)(Y0 + r) * P + Z0 + c : 0;
+        cp_async4(&st.g[r][c], Gi + off, ok);
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* E,
+                                                         const float* F, const float* G,
+                                                         int P, int nI) {
+    extern __shared__ __align__(16) unsigned char tri_smem[];
+    TriStage* st = reinterpret_cast<TriStage*>(tri_smem);
+    const int Z0 = blockIdx.x * TT, Y0 = blockIdx.y * TT, X0 = blockIdx.z * TT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wy = warp >> 2, wz = warp & 3;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    for (int s = 0; s < TSTAGES - 1; ++s) {
+        if (s < nI) tri_load(st[s], E, F, G, s, P, X0, Y0, Z0);
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    for (int I = 0; I < nI; ++I) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TSTAGES - 2));
+        __syncthreads();
+        const int nxt = I + TSTAGES - 1;
+        if (nxt < nI) tri_load(st[nxt % TSTAGES], E, F, G, nxt, P, X0, Y0, Z0);
+        asm volatile("cp.async.commit_group;\n" ::);
+        const TriStage& c = st[I % TSTAGES];
+        float ey[8], fy[8], ez[8], fz[8];
+        const float4* er = reinterpret_cast<const float4*>(&c.e[lane][0]);
+        const float4* fr = reinterpret_cast<const float4*>(&c.f[lane][0]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float4 a = er[wy * 2 + q], b = fr[wy * 2 + q];
+            float4 d = er[8 + wz * 2 + q], h = fr[8 + wz * 2 + q];
+            ey[4 * q] = a.x; ey[4 * q + 1] = a.y; ey[4 * q + 2] = a.z; ey[4 * q + 3] = a.w;
+            fy[4 * q] = b.x; fy[4 * q + 1] = b.y; fy[4 * q + 2] = b.z; fy[4 * q + 3] = b.w;
+            ez[4 * q] = d.x; ez[4 * q + 1] = d.y; ez[4 * q + 2] = d.z; ez[4 * q + 3] = d.w;
+            fz[4 * q] = h.x; fz[4 * q + 1] = h.y; fz[4 * q + 2] = h.z; fz[4 * q + 3] = h.w;
+        }
+#pragma unroll
+        for (int yy = 0; yy < 8; ++yy) {
+            const float4* gr = reinterpret_cast<const float4*>(&c.g[wy * 8 + yy][wz * 8]);
+            const float4 g0 = gr[0], g1 = gr[1];
+            const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int zz = 0; zz < 8; ++zz) {
+                float t = ey[yy] * fz[zz];
+                t = fmaf(ez[zz], fy[yy], t);
+                acc[yy][zz] = fmaf(t, g[zz], acc[yy][zz]);
+            }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    const int X = X0 + lane;
+    if (X >= P) return;
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        const int Y = Y0 + wy * 8 + yy;
+        if (Y >= P) continue;
+        float* h = H + ((long long)X * P + Y) * P;
+#pragma unroll
+        for (int zz = 0; zz < 8; ++zz) {
+            const int Z = Z0 + wz * 8 + zz;
+            if (Z < P) h[Z] += acc[yy][zz];
+        }
+    }
+}
+
 __device__ double block_sum(double v) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -425,6 +541,20 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* 
 template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
                      cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        static bool attr_set = false;
+        const int smem = (int)(TSTAGES * sizeof(TriStage));
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(k_triangle_f32,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(P, TT));
+        k_triangle_f32<<<grid, 512, smem, s>>>(H, E, F, G, P, nI);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
     k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
     count_launches(1);

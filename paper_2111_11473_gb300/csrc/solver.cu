@@ -326,6 +326,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         THC_TRY(eng.set_state(Zc.p, x.p));
         THC_TRY(eng.residual_dev(true));
         THC_TRY(eng.prof_collect());
+        THC_TRY(eng.check_timeout());
         // sigma_q = C^T sigma C
         THC_TRY(mm(st, P, r, P, rm64(eng.sig.p, P), rm64(C.p, r), tmp.p, r, 1, 0));
         THC_TRY(mm(st, r, r, P, tr64(C.p, r), rm64(tmp.p, r), sq.p, r, 1, 0));
