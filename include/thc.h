@@ -71,6 +71,12 @@ typedef struct {
     int tc_products;         /* MIXED only: tensor-core products per contraction,
                                 3 = bf16 hi*hi + hi*lo + lo*hi (default),
                                 1 = bf16 hi*hi, 0 = float32 CUDA cores */
+    int alg7_route;          /* exchange part of Alg. 7 (Eq. 37): 0 = automatic,
+                                1 = through the THC factors as printed (G x G
+                                intermediates per X), 2 = through the dense
+                                (ib|ja) matrix, (ov)^2 words, built once at init
+                                from the THC factors; automatic picks 2 when
+                                that matrix takes at most 16 GiB */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */

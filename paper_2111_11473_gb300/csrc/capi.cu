@@ -36,6 +36,8 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "blocking sizes must be >= 0"};
     if (cfg->tc_products != 0 && cfg->tc_products != 1 && cfg->tc_products != 3)
         return {THC_ERR_ARG, "tc_products must be 0, 1 or 3"};
+    if (cfg->alg7_route < 0 || cfg->alg7_route > 2)
+        return {THC_ERR_ARG, "alg7_route must be 0, 1 or 2"};
     return {};
 }
 

@@ -233,7 +233,16 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                     cudaStream_t s) {
     st = s;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
-    kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, K) : std::min(K, 64);
+    {
+        // Cholesky slab: as many vectors as 2 GiB of per-vector scratch holds
+        // (six P x P intermediates dominate), at least 16.
+        const long long per = 6LL * cfg.n_p * cfg.n_p + 2LL * cfg.n_vir * cfg.n_vir +
+                              8LL * (cfg.n_occ + cfg.n_vir) * cfg.n_p;
+        const long long fit = (2LL << 30) / (per * (long long)sizeof(T));
+        kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, cfg.n_k)
+                            : (int)std::max<long long>(1, std::min<long long>(
+                                  cfg.n_k, std::max<long long>(16, fit)));
+    }
     // Alg. 6 grid chunk: as many grid points as 4 GB of E/F chunk buffers hold,
     // so that H is read and written once per chunk.
     ic = cfg.i_chunk > 0
@@ -423,6 +432,20 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(H.alloc((size_t)P * PP));
     THC_TRY(M6.alloc((size_t)P * o * P));
     THC_TRY(I6.alloc((size_t)P * ov));
+    // ---- Alg. 7 exchange route.  Dense route: Kx[(ia),(jb)] = (ib|ja)
+    //      = sum_J B[(i,b),J] x_j^J x_a^J, one v x v block per (i, j).
+    {
+        const double kx_bytes = (double)ov * ov * sizeof(T);
+        alg7_dense = cfg.alg7_route == 2 ||
+                     (cfg.alg7_route == 0 && kx_bytes <= 16.0 * (1LL << 30));
+        if (alg7_dense) {
+            THC_TRY(Kx.alloc((size_t)ov * ov));
+            THC_TRY(W7.alloc((size_t)P * ov));
+            for (int i = 0; i < o; ++i)
+                THC_TRY(mm(v, v, G, rm(KRx.p, G), tr(B6.p + (long long)i * v * G, G),
+                           Kx.p + (long long)i * v * ov, ov, 1, 0, o, (long long)v * G, 0, v));
+        }
+    }
     // ---- Alg. 7 scratch
     THC_TRY(R7.alloc((size_t)P * ov));
     THC_TRY(S7.alloc((size_t)P * ov));
@@ -435,6 +458,8 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(E7.alloc((size_t)xb * G * G));
     THC_TRY(P7.alloc((size_t)xb * o * G));
     THC_TRY(G7.alloc((size_t)xb * ov));
+    THC_TRY(tcerr.alloc(1));
+    THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
     if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
         // Packed-operand workspace: the largest product of the residual.
         struct Shape { long long M, N, K, b; };
@@ -454,8 +479,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         tc_products = cfg.tc_products;
         THC_TRY(tcpack.alloc(need));
         THC_TRY(tcpart.alloc((size_t)std::max<long long>(8 * PP, 1 << 22)));
-        THC_TRY(tcerr.alloc(1));
-        THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
+
         tcws.buf = tcpack.p;
         tcws.elems = tcpack.n;
         tcws.partial = tcpart.p;
@@ -527,7 +551,7 @@ Err Engine<T>::alg6(T* sgm) {
         // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
         seg_begin(THC_STEP_TRIANGLE);
         if (prof.on) prof.flops[THC_STEP_TRIANGLE] += 5.0 * nI * (double)P * P * P;
-        THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st));
+        THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st, tcerr.p));
         seg_end();
     }
     seg_begin(THC_STEP_ALG6_POST);
@@ -563,6 +587,17 @@ Err Engine<T>::alg7(T* sgm) {
     THC_TRY(mm(P, G, (int)ov, rm(R7.p, ov), rm(KRx.p, G), C7.p, G, 1, 0));
     THC_TRY(mm(P, G, G, rm(C7.p, G), rm(z.p, G), D7.p, G, 1, 0));
     THC_TRY(mm(P, P, G, rm(C7.p, G), tr(D7.p, G), sgm, P, 1, 1));
+    if (alg7_dense) {
+        // Exchange parts through the dense (ib|ja): sigma -= 1/2 R Kx R^T,
+        // sigma += 1/2 S Kx S^T (the same sums as lines 12-22).
+        for (int pass = 0; pass < 2; ++pass) {
+            const T* src = pass == 0 ? R7.p : S7.p;
+            const double sign = pass == 0 ? -0.5 : 0.5;
+            THC_TRY(mm(P, (int)ov, (int)ov, rm(src, ov), rm(Kx.p, ov), W7.p, ov, 1, 0));
+            THC_TRY(mm(P, P, (int)ov, rm(W7.p, ov), tr(src, ov), sgm, P, sign, 1));
+        }
+        return Err{};
+    }
     // Exchange parts (lines 12-21), blocked over X
     for (int pass = 0; pass < 2; ++pass) {
         const T* src = pass == 0 ? R7.p : S7.p;

@@ -120,6 +120,9 @@ struct Engine {
     DBuf<T> A6, C6, D6, Ech, Fch, Gch, H, M6, I6;
     // Alg. 7 scratch.
     DBuf<T> R7, S7, C7, D7, Yv, M7, Yo, N7, E7, P7, G7;
+    bool alg7_dense = false;
+    DBuf<T> Kx;                             // (ov) x (ov): Kx[(ia),(jb)] = (ib|ja)
+    DBuf<T> W7;                             // P x (ov)
 
     Err init(const thc_config& cfg, const double* eps_o, const double* eps_v,
              const double* Y, const double* L, const double* xin, const double* zin,

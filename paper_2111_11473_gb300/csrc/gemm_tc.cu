@@ -124,6 +124,7 @@ struct TcArgs {
     long long crs, ccs, cbs;   // C(i, j) of batch b at C[b*cbs + i*crs + j*ccs]
     float alpha, beta;
     int nprod;
+    int a_bcast, b_bcast;  // operand shared by every batch: packed once, batch coord 0
     int* err;
 };
 
@@ -178,11 +179,12 @@ __global__ void __launch_bounds__(128, 1)
             if (sm.fail) break;
             const int kc = (k_lo + i) * BK;
             mbar_expect_tx(&sm.full[s], stage_bytes);
-            tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, m0, bo);
-            tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, n0, bo);
+            const int ba = args.a_bcast ? 0 : bo, bb = args.b_bcast ? 0 : bo;
+            tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, m0, ba);
+            tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, n0, bb);
             if (args.nprod == 3) {
-                tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, m0, bo);
-                tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, n0, bo);
+                tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, m0, ba);
+                tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, n0, bb);
             }
         }
     } else if (warp == 1 && lane == 0 && nk > 0) {
@@ -218,10 +220,15 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     const bool ok = sm.fail == 0;   // uniform across the block
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
+    // The operand ring is idle now (every load was consumed by an MMA that
+    // completed before `done`): stage the 128 x BN accumulator tile there and
+    // write it out along whichever index of C is contiguous.
+    float* stage = reinterpret_cast<float*>(&sm.a_hi[0][0]);
+    constexpr int LDS_ = BN + 1;
     float* Cb = args.C + (long long)bo * args.cbs +
                 (args.splits > 1 ? (long long)split * args.nbo * args.cbs : 0);
     if (ok) {
+        const int rl = warp * 32 + lane;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];
@@ -239,16 +246,28 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) r[j] = 0u;
             }
-            if (row < args.M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= args.N) continue;
-                    float* c = Cb + (long long)row * args.crs + (long long)col * args.ccs;
-                    const float v = __uint_as_float(r[j]);
-                    if (args.splits > 1) *c = v;
-                    else *c = args.beta != 0.f ? fmaf(args.beta, *c, args.alpha * v) : args.alpha * v;
-                }
+            for (int j = 0; j < 16; ++j) stage[rl * LDS_ + c0 + j] = __uint_as_float(r[j]);
+        }
+    }
+    __syncthreads();
+    if (ok) {
+        auto put = [&](int i, int j, float v) {
+            float* c = Cb + (long long)(m0 + i) * args.crs + (long long)(n0 + j) * args.ccs;
+            if (args.splits > 1) *c = v;
+            else *c = args.beta != 0.f ? fmaf(args.beta, *c, args.alpha * v) : args.alpha * v;
+        };
+        if (args.ccs == 1) {
+            for (int i = warp; i < BM; i += 4) {
+                if (m0 + i >= args.M) break;
+                for (int j = lane; j < BN; j += 32)
+                    if (n0 + j < args.N) put(i, j, stage[i * LDS_ + j]);
+            }
+        } else {
+            for (int j = warp; j < BN; j += 4) {
+                if (n0 + j >= args.N) break;
+                for (int i = lane; i < BM; i += 32)
+                    if (m0 + i < args.M) put(i, j, stage[i * LDS_ + j]);
             }
         }
     }
@@ -268,28 +287,31 @@ __global__ void k_pack(const float* src, long long rs, long long ks, long long b
                        __nv_bfloat16* lo) {
     __shared__ float tile[32][33];
     const int b = blockIdx.z;
-    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int k0 = blockIdx.x * 32;
     const float* s = src + (long long)b * bs;
     const bool kfast = ks <= rs;
-    for (int j = threadIdx.y; j < 32; j += 8) {
-        int r, k;
-        if (kfast) { r = r0 + j; k = k0 + threadIdx.x; }
-        else       { r = r0 + threadIdx.x; k = k0 + j; }
-        const float v = (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.f;
-        if (kfast) tile[j][threadIdx.x] = v;
-        else tile[threadIdx.x][j] = v;
-    }
-    __syncthreads();
     const long long Ktot = reduce ? (long long)nb * Kp : Kp;
     const int bo = reduce ? 0 : b, kb = reduce ? b : 0;
-    for (int j = threadIdx.y; j < 32; j += 8) {
-        const int r = r0 + j, k = k0 + threadIdx.x;
-        if (r >= Rp || k >= Kp) continue;
-        const float v = tile[j][threadIdx.x];
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
-        hi[o] = h;
-        if (lo) lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+    for (int r0 = blockIdx.y * 32; r0 < Rp; r0 += gridDim.y * 32) {
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            int r, k;
+            if (kfast) { r = r0 + j; k = k0 + threadIdx.x; }
+            else       { r = r0 + threadIdx.x; k = k0 + j; }
+            const float v = (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.f;
+            if (kfast) tile[j][threadIdx.x] = v;
+            else tile[threadIdx.x][j] = v;
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int r = r0 + j, k = k0 + threadIdx.x;
+            if (r >= Rp || k >= Kp) continue;
+            const float v = tile[j][threadIdx.x];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
+            hi[o] = h;
+            if (lo) lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+        __syncthreads();
     }
 }
 
@@ -381,13 +403,6 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
     const int nbo = g.reduce ? 1 : nb;
     const long long Ktot = g.reduce ? Kp * nb : Kp;
     const long long RpA = rup(Mr, BM), RpB = rup(Nr, BN);
-    const size_t needA = (size_t)(RpA * Ktot * nbo), needB = (size_t)(RpB * Ktot * nbo);
-    const size_t need = (nprod == 3 ? 2 : 1) * (needA + needB);
-    if (need > ws.elems) return cudaErrorMemoryAllocation;
-    __nv_bfloat16* a_hi = ws.buf;
-    __nv_bfloat16* b_hi = a_hi + needA;
-    __nv_bfloat16* a_lo = nprod == 3 ? b_hi + needB : nullptr;
-    __nv_bfloat16* b_lo = nprod == 3 ? a_lo + needA : nullptr;
     // Operand views: UMMA-A rows r, K index k.
     // Unswapped: A side = A(m, k), B side = B(k, n) read as (n, k).
     View<float> va = g.A, vb{g.B.p, g.B.cs, g.B.rs};
@@ -396,9 +411,20 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
         std::swap(va, vb);
         std::swap(sa, sb);
     }
+    const bool a_bc = !g.reduce && nb > 1 && sa == 0;
+    const bool b_bc = !g.reduce && nb > 1 && sb == 0;
+    const int nba = a_bc ? 1 : nbo, nbb = b_bc ? 1 : nbo;
+    const size_t needA = (size_t)(RpA * Ktot * nba), needB = (size_t)(RpB * Ktot * nbb);
+    const size_t need = (nprod == 3 ? 2 : 1) * (needA + needB);
+    if (need > ws.elems) return cudaErrorMemoryAllocation;
+    __nv_bfloat16* a_hi = ws.buf;
+    __nv_bfloat16* b_hi = a_hi + needA;
+    __nv_bfloat16* a_lo = nprod == 3 ? b_hi + needB : nullptr;
+    __nv_bfloat16* b_lo = nprod == 3 ? a_lo + needA : nullptr;
     {
         dim3 blk(32, 8);
-        dim3 gA(cdiv(Kp, 32), cdiv(RpA, 32), nb), gB(cdiv(Kp, 32), cdiv(RpB, 32), nb);
+        dim3 gA(cdiv(Kp, 32), std::min<unsigned>(cdiv(RpA, 32), 65535), a_bc ? 1 : nb);
+        dim3 gB(cdiv(Kp, 32), std::min<unsigned>(cdiv(RpB, 32), 65535), b_bc ? 1 : nb);
         k_pack<<<gA, blk, 0, s>>>(va.p, va.rs, va.cs, sa, Mr, g.K, nb, (int)RpA, (int)Kp,
                                   g.reduce ? 1 : 0, a_hi, a_lo);
         k_pack<<<gB, blk, 0, s>>>(vb.p, vb.rs, vb.cs, sb, Nr, g.K, nb, (int)RpB, (int)Kp,
@@ -407,10 +433,10 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     CUtensorMap maps[4];
-    if ((e = make_map(&maps[0], a_hi, Ktot, RpA, nbo, BM)) != cudaSuccess) return e;
-    if ((e = make_map(&maps[1], nprod == 3 ? a_lo : a_hi, Ktot, RpA, nbo, BM)) != cudaSuccess) return e;
-    if ((e = make_map(&maps[2], b_hi, Ktot, RpB, nbo, BN)) != cudaSuccess) return e;
-    if ((e = make_map(&maps[3], nprod == 3 ? b_lo : b_hi, Ktot, RpB, nbo, BN)) != cudaSuccess) return e;
+    if ((e = make_map(&maps[0], a_hi, Ktot, RpA, nba, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&maps[1], nprod == 3 ? a_lo : a_hi, Ktot, RpA, nba, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&maps[2], b_hi, Ktot, RpB, nbb, BN)) != cudaSuccess) return e;
+    if ((e = make_map(&maps[3], nprod == 3 ? b_lo : b_hi, Ktot, RpB, nbb, BN)) != cudaSuccess) return e;
 
     TcArgs a{};
     a.M = Mr;
@@ -418,6 +444,8 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
     a.nbo = nbo;
     a.ksteps = (int)(Ktot / BK);
     a.nprod = nprod;
+    a.a_bcast = a_bc ? 1 : 0;
+    a.b_bcast = b_bc ? 1 : 0;
     a.err = ws.err;
     a.alpha = (float)g.alpha;
     a.beta = (float)g.beta;

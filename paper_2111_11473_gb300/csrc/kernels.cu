@@ -1,4 +1,8 @@
 // Element-wise, reduction and triangle kernels of the residual engine.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -371,6 +375,229 @@ __global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* 
     }
 }
 
+// TMA-fed float32 triangle kernel (P a multiple of 4, so that every row of
+// E, F and G starts on a 16-byte boundary).  Same 32^3 tile and 8 x 8 register
+// tile as k_triangle_f32; one thread issues five 3-D TMA box copies per stage
+// (E and F rows for the Y and Z ranges, the G tile) of TI grid points with
+// 128-byte swizzle, through a TSTG-deep mbarrier ring; each warp releases a
+// stage with one arrive.  Reads undo the swizzle: 16-byte chunk c of row r
+// sits at chunk c ^ (r & 7), which also makes the row-per-lane loads
+// conflict-free.  All waits are bounded by a clock64 budget.
+constexpr int TI = 2, TSTG = 4;
+constexpr long long kTriWait = 4000000000LL;
+
+struct TriTmaSmem {
+    float ey[TSTG][TI][TT * TT];
+    float ez[TSTG][TI][TT * TT];
+    float fy[TSTG][TI][TT * TT];
+    float fz[TSTG][TI][TT * TT];
+    float g[TSTG][TI][TT * TT];
+    unsigned long long full[TSTG];
+    unsigned long long empty[TSTG];
+    int fail;
+};
+
+__device__ __forceinline__ unsigned tri_su32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool tri_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = tri_su32(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity));
+        if (done) return true;
+        if (clock64() - t0 > kTriWait) return false;
+    }
+}
+
+__device__ __forceinline__ bool tri_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(tri_su32(bar)), "r"(parity));
+    return done != 0;
+}
+
+__device__ __forceinline__ void tri_tma(void* dst, const CUtensorMap* m, unsigned long long* bar,
+                                        int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tri_su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(tri_su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float4 tri_ld4(const float* tile, int r, int chunk) {
+    return *reinterpret_cast<const float4*>(tile + r * TT + ((chunk ^ (r & 7)) << 2));
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_triangle_f32_tma(float* H, const __grid_constant__ CUtensorMap tmE,
+                       const __grid_constant__ CUtensorMap tmF,
+                       const __grid_constant__ CUtensorMap tmG, int P, int nI, int* err) {
+    extern __shared__ __align__(1024) unsigned char tri_raw[];
+    TriTmaSmem& sm = *reinterpret_cast<TriTmaSmem*>(
+        (reinterpret_cast<uintptr_t>(tri_raw) + 1023) & ~uintptr_t(1023));
+    const int Z0 = blockIdx.x * TT, Y0 = blockIdx.y * TT, X0 = blockIdx.z * TT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // 8 warps: 4 (Y) x 2 (Z); a thread owns 8 Y x 16 Z of its lane's X.
+    const int wy = warp >> 1, wz = warp & 1;
+    const int nst = (nI + TI - 1) / TI;
+    const unsigned stage_bytes = 5u * TI * TT * TT * 4u;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TSTG; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tri_su32(&sm.full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(tri_su32(&sm.empty[s])));
+        }
+        sm.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int k) {
+        const int s = k % TSTG, I0 = k * TI;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                         tri_su32(&sm.full[s])),
+                     "r"(stage_bytes));
+        tri_tma(&sm.ey[s][0][0], &tmE, &sm.full[s], Y0, X0, I0);
+        tri_tma(&sm.ez[s][0][0], &tmE, &sm.full[s], Z0, X0, I0);
+        tri_tma(&sm.fy[s][0][0], &tmF, &sm.full[s], Y0, X0, I0);
+        tri_tma(&sm.fz[s][0][0], &tmF, &sm.full[s], Z0, X0, I0);
+        tri_tma(&sm.g[s][0][0], &tmG, &sm.full[s], Z0, Y0, I0);
+    };
+    int next = 0;   // next step to load (thread 0 only)
+    if (threadIdx.x == 0)
+        for (; next < TSTG - 1 && next < nst; ++next) issue(next);
+
+    float acc[8][16];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
+
+    for (int k = 0; k < nst; ++k) {
+        const int s = k % TSTG;
+        // Refill every stage whose consumers are done, without blocking, up
+        // to TSTG - 1 steps ahead; block (bounded) only if step k itself has
+        // not been issued yet.
+        if (threadIdx.x == 0) {
+            while (next < nst && next <= k + TSTG - 1) {
+                const bool need = next <= k;
+                if (next >= TSTG) {
+                    const unsigned par = ((next / TSTG) - 1) & 1;
+                    if (need) {
+                        if (!tri_wait(&sm.empty[next % TSTG], par)) {
+                            atomicExch(&sm.fail, 1);
+                            break;
+                        }
+                    } else if (!tri_test(&sm.empty[next % TSTG], par)) {
+                        break;
+                    }
+                }
+                issue(next);
+                ++next;
+            }
+        }
+        if (!tri_wait(&sm.full[s], (k / TSTG) & 1)) atomicExch(&sm.fail, 1);
+        if (*(volatile int*)&sm.fail) break;
+#pragma unroll 1
+        for (int ii = 0; ii < TI; ++ii) {
+            if (k * TI + ii >= nI) break;
+            const float* ey_t = sm.ey[s][ii];
+            const float* ez_t = sm.ez[s][ii];
+            const float* fy_t = sm.fy[s][ii];
+            const float* fz_t = sm.fz[s][ii];
+            const float* g_t = sm.g[s][ii];
+            float ez[16], fz[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 d = tri_ld4(ez_t, lane, wz * 4 + q);
+                const float4 h = tri_ld4(fz_t, lane, wz * 4 + q);
+                ez[4 * q] = d.x; ez[4 * q + 1] = d.y; ez[4 * q + 2] = d.z; ez[4 * q + 3] = d.w;
+                fz[4 * q] = h.x; fz[4 * q + 1] = h.y; fz[4 * q + 2] = h.z; fz[4 * q + 3] = h.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 a = tri_ld4(ey_t, lane, wy * 2 + q);
+                const float4 b = tri_ld4(fy_t, lane, wy * 2 + q);
+                const float ey4[4] = {a.x, a.y, a.z, a.w};
+                const float fy4[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int y4 = 0; y4 < 4; ++y4) {
+                    const int yy = q * 4 + y4;
+                    const int r = wy * 8 + yy;
+#pragma unroll
+                    for (int zq = 0; zq < 4; ++zq) {
+                        const float4 g4 = tri_ld4(g_t, r, wz * 4 + zq);
+                        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                        for (int z4 = 0; z4 < 4; ++z4) {
+                            const int zz = zq * 4 + z4;
+                            float t = ey4[y4] * fz[zz];
+                            t = fmaf(ez[zz], fy4[y4], t);
+                            acc[yy][zz] = fmaf(t, g[z4], acc[yy][zz]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tri_su32(&sm.empty[s]))
+                         : "memory");
+    }
+    __syncthreads();
+    if (*(volatile int*)&sm.fail) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        return;
+    }
+    const int X = X0 + lane;
+    if (X >= P) return;
+#pragma unroll
+    for (int yy = 0; yy < 8; ++yy) {
+        const int Y = Y0 + wy * 8 + yy;
+        if (Y >= P) continue;
+        float* h = H + ((long long)X * P + Y) * P;
+#pragma unroll
+        for (int zz = 0; zz < 16; ++zz) {
+            const int Z = Z0 + wz * 16 + zz;
+            if (Z < P) h[Z] += acc[yy][zz];
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_tri_encode = nullptr;
+std::once_flag g_tri_once;
+
+cudaError_t tri_map(CUtensorMap* m, const float* base, int P, int nI) {
+    std::call_once(g_tri_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_tri_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_tri_encode) return cudaErrorNotSupported;
+    cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)nI};
+    cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * P * 4};
+    cuuint32_t box[3] = {(cuuint32_t)TT, (cuuint32_t)TT, (cuuint32_t)TI};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_tri_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box,
+                              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 __device__ double block_sum(double v) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -540,8 +767,28 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* 
 
 template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
-                     cudaStream_t s) {
+                     cudaStream_t s, int* tri_err) {
     if constexpr (std::is_same<T, float>::value) {
+        if (P % 4 == 0 && ((uintptr_t)E % 16 == 0) && ((uintptr_t)F % 16 == 0) &&
+            ((uintptr_t)G % 16 == 0) && tri_err) {
+            CUtensorMap mE, mF, mG;
+            cudaError_t e = tri_map(&mE, E, P, nI);
+            if (e == cudaSuccess) e = tri_map(&mF, F, P, nI);
+            if (e == cudaSuccess) e = tri_map(&mG, G, P, nI);
+            if (e != cudaSuccess) return e;
+            static bool tma_attr = false;
+            const int smem = (int)sizeof(TriTmaSmem) + 1024;
+            if (!tma_attr) {
+                e = cudaFuncSetAttribute(k_triangle_f32_tma,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                if (e != cudaSuccess) return e;
+                tma_attr = true;
+            }
+            dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(P, TT));
+            k_triangle_f32_tma<<<grid, 256, smem, s>>>(H, mE, mF, mG, P, nI, tri_err);
+            count_launches(1);
+            return cudaGetLastError();
+        }
         static bool attr_set = false;
         const int smem = (int)(TSTAGES * sizeof(TriStage));
         if (!attr_set) {
@@ -614,7 +861,7 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
     template cudaError_t scale_rows<T>(const T*, int, int, const T*, int, int, T*,     \
                                        cudaStream_t);                                   \
     template cudaError_t triangle<T>(T*, const T*, const T*, const T*, int, int,       \
-                                     cudaStream_t);                                     \
+                                     cudaStream_t, int*);                               \
     template cudaError_t dot<T>(const T*, const T*, long long, double*, double*,       \
                                 cudaStream_t);                                          \
     template cudaError_t singles_energy<T>(const T*, const T*, const T*, int, int, int, \

@@ -71,9 +71,10 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx,
                        T* out, cudaStream_t s);
 
 // Alg. 6 line 11: H[X][Y][Z] += sum_I (E_I^XY F_I^XZ + E_I^XZ F_I^XY) G_I^YZ.
+// tri_err (device int, may be null) receives 1 if a bounded wait expired.
 template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
-                     cudaStream_t s);
+                     cudaStream_t s, int* tri_err = nullptr);
 
 // Deterministic float64 sums.
 // out[0] = sum_i a[i] b[i]

@@ -48,6 +48,18 @@ def test_mixed_matches_oracle_within_bound(case, tcp):
     assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))
 
 
+@pytest.mark.parametrize("route", [1, 2])
+def test_mixed_alg7_routes(route):
+    import paper_2111_11473_gb300 as pkg
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(8, 60, 120, 200, 80, 13)
+    with context(s, precision=pkg.THC_PREC_MIXED, alg7_route=route) as ctx:
+        sig, sig1, E = ctx.residual(Zc, t1)
+    scale = max(np.abs(sig_ref).max(), np.abs(r1_ref).max())
+    err = max(np.abs(sig - sig_ref).max(), np.abs(sig1 - r1_ref).max())
+    print(f"mixed alg7 route {route}: {err / scale:.2e}")
+    assert err < BOUND[3] * scale
+
+
 @pytest.mark.parametrize("tcp", [3, 0])
 def test_mixed_fullsize_error_against_fp64_gpu(tcp):
     import paper_2111_11473_gb300 as pkg

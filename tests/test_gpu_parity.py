@@ -110,3 +110,13 @@ def test_argument_and_numeric_errors():
     with pytest.raises(pkg.ThcError) as e:
         pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, zbad)
     assert e.value.name == "THC_ERR_ARG"
+
+
+@pytest.mark.parametrize("route", [1, 2])
+def test_alg7_routes_match_oracle(route):
+    """Alg. 7 through the THC factors (as printed) and through the dense (ib|ja)."""
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(7, 37, 70, 90, 45, 11)
+    with context(s, alg7_route=route, x_block=9) as ctx:
+        sig, sig1, E = ctx.residual(Zc, t1)
+    assert np.abs(sig - sig_ref).max() < RES_TOL
+    assert np.abs(sig1 - r1_ref).max() < RES_TOL
