@@ -440,6 +440,16 @@ __device__ __forceinline__ float4 tri_ld4(const float* tile, int r, int chunk) {
     return *reinterpret_cast<const float4*>(tile + r * TT + ((chunk ^ (r & 7)) << 2));
 }
 
+// Same load on a 32-bit shared-memory address (tile base in bytes).
+__device__ __forceinline__ float4 tri_lds4(unsigned tile, int r, int chunk) {
+    float4 v;
+    const unsigned a = tile + (unsigned)(r * TT * 4) + ((unsigned)(chunk ^ (r & 7)) << 4);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+
 __global__ void __launch_bounds__(256, 1)
     k_triangle_f32_tma(float* H, const __grid_constant__ CUtensorMap tmE,
                        const __grid_constant__ CUtensorMap tmF,
@@ -449,8 +459,10 @@ __global__ void __launch_bounds__(256, 1)
         (reinterpret_cast<uintptr_t>(tri_raw) + 1023) & ~uintptr_t(1023));
     const int Z0 = blockIdx.x * TT, Y0 = blockIdx.y * TT, X0 = blockIdx.z * TT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // 8 warps: 4 (Y) x 2 (Z); a thread owns 8 Y x 16 Z of its lane's X.
-    const int wy = warp >> 1, wz = warp & 1;
+    // 8 warps = 4 (Y, 8 each) x 2 (Z, 16 each).  Lane = (lx, lz): the thread
+    // owns X = lx + 8j (j < 4), Z = z_base + 4 lz + (0..3), Y = y_base + (0..7).
+    const int y_base = (warp >> 1) * 8, zc = (warp & 1) * 4 + (lane >> 3);
+    const int lx = lane & 7;
     const int nst = (nI + TI - 1) / TI;
     const unsigned stage_bytes = 5u * TI * TT * TT * 4u;
     if (threadIdx.x == 0) {
@@ -478,11 +490,13 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0)
         for (; next < TSTG - 1 && next < nst; ++next) issue(next);
 
-    float acc[8][16];
+    float acc[4][8][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[i][j] = 0.f;
+        for (int y = 0; y < 8; ++y)
+#pragma unroll
+            for (int z = 0; z < 4; ++z) acc[j][y][z] = 0.f;
 
     for (int k = 0; k < nst; ++k) {
         const int s = k % TSTG;
@@ -512,40 +526,29 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll 1
         for (int ii = 0; ii < TI; ++ii) {
             if (k * TI + ii >= nI) break;
-            const float* ey_t = sm.ey[s][ii];
-            const float* ez_t = sm.ez[s][ii];
-            const float* fy_t = sm.fy[s][ii];
-            const float* fz_t = sm.fz[s][ii];
-            const float* g_t = sm.g[s][ii];
-            float ez[16], fz[16];
+            // 32-bit shared addresses of this step's five tiles.
+            const unsigned ey_t = tri_su32(sm.ey[s][ii]), ez_t = tri_su32(sm.ez[s][ii]);
+            const unsigned fy_t = tri_su32(sm.fy[s][ii]), fz_t = tri_su32(sm.fz[s][ii]);
+            const unsigned g_t = tri_su32(sm.g[s][ii]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 d = tri_ld4(ez_t, lane, wz * 4 + q);
-                const float4 h = tri_ld4(fz_t, lane, wz * 4 + q);
-                ez[4 * q] = d.x; ez[4 * q + 1] = d.y; ez[4 * q + 2] = d.z; ez[4 * q + 3] = d.w;
-                fz[4 * q] = h.x; fz[4 * q + 1] = h.y; fz[4 * q + 2] = h.z; fz[4 * q + 3] = h.w;
-            }
+            for (int j = 0; j < 4; ++j) {
+                const int xr = lx + 8 * j;
+                const float4 e0 = tri_lds4(ey_t, xr, (y_base >> 2)), e1 = tri_lds4(ey_t, xr, (y_base >> 2) + 1);
+                const float4 f0 = tri_lds4(fy_t, xr, (y_base >> 2)), f1 = tri_lds4(fy_t, xr, (y_base >> 2) + 1);
+                const float4 ez4 = tri_lds4(ez_t, xr, zc), fz4 = tri_lds4(fz_t, xr, zc);
+                const float ey[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+                const float fy[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                const float ez[4] = {ez4.x, ez4.y, ez4.z, ez4.w};
+                const float fz[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float4 a = tri_ld4(ey_t, lane, wy * 2 + q);
-                const float4 b = tri_ld4(fy_t, lane, wy * 2 + q);
-                const float ey4[4] = {a.x, a.y, a.z, a.w};
-                const float fy4[4] = {b.x, b.y, b.z, b.w};
+                for (int y = 0; y < 8; ++y) {
+                    const float4 g4 = tri_lds4(g_t, y_base + y, zc);
+                    const float g[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                for (int y4 = 0; y4 < 4; ++y4) {
-                    const int yy = q * 4 + y4;
-                    const int r = wy * 8 + yy;
-#pragma unroll
-                    for (int zq = 0; zq < 4; ++zq) {
-                        const float4 g4 = tri_ld4(g_t, r, wz * 4 + zq);
-                        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                        for (int z4 = 0; z4 < 4; ++z4) {
-                            const int zz = zq * 4 + z4;
-                            float t = ey4[y4] * fz[zz];
-                            t = fmaf(ez[zz], fy4[y4], t);
-                            acc[yy][zz] = fmaf(t, g[z4], acc[yy][zz]);
-                        }
+                    for (int z = 0; z < 4; ++z) {
+                        float t = ey[y] * fz[z];
+                        t = fmaf(ez[z], fy[y], t);
+                        acc[j][y][z] = fmaf(t, g[z], acc[j][y][z]);
                     }
                 }
             }
@@ -560,17 +563,25 @@ __global__ void __launch_bounds__(256, 1)
         if (threadIdx.x == 0) atomicExch(err, 1);
         return;
     }
-    const int X = X0 + lane;
-    if (X >= P) return;
 #pragma unroll
-    for (int yy = 0; yy < 8; ++yy) {
-        const int Y = Y0 + wy * 8 + yy;
-        if (Y >= P) continue;
-        float* h = H + ((long long)X * P + Y) * P;
+    for (int j = 0; j < 4; ++j) {
+        const int X = X0 + lx + 8 * j;
+        if (X >= P) continue;
 #pragma unroll
-        for (int zz = 0; zz < 16; ++zz) {
-            const int Z = Z0 + wz * 16 + zz;
-            if (Z < P) h[Z] += acc[yy][zz];
+        for (int y = 0; y < 8; ++y) {
+            const int Y = Y0 + y_base + y;
+            if (Y >= P) continue;
+            const int Zb = Z0 + zc * 4;
+            float* h = H + ((long long)X * P + Y) * P + Zb;
+            if (Zb + 3 < P) {
+                float4 v = *reinterpret_cast<float4*>(h);
+                v.x += acc[j][y][0]; v.y += acc[j][y][1]; v.z += acc[j][y][2]; v.w += acc[j][y][3];
+                *reinterpret_cast<float4*>(h) = v;
+            } else {
+#pragma unroll
+                for (int z = 0; z < 4; ++z)
+                    if (Zb + z < P) h[z] += acc[j][y][z];
+            }
         }
     }
 }
