@@ -132,6 +132,9 @@ thc_status thc_residual(thc_ctx* ctx, const double* Zc, const double* t1,
 thc_status thc_energy(thc_ctx* ctx, const double* Zc, const double* t1,
                       double* energy);
 
+/* Learned preconditioner network (see thc_mlp_create). */
+typedef struct thc_mlp thc_mlp;
+
 typedef struct {
     double r_tol;        /* stop when |residual| < r_tol (1e-8) */
     double e_tol;        /* and |dE| < e_tol (0 = not used) */
@@ -142,6 +145,10 @@ typedef struct {
     double* history;     /* nullable host array of max_iter x 3 doubles: per
                             iteration (energy, residual norm, seconds since
                             the call started) */
+    thc_mlp* mlp;        /* network proposing steps when use_mlp = 1 */
+    int record_pairs;    /* > 0: record this many training pairs per
+                            iteration (elements drawn with replacement) */
+    unsigned long long record_seed;   /* seed of that draw */
 } thc_solve_opts;
 
 typedef struct {
@@ -168,6 +175,52 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts);
  */
 thc_status thc_solve(thc_ctx* ctx, const thc_solve_opts* opts,
                      double* Zc_inout, double* t1_inout, thc_report* report);
+
+/*
+ * Learned preconditioner (spec addition; the paper's update is not
+ * specified).  A pointwise MLP over the elements (P, Q) of the working basis:
+ * 8 features -> tanh(W1 x + b1) -> tanh(W2 a1 + b2) -> y = w3 . a2 + b3, width
+ * `hidden` (256).  Features of element (P, Q) at iteration k, with s the RMS
+ * of the doubles Jacobi step j = -sigma_q/(e_P + e_Q):
+ *   e_P/2, e_Q/2, clip(j/s, 10), clip(dT_prev/s, 10), sign(T) log1p(|T|/s)/5,
+ *   log10|r|/10, |e_P - e_Q|/2, 1.
+ * The proposed doubles step is j (1 + clamp(y, -0.95, 4)); singles keep
+ * Jacobi.  In thc_solve a proposal is accepted only if the next residual
+ * norm is smaller than the current one; otherwise the Jacobi + DIIS iterate
+ * from the same point is evaluated instead (one extra residual) and
+ * proposals pause for 3 iterations.
+ *
+ * Training pairs come from thc_solve with record_pairs > 0: per iteration
+ * k >= 2 the features X (n x 8), the scaled Jacobi step j/s and the scaled
+ * ideal step t = (T* - T_k)/s, T* the converged core.  Loss:
+ *   L = mean_n (j_n (1 + y_n) - t_n)^2,  trained with Adam.
+ * Parameters are one float32 vector [W1 (H x 8) | b1 | W2 (H x H) | b2 | w3 | b3]
+ * (row-major).  bf16 = 1 runs the H x H layer on the tensor cores with bf16
+ * weights/activations and float32 accumulation.  All pointers may be host or
+ * device memory; calls are synchronous on the network's stream.
+ */
+thc_status thc_mlp_create(int hidden, unsigned long long seed, int bf16, void* stream,
+                          thc_mlp** out);
+thc_status thc_mlp_num_params(const thc_mlp* mlp, long long* n);
+thc_status thc_mlp_get_params(thc_mlp* mlp, float* params);
+thc_status thc_mlp_set_params(thc_mlp* mlp, const float* params);
+/* y[n] = network(X[n]) for n samples of 8 features. */
+thc_status thc_mlp_predict(thc_mlp* mlp, const float* X, long long n, float* y);
+/* Loss of the samples and, if grad is not NULL, its gradient (n_params floats). */
+thc_status thc_mlp_loss_grad(thc_mlp* mlp, const float* X, const float* j, const float* t,
+                             long long n, double* loss, float* grad);
+/* Adam (beta 0.9/0.999, eps 1e-8) over `epochs` passes in minibatches of
+ * `batch`; *final_loss = mean loss of the last pass. */
+thc_status thc_mlp_train(thc_mlp* mlp, const float* X, const float* j, const float* t,
+                         long long n, int epochs, int batch, double lr,
+                         unsigned long long seed, double* final_loss);
+void thc_mlp_destroy(thc_mlp* mlp);
+
+/* Copy the training pairs recorded by the last thc_solve (record_pairs > 0,
+ * converged) into X (n x 8), j (n), t (n), at most max_n; *n_out = recorded
+ * count.  Any output pointer may be NULL. */
+thc_status thc_solve_pairs(thc_ctx* ctx, float* X, float* j, float* t, long long max_n,
+                           long long* n_out);
 
 /*
  * Per-step device timing (CUDA events recorded on the context's stream
@@ -224,8 +277,9 @@ const char* thc_step_name(int step);
  *   energy  host or device scalar, output
  *   stream  cudaStream_t or NULL
  *
- * Needs o*P + P*P + P + o*o + K + 1 <= THC_NOALLOC_SCRATCH; larger sizes
- * return THC_ERR_ARG with the reason in thc_last_error(NULL).  The first call
+ * Needs o*P + P*P + P + o*o + K + 1 <= THC_NOALLOC_SCRATCH; larger sizes, and
+ * inputs that are not device memory, return THC_ERR_ARG with the reason in
+ * thc_last_error(NULL).  The first call
  * on a device looks up the scratch array's device address (with that device
  * current), so make it before any stream capture.  Every call on a device
  * shares the one array and leaves its contents behind: calls whose work

@@ -5,8 +5,8 @@ in the CUDA library behind the C ABI declared in ``include/thc.h``.  There is
 no CPU fallback: if the library is not built, or no GPU is visible, the calls
 raise.
 """
-from .binding import (Context, Report, ThcError, load_library, exported_symbols,
+from .binding import (Context, Mlp, Report, ThcError, load_library, exported_symbols,
                       THC_PREC_FP64, THC_PREC_MIXED)
 
-__all__ = ["Context", "Report", "ThcError", "load_library", "exported_symbols",
+__all__ = ["Context", "Mlp", "Report", "ThcError", "load_library", "exported_symbols",
            "THC_PREC_FP64", "THC_PREC_MIXED"]

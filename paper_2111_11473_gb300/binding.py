@@ -29,7 +29,8 @@ class ThcConfig(C.Structure):
 class ThcSolveOpts(C.Structure):
     _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
                 ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int),
-                ("history", C.c_void_p)]
+                ("history", C.c_void_p), ("mlp", C.c_void_p), ("record_pairs", C.c_int),
+                ("record_seed", C.c_ulonglong)]
 
 
 class ThcReport(C.Structure):
@@ -82,6 +83,18 @@ _SIGNATURES = {
     "thc_step_name": (C.c_char_p, [C.c_int]),
     "thc_energy_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP,
                                      _DP, _DP, _VP]),
+    "thc_solve_pairs": (C.c_int, [_VP, _DP, _DP, _DP, C.c_longlong,
+                                  C.POINTER(C.c_longlong)]),
+    "thc_mlp_create": (C.c_int, [C.c_int, C.c_ulonglong, C.c_int, _VP, C.POINTER(_VP)]),
+    "thc_mlp_num_params": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+    "thc_mlp_get_params": (C.c_int, [_VP, _DP]),
+    "thc_mlp_set_params": (C.c_int, [_VP, _DP]),
+    "thc_mlp_predict": (C.c_int, [_VP, _DP, C.c_longlong, _DP]),
+    "thc_mlp_loss_grad": (C.c_int, [_VP, _DP, _DP, _DP, C.c_longlong, C.POINTER(C.c_double),
+                                    _DP]),
+    "thc_mlp_train": (C.c_int, [_VP, _DP, _DP, _DP, C.c_longlong, C.c_int, C.c_int, C.c_double,
+                                C.c_ulonglong, C.POINTER(C.c_double)]),
+    "thc_mlp_destroy": (None, [_VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }
@@ -207,7 +220,8 @@ class Context:
         return e.value
 
     def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
-              use_mlp=False, verbose=False, raise_on_failure=True, history=None):
+              use_mlp=False, verbose=False, raise_on_failure=True, history=None, mlp=None,
+              record_pairs=0, record_seed=0):
         """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero.
 
         If ``history`` is a list, (energy, |r|, seconds) per iteration is
@@ -224,6 +238,8 @@ class Context:
         opts.diis_n, opts.use_mlp, opts.verbose = diis_n, int(use_mlp), int(verbose)
         hbuf = np.zeros((max(1, max_iter), 3))
         opts.history = hbuf.ctypes.data
+        opts.mlp = mlp._h.value if mlp is not None else None
+        opts.record_pairs, opts.record_seed = int(record_pairs), int(record_seed)
         rep = ThcReport()
         st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
         if history is not None:
@@ -233,6 +249,18 @@ class Context:
         if st != 0 and raise_on_failure:
             self._check(st)
         return Zc, t1, report
+
+    def solve_pairs(self):
+        """Training pairs (X, j, t) recorded by the last solve, as numpy float32."""
+        n = C.c_longlong(0)
+        self._check(self._lib.thc_solve_pairs(self._h, None, None, None, 0, C.byref(n)))
+        X = np.empty((n.value, 8), np.float32)
+        j = np.empty(n.value, np.float32)
+        t = np.empty(n.value, np.float32)
+        if n.value:
+            self._check(self._lib.thc_solve_pairs(self._h, X.ctypes.data, j.ctypes.data,
+                                                  t.ctypes.data, n.value, C.byref(n)))
+        return X, j, t
 
     def profile(self, on=True):
         """Switch per-step device timing on (clears counters) or off."""
@@ -265,3 +293,72 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Mlp:
+    """The learned preconditioner network (wraps thc_mlp*)."""
+
+    def __init__(self, hidden=256, seed=0, bf16=True, stream=None):
+        lib = load_library()
+        h = _VP()
+        stream_ptr = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        st = lib.thc_mlp_create(hidden, seed, int(bf16), _VP(stream_ptr), C.byref(h))
+        if st != 0:
+            raise ThcError(st, lib.thc_last_error(None).decode())
+        self._lib = lib
+        self._h = h
+        self.hidden = hidden
+        n = C.c_longlong(0)
+        lib.thc_mlp_num_params(h, C.byref(n))
+        self.n_params = n.value
+
+    def _check(self, st):
+        if st != 0:
+            raise ThcError(st, self._lib.thc_last_error(None).decode())
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32)
+        self._check(self._lib.thc_mlp_get_params(self._h, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.shape == (self.n_params,)
+        self._check(self._lib.thc_mlp_set_params(self._h, p.ctypes.data))
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.empty(X.shape[0], np.float32)
+        self._check(self._lib.thc_mlp_predict(self._h, X.ctypes.data, X.shape[0], y.ctypes.data))
+        return y
+
+    def loss_grad(self, X, j, t):
+        X = np.ascontiguousarray(X, np.float32)
+        j = np.ascontiguousarray(j, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        g = np.empty(self.n_params, np.float32)
+        loss = C.c_double(0)
+        self._check(self._lib.thc_mlp_loss_grad(self._h, X.ctypes.data, j.ctypes.data,
+                                                t.ctypes.data, X.shape[0], C.byref(loss),
+                                                g.ctypes.data))
+        return loss.value, g
+
+    def train(self, X, j, t, epochs=10, batch=4096, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        j = np.ascontiguousarray(j, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        loss = C.c_double(0)
+        self._check(self._lib.thc_mlp_train(self._h, X.ctypes.data, j.ctypes.data, t.ctypes.data,
+                                            X.shape[0], epochs, batch, lr, seed, C.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.thc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

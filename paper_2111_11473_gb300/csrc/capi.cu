@@ -4,9 +4,16 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <algorithm>
 
 #include "engine.cuh"
 #include "solver.cuh"
+
+struct thc_mlp {
+    thc::Mlp m;
+    std::string err;
+    ~thc_mlp() { m.destroy(); }
+};
 
 struct thc_ctx {
     thc_config cfg{};
@@ -72,6 +79,10 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts) {
     opts->diis_n = 8;
     opts->use_mlp = 0;
     opts->verbose = 0;
+    opts->history = nullptr;
+    opts->mlp = nullptr;
+    opts->record_pairs = 0;
+    opts->record_seed = 0;
     return THC_OK;
 }
 
@@ -140,8 +151,10 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
         if (!e.ok()) { c->solver.reset(); return fail(c, e); }
     }
     thc_report rep{};
-    thc::Err e = c->e64 ? c->solver->run(*c->e64, *opts, Zc_inout, t1_inout, &rep)
-                        : c->solver->run(*c->e32, *opts, Zc_inout, t1_inout, &rep);
+    thc::Mlp* mlp = opts->mlp ? &opts->mlp->m : nullptr;
+    if (mlp) mlp->st = c->st;
+    thc::Err e = c->e64 ? c->solver->run(*c->e64, *opts, Zc_inout, t1_inout, &rep, mlp)
+                        : c->solver->run(*c->e32, *opts, Zc_inout, t1_inout, &rep, mlp);
     if (report) *report = rep;
     if (!e.ok()) return fail(c, e);
     return THC_OK;
@@ -177,6 +190,129 @@ const char* thc_step_name(int step) {
                                              "energy"};
     if (step < 0 || step >= THC_N_STEPS) return nullptr;
     return names[step];
+}
+
+thc_status thc_solve_pairs(thc_ctx* c, float* X, float* j, float* t, long long max_n,
+                           long long* n_out) {
+    if (!c || !n_out) return THC_ERR_ARG;
+    if (!c->solver) { *n_out = 0; return THC_OK; }
+    thc::Err e = c->solver->pairs(X, j, t, max_n, n_out, c->st);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+// Device copies of possibly-host arrays for the network entry points.
+struct DevArr {
+    float* p = nullptr;
+    bool own = false;
+    ~DevArr() { if (own && p) cudaFree(p); }
+};
+
+// Kernels only ever see device allocations: a caller's pointer is used in
+// place only if the runtime reports it as device memory; host memory of any
+// kind (pageable, pinned, managed or system-allocated) is staged through a
+// device copy.
+static thc::Err dev_in(const float* src, long long n, cudaStream_t st, DevArr& out) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeDevice &&
+        a.devicePointer == (const void*)src) {
+        out.p = const_cast<float*>(src);
+        return {};
+    }
+    cudaGetLastError();
+    THC_CUDA(cudaMalloc(&out.p, sizeof(float) * std::max<long long>(n, 1)));
+    out.own = true;
+    THC_CUDA(cudaMemcpyAsync(out.p, src, sizeof(float) * n, cudaMemcpyDefault, st));
+    return {};
+}
+
+thc_status thc_mlp_create(int hidden, unsigned long long seed, int bf16, void* stream,
+                          thc_mlp** out) {
+    if (!out || hidden <= 0 || hidden % 16) {
+        g_init_error = "thc_mlp_create: hidden must be a positive multiple of 16";
+        return THC_ERR_ARG;
+    }
+    *out = nullptr;
+    thc_mlp* m = new (std::nothrow) thc_mlp;
+    if (!m) return THC_ERR_OOM;
+    thc::Err e = m->m.create(hidden, seed, bf16 != 0, (cudaStream_t)stream);
+    if (!e.ok()) { g_init_error = e.msg; delete m; return e.code; }
+    *out = m;
+    return THC_OK;
+}
+
+thc_status thc_mlp_num_params(const thc_mlp* m, long long* n) {
+    if (!m || !n) return THC_ERR_ARG;
+    *n = m->m.np;
+    return THC_OK;
+}
+
+thc_status thc_mlp_get_params(thc_mlp* m, float* params) {
+    if (!m || !params) return THC_ERR_ARG;
+    if (cudaMemcpy(params, m->m.theta, sizeof(float) * m->m.np, cudaMemcpyDefault) != cudaSuccess)
+        return THC_ERR_CUDA;
+    return THC_OK;
+}
+
+thc_status thc_mlp_set_params(thc_mlp* m, const float* params) {
+    if (!m || !params) return THC_ERR_ARG;
+    if (cudaMemcpy(m->m.theta, params, sizeof(float) * m->m.np, cudaMemcpyDefault) != cudaSuccess)
+        return THC_ERR_CUDA;
+    cudaMemset(m->m.m, 0, sizeof(float) * m->m.np);
+    cudaMemset(m->m.v, 0, sizeof(float) * m->m.np);
+    m->m.step = 0;
+    return THC_OK;
+}
+
+thc_status thc_mlp_predict(thc_mlp* m, const float* X, long long n, float* y) {
+    if (!m || !X || !y || n <= 0) return THC_ERR_ARG;
+    DevArr dx, dy;
+    thc::Err e = dev_in(X, n * thc::kMlpFeatures, m->m.st, dx);
+    if (e.ok()) e = dev_in(y, n, m->m.st, dy);
+    if (e.ok()) e = m->m.forward(dx.p, n, dy.p);
+    if (e.ok() && dy.own)
+        if (cudaMemcpyAsync(y, dy.p, sizeof(float) * n, cudaMemcpyDefault, m->m.st) != cudaSuccess)
+            e = {THC_ERR_CUDA, "copy-out failed"};
+    if (e.ok() && cudaStreamSynchronize(m->m.st) != cudaSuccess) e = {THC_ERR_CUDA, "sync failed"};
+    if (!e.ok()) { g_init_error = e.msg; return e.code; }
+    return THC_OK;
+}
+
+thc_status thc_mlp_loss_grad(thc_mlp* m, const float* X, const float* j, const float* t,
+                             long long n, double* loss, float* grad) {
+    if (!m || !X || !j || !t || n <= 0) return THC_ERR_ARG;
+    DevArr dx, dj, dt;
+    thc::Err e = dev_in(X, n * thc::kMlpFeatures, m->m.st, dx);
+    if (e.ok()) e = dev_in(j, n, m->m.st, dj);
+    if (e.ok()) e = dev_in(t, n, m->m.st, dt);
+    double l = 0;
+    if (e.ok()) e = m->m.loss_grad(dx.p, dj.p, dt.p, n, &l);
+    if (e.ok() && grad &&
+        cudaMemcpy(grad, m->m.grad, sizeof(float) * m->m.np, cudaMemcpyDefault) != cudaSuccess)
+        e = {THC_ERR_CUDA, "copy-out failed"};
+    if (!e.ok()) { g_init_error = e.msg; return e.code; }
+    if (loss) *loss = l;
+    return THC_OK;
+}
+
+thc_status thc_mlp_train(thc_mlp* m, const float* X, const float* j, const float* t,
+                         long long n, int epochs, int batch, double lr,
+                         unsigned long long seed, double* final_loss) {
+    if (!m || !X || !j || !t || n <= 0) return THC_ERR_ARG;
+    DevArr dx, dj, dt;
+    thc::Err e = dev_in(X, n * thc::kMlpFeatures, m->m.st, dx);
+    if (e.ok()) e = dev_in(j, n, m->m.st, dj);
+    if (e.ok()) e = dev_in(t, n, m->m.st, dt);
+    if (e.ok()) e = m->m.train(dx.p, dj.p, dt.p, n, epochs, batch, (float)lr, seed, final_loss);
+    if (e.ok() && cudaStreamSynchronize(m->m.st) != cudaSuccess) e = {THC_ERR_CUDA, "sync failed"};
+    if (!e.ok()) { g_init_error = e.msg; return e.code; }
+    return THC_OK;
+}
+
+void thc_mlp_destroy(thc_mlp* m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->m.st);
+    delete m;
 }
 
 const char* thc_last_error(const thc_ctx* c) {

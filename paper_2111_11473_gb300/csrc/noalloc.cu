@@ -108,6 +108,15 @@ extern "C" thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
         set_thread_error("thc_energy_noalloc: non-positive size or NULL pointer");
         return THC_ERR_ARG;
     }
+    // The kernels read the inputs in place: they must be device memory.
+    for (const double* p : {Y, Lov, Zc, t1}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            set_thread_error("thc_energy_noalloc: Y, Lov, Zc and t1 must be device memory");
+            return THC_ERR_ARG;
+        }
+    }
     // Scratch layout: M3 (o P) | B (P P) | a (P) | Mo (o o) | part (K) | result (1)
     const long long need = (long long)o * P + (long long)P * P + P + (long long)o * o + K + 1;
     if (need > (long long)THC_NOALLOC_SCRATCH) {

@@ -128,6 +128,41 @@ __global__ void k_multidot(const double* A, const double* b, long long len, doub
 
 unsigned nb(long long n) { return (unsigned)std::min<long long>((n + 255) / 256, 152 * 32); }
 
+// out = a + b (n elements)
+__global__ void k_add(const double* a, const double* b, long long n, double* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] + b[i];
+}
+
+// out = a - b
+__global__ void k_sub(const double* a, const double* b, long long n, double* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+// out[k] = src[idx[k]]
+__global__ void k_gather64(const double* src, const long long* idx, long long n, double* out) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        out[k] = src[idx[k]];
+}
+
+// t[k] = (Tstar[idx[k]] - Tk[k]) / s[k]
+__global__ void k_targets(const double* Tstar, const long long* idx, const double* Tk,
+                          const double* sk, long long n, float* t) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        t[k] = (float)((Tstar[idx[k]] - Tk[k]) / sk[k]);
+}
+
+__global__ void k_fill64(double* p, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
 // Solve the bordered DIIS system; returns false if it is singular.
 bool diis_coefficients(const std::vector<double>& Bm, int m, std::vector<double>& c) {
     const int N = m + 1;
@@ -292,7 +327,7 @@ Err Solver::setup(Engine<T>& eng, double cutoff) {
 
 template <typename T>
 Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, double* t1_io,
-                thc_report* rep) {
+                thc_report* rep, Mlp* mlp) {
     cudaStream_t st = eng.st;
     const auto t0 = std::chrono::steady_clock::now();
     const long long PP = (long long)P * P, ov = (long long)o * v, rr = (long long)r * r;
@@ -316,6 +351,38 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     bool converged = false;
     int it = 0;
     const int max_iter = opts.max_iter > 0 ? opts.max_iter : 100;
+    // learned preconditioner and training-pair recording
+    const bool use_mlp = opts.use_mlp && mlp;
+    const long long nrec = std::max(0, opts.record_pairs);
+    if (use_mlp || nrec > 0) {
+        if (xprev.n < (size_t)len) {
+            THC_TRY(xprev.alloc(len));
+            THC_TRY(saved_x.alloc(len));
+            THC_TRY(saved_j.alloc(len));
+            THC_TRY(dprev.alloc(rr));
+            THC_TRY(smlp.alloc(rr));
+        }
+    }
+    if (use_mlp && feat.n < (size_t)rr * kMlpFeatures) {
+        THC_TRY(feat.alloc((size_t)rr * kMlpFeatures));
+        THC_TRY(jjb.alloc(rr));
+        THC_TRY(yb.alloc(rr));
+    }
+    n_rec = 0;
+    if (nrec > 0 && cap_rec < nrec * max_iter) {
+        cap_rec = nrec * max_iter;
+        THC_TRY(recX.alloc((size_t)cap_rec * kMlpFeatures));
+        THC_TRY(recJ.alloc(cap_rec));
+        THC_TRY(recT.alloc(cap_rec));
+        THC_TRY(recTk.alloc(cap_rec));
+        THC_TRY(recS.alloc(cap_rec));
+        THC_TRY(recIdx.alloc(cap_rec));
+    }
+    std::vector<long long> hidx(nrec);
+    unsigned long long rng = 0x2545F4914F6CDD1DULL ^ (unsigned long long)opts.record_seed;
+    bool have_prev = false, last_was_mlp = false;
+    double last_norm = 0;
+    int saved_slot = -1, cooldown = 0, n_acc = 0, n_rej = 0;
     for (it = 1; it <= max_iter; ++it) {
         // Zc = C T C^T
         THC_TRY(mm(st, P, r, r, rm64(C.p, r), rm64(x.p + ov, r), tmp.p, r, 1, 0));
@@ -350,6 +417,44 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         }
         if (opts.verbose)
             fprintf(stderr, "thc_solve it %3d  E = %.12f  |r| = %.3e\n", it, energy, norm);
+        if (last_was_mlp) {
+            last_was_mlp = false;
+            if (norm < last_norm) {
+                ++n_acc;
+            } else {
+                // Rejected: fall back to the Jacobi + DIIS iterate from the
+                // point the proposal was made at, and pause proposals.
+                ++n_rej;
+                cooldown = 3;
+                k_add<<<nb(len), 256, 0, st>>>(saved_x.p, saved_j.p, len, xnew.p);
+                count_launches(1);
+                THC_CUDA(cudaGetLastError());
+                if (m > 0 && saved_slot >= 0) {
+                    THC_CUDA(cudaMemcpyAsync(hx.p + (long long)saved_slot * len, xnew.p,
+                                             sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+                    std::vector<double> c;
+                    std::vector<double> Bsub((size_t)nhist * nhist);
+                    for (int i = 0; i < nhist; ++i)
+                        for (int j = 0; j < nhist; ++j) Bsub[(size_t)i * nhist + j] = B[(size_t)i * m + j];
+                    if (nhist >= 2 && diis_coefficients(Bsub, nhist, c)) {
+                        THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
+                                                 cudaMemcpyHostToDevice, st));
+                        k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
+                        count_launches(1);
+                        THC_CUDA(cudaGetLastError());
+                    } else {
+                        THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len,
+                                                 cudaMemcpyDeviceToDevice, st));
+                    }
+                } else {
+                    THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len,
+                                             cudaMemcpyDeviceToDevice, st));
+                }
+                THC_CUDA(cudaMemcpyAsync(xprev.p, saved_x.p, sizeof(double) * len,
+                                         cudaMemcpyDeviceToDevice, st));
+                continue;
+            }
+        }
         const bool de_ok = opts.e_tol <= 0 || (it > 1 && std::fabs(energy - e_prev) < opts.e_tol);
         e_prev = energy;
         if (norm < opts.r_tol && de_ok) {
@@ -360,8 +465,61 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
                                            step.p, xnew.p);
         count_launches(1);
         THC_CUDA(cudaGetLastError());
+        bool mlp_used = false;
+        if ((nrec > 0 || use_mlp) && it >= 2) {
+            // scale of this iteration's doubles Jacobi step, previous step
+            k_multidot<<<1, 256, 0, st>>>(step.p + ov, step.p + ov, rr, dots.p + 8);
+            k_sub<<<nb(rr), 256, 0, st>>>(x.p + ov, xprev.p + ov, rr, dprev.p);
+            count_launches(2);
+            THC_CUDA(cudaGetLastError());
+            double ss = 0;
+            THC_CUDA(cudaMemcpyAsync(&ss, dots.p + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+            THC_CUDA(cudaStreamSynchronize(st));
+            const double sc = std::max(std::sqrt(ss / (double)rr), 1e-300);
+            const double lr = std::log10(std::max(norm, 1e-300));
+            const double* dp = have_prev ? dprev.p : nullptr;
+            if (nrec > 0 && n_rec + nrec <= cap_rec) {
+                for (long long k = 0; k < nrec; ++k) {
+                    rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17;
+                    hidx[k] = (long long)(rng % (unsigned long long)rr);
+                }
+                long long* di = recIdx.p + n_rec;
+                THC_CUDA(cudaMemcpyAsync(di, hidx.data(), sizeof(long long) * nrec,
+                                         cudaMemcpyHostToDevice, st));
+                THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, di, nrec, r, sc, lr,
+                                      recX.p + n_rec * kMlpFeatures, recJ.p + n_rec, st));
+                k_gather64<<<nb(nrec), 256, 0, st>>>(x.p + ov, di, nrec, recTk.p + n_rec);
+                k_fill64<<<nb(nrec), 256, 0, st>>>(recS.p + n_rec, nrec, sc);
+                count_launches(2);
+                THC_CUDA(cudaGetLastError());
+                // hidx is reused next iteration: the copy must finish first
+                THC_CUDA(cudaStreamSynchronize(st));
+                n_rec += nrec;
+            }
+            if (use_mlp && cooldown == 0) {
+                THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, nullptr, rr, r, sc, lr, feat.p,
+                                      jjb.p, st));
+                THC_TRY(mlp->forward(feat.p, rr, yb.p));
+                THC_CUDA(mlp_apply(sq.p, e.p, yb.p, r, smlp.p, st));
+                k_add<<<nb(rr), 256, 0, st>>>(x.p + ov, smlp.p, rr, xnew.p + ov);
+                count_launches(1);
+                THC_CUDA(cudaGetLastError());
+                mlp_used = true;
+            }
+        }
+        if (use_mlp || nrec > 0) {
+            THC_CUDA(cudaMemcpyAsync(saved_x.p, x.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+            THC_CUDA(cudaMemcpyAsync(saved_j.p, step.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+            THC_CUDA(cudaMemcpyAsync(xprev.p, x.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+            have_prev = true;
+        }
+        last_norm = norm;
+        last_was_mlp = mlp_used;
+        if (cooldown > 0) --cooldown;
+        saved_slot = -1;
         if (m > 0) {
             const int slot = head;
+            saved_slot = slot;
             head = (head + 1) % m;
             nhist = std::min(nhist + 1, m);
             THC_CUDA(cudaMemcpyAsync(hx.p + (long long)slot * len, xnew.p, sizeof(double) * len,
@@ -399,7 +557,17 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     THC_CUDA(cudaMemcpyAsync(Zc_io, Zc.p, sizeof(double) * PP, cudaMemcpyDefault, st));
     THC_CUDA(cudaMemcpyAsync(t1_io, eng.t1d.p, sizeof(double) * ov, cudaMemcpyDefault, st));
     THC_CUDA(cudaStreamSynchronize(st));
+    if (converged && n_rec > 0) {
+        k_targets<<<nb(n_rec), 256, 0, st>>>(x.p + ov, recIdx.p, recTk.p, recS.p, n_rec, recT.p);
+        count_launches(1);
+        THC_CUDA(cudaGetLastError());
+        THC_CUDA(cudaStreamSynchronize(st));
+    } else {
+        n_rec = 0;
+    }
     rep->iters = converged ? it : max_iter;
+    rep->mlp_accepted = n_acc;
+    rep->mlp_rejected = n_rej;
     rep->energy = energy;
     rep->r_norm = norm;
     rep->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -410,8 +578,21 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
 template Err Solver::setup<double>(Engine<double>&, double);
 template Err Solver::setup<float>(Engine<float>&, double);
 template Err Solver::run<double>(Engine<double>&, const thc_solve_opts&, double*, double*,
-                                 thc_report*);
+                                 thc_report*, Mlp*);
 template Err Solver::run<float>(Engine<float>&, const thc_solve_opts&, double*, double*,
-                                thc_report*);
+                                thc_report*, Mlp*);
+
+Err Solver::pairs(float* X, float* j, float* t, long long max_n, long long* n_out,
+                  cudaStream_t st) {
+    const long long n = std::min(n_rec, max_n);
+    if (n > 0) {
+        if (X) THC_CUDA(cudaMemcpyAsync(X, recX.p, sizeof(float) * n * kMlpFeatures, cudaMemcpyDefault, st));
+        if (j) THC_CUDA(cudaMemcpyAsync(j, recJ.p, sizeof(float) * n, cudaMemcpyDefault, st));
+        if (t) THC_CUDA(cudaMemcpyAsync(t, recT.p, sizeof(float) * n, cudaMemcpyDefault, st));
+        THC_CUDA(cudaStreamSynchronize(st));
+    }
+    *n_out = n_rec;
+    return Err{};
+}
 
 }  // namespace thc

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "mlp.cuh"
 
 namespace thc {
 
@@ -28,11 +29,24 @@ struct Solver {
     std::vector<double> B;             // DIIS overlap matrix (host)
     int nhist = 0, head = 0;
 
+    // Learned-preconditioner state: previous iterate, saved point of the last
+    // proposal, features and network outputs for all r^2 elements.
+    DBuf<double> xprev, dprev, saved_x, saved_j, smlp;
+    DBuf<float> feat, jjb, yb;
+    // Recorded training pairs (features, scaled Jacobi step, scaled target).
+    DBuf<float> recX, recJ, recT;
+    DBuf<double> recTk, recS;
+    DBuf<long long> recIdx;
+    long long n_rec = 0, cap_rec = 0;
+
     template <typename T>
     Err setup(Engine<T>& eng, double cutoff);
     template <typename T>
     Err run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, double* t1_io,
-            thc_report* rep);
+            thc_report* rep, Mlp* mlp);
+    // Copy out the pairs recorded by the last run (host or device pointers).
+    Err pairs(float* X, float* j, float* t, long long max_n, long long* n_out,
+              cudaStream_t st);
 
     Err mm(cudaStream_t st, int M, int N, int K, View<double> A, View<double> Bv, double* Cp,
            long long ldc, double alpha, double beta);

@@ -26,9 +26,12 @@ def lib():
 def test_header_declares_the_abi():
     assert _declared() == ["thc_config_default", "thc_destroy", "thc_energy",
                            "thc_energy_noalloc", "thc_init",
-                           "thc_last_error", "thc_profile_enable", "thc_profile_read",
+                           "thc_last_error", "thc_mlp_create", "thc_mlp_destroy",
+                           "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",
+                           "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
+                           "thc_profile_enable", "thc_profile_read",
                            "thc_residual", "thc_solve", "thc_solve_opts_default",
-                           "thc_step_name"]
+                           "thc_solve_pairs", "thc_step_name"]
 
 
 def test_library_exports_every_declared_symbol(lib):
