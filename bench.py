@@ -13,8 +13,11 @@ from zero.
   roofline   dominant kernel: algorithmic flops per launch / average launch
              time, from the library's per-step CUDA-event profile
   cpu_baseline  the FP64 CPU oracle, one full residual on the same system
-  solve      wall time of thc_solve to |r| < 1e-8 and time until the energy
-             is within 1e-6 Eh of its converged value
+  solve      solves from zero of the same system: float64 to |r| < 1e-8 (its
+             energy is the reference), mixed precision, and mixed precision
+             with the learned preconditioner (trained on the GPU on pairs
+             from six small systems of the same family); for each the wall
+             time until the energy is within 1e-6 Eh of the reference
 
 Multi-GPU (torchrun): every rank evaluates residuals of its own system
 (independent problems, weak scaling, no collective in the data path).
@@ -115,6 +118,23 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest per-rank value (a time) over all ranks; x itself at N = 1."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, ms_max):
+    """Residual evaluations per second of the whole job: every rank evaluates
+    one residual of its own system per step, and the slowest rank sets the
+    step time."""
+    return world * 1e3 / ms_max
+
+
 def _system(seed_offset=0):
     from synth import make_system
     w = WORKLOAD
@@ -172,6 +192,88 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _rate(ctx, Zc, t1, sig, sig1, stream, dev, steps=5, warmup=3):
+    """Residual evaluations per second (CUDA events on the library's stream)."""
+    import torch
+    for _ in range(warmup):
+        ctx.residual(Zc, t1, out=(sig, sig1))
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.residual(Zc, t1, out=(sig, sig1))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return 1e3 * steps / e0.elapsed_time(e1)
+
+
+def solve_variants(pkg, s, dev, stream, ctx, args, prec):
+    """Solves from zero: float64, mixed precision, and mixed precision with the
+    learned preconditioner; time to 1e-6 Eh of the float64 converged energy."""
+    import numpy as np
+    import torch
+    from paper_2111_11473_gb300 import precond
+    from synth import make_system
+    out = {}
+    fp64_ctx = ctx
+    if prec != pkg.THC_PREC_FP64:
+        fp64_ctx = pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z,
+                               precision=pkg.THC_PREC_FP64, stream=stream)
+    f = precond.run_solve(fp64_ctx, None, None, r_tol=1e-8, max_iter=60)
+    e_ref = f["energy"]
+    f["evals_per_s"] = None
+    out["fp64"] = f
+    if fp64_ctx is not ctx:
+        fp64_ctx.close()
+    # Mixed precision: residual rate on the bench state, then solves.
+    mctx = ctx if prec == pkg.THC_PREC_MIXED else pkg.Context(
+        s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z, precision=pkg.THC_PREC_MIXED, stream=stream)
+    Zc0, t10, _ = mctx.solve(max_iter=3, diis_n=0, raise_on_failure=False)
+    Zc = torch.from_numpy(Zc0).to(dev)
+    t1 = torch.from_numpy(t10).to(dev)
+    sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
+    sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
+    mrate = _rate(mctx, Zc, t1, sig, sig1, stream, dev)
+    # The mixed-precision residual has a floor near 5e-6 at this size (the
+    # bf16x3 products' rounding): the mixed solves stop at |r| < 1e-5 once
+    # the energy changes by less than 1e-8 Eh per iteration.
+    m = precond.run_solve(mctx, e_ref, None, r_tol=1e-5, max_iter=60, stop_de=1e-8)
+    m["evals_per_s"] = mrate
+    out["mixed"] = m
+    # Learned preconditioner: pairs from small systems of the same family
+    # (v = 5o, P = 10o, G = 30o, K = 15o), trained on the GPU.
+    t0 = time.perf_counter()
+    Xs, js, ts = [], [], []
+    for k, o in enumerate((8, 10, 12, 14, 16, 18)):
+        ss = make_system(o, 5 * o, 10 * o, 30 * o, 15 * o, 100 + k)
+        with pkg.Context(ss.eps_o, ss.eps_v, ss.Y, ss.L, ss.x, ss.z,
+                         precision=pkg.THC_PREC_MIXED, stream=stream) as c:
+            X, j, t, _ = precond.collect_pairs(c, seed=k)
+        Xs.append(X)
+        js.append(j)
+        ts.append(t)
+    X, j, t = (np.concatenate(a) for a in (Xs, js, ts))
+    net, loss, jacobi = precond.train(X, j, t, epochs=20)
+    train_s = time.perf_counter() - t0
+    lrn = precond.run_solve(mctx, e_ref, net, r_tol=1e-5, max_iter=60, stop_de=1e-8)
+    lrn["evals_per_s"] = mrate
+    lrn["training"] = {"systems": "o = 8..18, v = 5o, P = 10o, G = 30o, K = 15o, seeds 100-105",
+                       "pairs": int(len(j)), "loss": loss, "loss_plain_jacobi": jacobi,
+                       "seconds": train_s, "hidden": 256, "weights": "bf16"}
+    out["mixed+learned"] = lrn
+    net.close()
+    if mctx is not ctx:
+        mctx.close()
+    t_ref = f["time_to_e_tol_s"]
+    out["e_ref"] = e_ref
+    out["speedup_time_to_1e-6_Eh_vs_fp64"] = {
+        k: (t_ref / out[k]["time_to_e_tol_s"]
+            if t_ref and out[k]["time_to_e_tol_s"] else None)
+        for k in ("mixed", "mixed+learned")}
+    return out
 
 
 def main():
@@ -240,12 +342,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * 1e3 / ms_max
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_rate(world, ms_max)
 
     # End to end through the public API with pinned host buffers.
     Zh = torch.from_numpy(Zc0).pin_memory()
@@ -259,11 +357,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.residual(Zh, t1h, out=(sh, s1h))
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
     h2d = (s.P * s.P + s.o * s.v) * 8
     d2h = (s.P * s.P + s.o * s.v + 1) * 8
 
@@ -295,7 +389,7 @@ def main():
                    "l2": "inputs larger than L2 (Cholesky blocks 238 MB, grid factors 1.5 GB)",
                    "parallelism": f"{world} independent system(s), one per GPU"},
         "energy": energy,
-        "e2e": {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(world, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": prof["kernel_launches"],
         "clocks": clocks,
@@ -305,18 +399,7 @@ def main():
     }
 
     if not args.no_solve:
-        Zs = np.zeros((s.P, s.P))
-        ts = np.zeros((s.o, s.v))
-        hist = []
-        t0 = time.perf_counter()
-        _, _, rep = ctx.solve(Zs, ts, r_tol=1e-8, max_iter=60, history=hist,
-                              raise_on_failure=False)
-        wall = time.perf_counter() - t0
-        e_fin = rep.energy
-        t_1e6 = next((h[2] for h in hist if abs(h[0] - e_fin) < 1e-6), None)
-        line["solve"] = {"status": rep.status, "iters": rep.iters, "energy": e_fin,
-                         "r_norm": rep.r_norm, "wall_s": wall,
-                         "time_to_1e-6_Eh_s": t_1e6, "precision": args.precision}
+        line["solve"] = solve_variants(pkg, s, dev, stream, ctx, args, prec)
     ctx.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

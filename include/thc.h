@@ -177,18 +177,20 @@ thc_status thc_solve(thc_ctx* ctx, const thc_solve_opts* opts,
                      double* Zc_inout, double* t1_inout, thc_report* report);
 
 /*
- * Learned preconditioner (spec addition; the paper's update is not
- * specified).  A pointwise MLP over the elements (P, Q) of the working basis:
+ * Learned preconditioner (an addition to the method: the paper does not
+ * specify the amplitude update).  A pointwise MLP over the elements (P, Q) of the working basis:
  * 8 features -> tanh(W1 x + b1) -> tanh(W2 a1 + b2) -> y = w3 . a2 + b3, width
  * `hidden` (256).  Features of element (P, Q) at iteration k, with s the RMS
  * of the doubles Jacobi step j = -sigma_q/(e_P + e_Q):
  *   e_P/2, e_Q/2, clip(j/s, 10), clip(dT_prev/s, 10), sign(T) log1p(|T|/s)/5,
  *   log10|r|/10, |e_P - e_Q|/2, 1.
  * The proposed doubles step is j (1 + clamp(y, -0.95, 4)); singles keep
- * Jacobi.  In thc_solve a proposal is accepted only if the next residual
- * norm is smaller than the current one; otherwise the Jacobi + DIIS iterate
- * from the same point is evaluated instead (one extra residual) and
- * proposals pause for 3 iterations.
+ * Jacobi, and DIIS stores the step taken as its error vector.  In thc_solve
+ * a proposal is accepted only if the next residual norm is smaller than the
+ * current one by at least the factor the last plain Jacobi + DIIS iteration
+ * achieved; otherwise the plain iterate from the same point is evaluated
+ * instead (one extra residual), and after two rejections the solve continues
+ * without proposals.
  *
  * Training pairs come from thc_solve with record_pairs > 0: per iteration
  * k >= 2 the features X (n x 8), the scaled Jacobi step j/s and the scaled

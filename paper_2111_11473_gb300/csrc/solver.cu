@@ -380,9 +380,45 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     }
     std::vector<long long> hidx(nrec);
     unsigned long long rng = 0x2545F4914F6CDD1DULL ^ (unsigned long long)opts.record_seed;
-    bool have_prev = false, last_was_mlp = false;
-    double last_norm = 0;
-    int saved_slot = -1, cooldown = 0, n_acc = 0, n_rej = 0;
+    bool have_prev = false, last_was_mlp = false, mlp_off = false;
+    double last_norm = 0, rho_plain = 1.0;
+    int saved_slot = -1, n_acc = 0, n_rej = 0;
+    // DIIS history: store (x, e) in slot and refresh that row of B.
+    auto diis_store = [&](int slot, const double* xv, const double* ev) -> Err {
+        THC_CUDA(cudaMemcpyAsync(hx.p + (long long)slot * len, xv, sizeof(double) * len,
+                                 cudaMemcpyDeviceToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(he.p + (long long)slot * len, ev, sizeof(double) * len,
+                                 cudaMemcpyDeviceToDevice, st));
+        k_multidot<<<m, 256, 0, st>>>(he.p, he.p + (long long)slot * len, len, dots.p);
+        count_launches(1);
+        THC_CUDA(cudaGetLastError());
+        std::vector<double> row(m);
+        THC_CUDA(cudaMemcpyAsync(row.data(), dots.p, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        THC_CUDA(cudaStreamSynchronize(st));
+        for (int k = 0; k < nhist; ++k) {
+            B[(size_t)slot * m + k] = row[k];
+            B[(size_t)k * m + slot] = row[k];
+        }
+        return Err{};
+    };
+    // x = DIIS extrapolation of the stored pairs, or `fallback` if there is
+    // too little history or the DIIS system is singular.
+    auto diis_extrapolate = [&](const double* fallback) -> Err {
+        std::vector<double> c;
+        std::vector<double> Bsub((size_t)nhist * nhist);
+        for (int i = 0; i < nhist; ++i)
+            for (int j = 0; j < nhist; ++j) Bsub[(size_t)i * nhist + j] = B[(size_t)i * m + j];
+        if (nhist >= 2 && diis_coefficients(Bsub, nhist, c)) {
+            THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
+                                     cudaMemcpyHostToDevice, st));
+            k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
+            count_launches(1);
+            THC_CUDA(cudaGetLastError());
+        } else {
+            THC_CUDA(cudaMemcpyAsync(x.p, fallback, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+        }
+        return Err{};
+    };
     for (it = 1; it <= max_iter; ++it) {
         // Zc = C T C^T
         THC_TRY(mm(st, P, r, r, rm64(C.p, r), rm64(x.p + ov, r), tmp.p, r, 1, 0));
@@ -419,33 +455,22 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             fprintf(stderr, "thc_solve it %3d  E = %.12f  |r| = %.3e\n", it, energy, norm);
         if (last_was_mlp) {
             last_was_mlp = false;
-            if (norm < last_norm) {
+            // A proposal stands only if the residual norm drops, and by at
+            // least the factor the last plain Jacobi + DIIS iteration achieved.
+            if (norm < last_norm * std::min(1.0, rho_plain)) {
                 ++n_acc;
             } else {
-                // Rejected: fall back to the Jacobi + DIIS iterate from the
-                // point the proposal was made at, and pause proposals.
+                // Rejected: replace the proposal in the DIIS history by the
+                // Jacobi step from the same point and continue from the
+                // plain iterate.  Two rejections switch proposals off.
                 ++n_rej;
-                cooldown = 3;
+                if (n_rej >= 2) mlp_off = true;
                 k_add<<<nb(len), 256, 0, st>>>(saved_x.p, saved_j.p, len, xnew.p);
                 count_launches(1);
                 THC_CUDA(cudaGetLastError());
                 if (m > 0 && saved_slot >= 0) {
-                    THC_CUDA(cudaMemcpyAsync(hx.p + (long long)saved_slot * len, xnew.p,
-                                             sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
-                    std::vector<double> c;
-                    std::vector<double> Bsub((size_t)nhist * nhist);
-                    for (int i = 0; i < nhist; ++i)
-                        for (int j = 0; j < nhist; ++j) Bsub[(size_t)i * nhist + j] = B[(size_t)i * m + j];
-                    if (nhist >= 2 && diis_coefficients(Bsub, nhist, c)) {
-                        THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
-                                                 cudaMemcpyHostToDevice, st));
-                        k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
-                        count_launches(1);
-                        THC_CUDA(cudaGetLastError());
-                    } else {
-                        THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len,
-                                                 cudaMemcpyDeviceToDevice, st));
-                    }
+                    THC_TRY(diis_store(saved_slot, xnew.p, saved_j.p));
+                    THC_TRY(diis_extrapolate(xnew.p));
                 } else {
                     THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len,
                                              cudaMemcpyDeviceToDevice, st));
@@ -454,6 +479,8 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
                                          cudaMemcpyDeviceToDevice, st));
                 continue;
             }
+        } else if (it > 1 && last_norm > 0) {
+            rho_plain = norm / last_norm;
         }
         const bool de_ok = opts.e_tol <= 0 || (it > 1 && std::fabs(energy - e_prev) < opts.e_tol);
         e_prev = energy;
@@ -496,7 +523,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
                 THC_CUDA(cudaStreamSynchronize(st));
                 n_rec += nrec;
             }
-            if (use_mlp && cooldown == 0) {
+            if (use_mlp && !mlp_off) {
                 THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, nullptr, rr, r, sc, lr, feat.p,
                                       jjb.p, st));
                 THC_TRY(mlp->forward(feat.p, rr, yb.p));
@@ -513,42 +540,21 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             THC_CUDA(cudaMemcpyAsync(xprev.p, x.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
             have_prev = true;
         }
+        // DIIS error vector = the step actually taken: the proposal replaces
+        // the doubles part of the Jacobi step when one is made.
+        if (mlp_used)
+            THC_CUDA(cudaMemcpyAsync(step.p + ov, smlp.p, sizeof(double) * rr,
+                                     cudaMemcpyDeviceToDevice, st));
         last_norm = norm;
         last_was_mlp = mlp_used;
-        if (cooldown > 0) --cooldown;
         saved_slot = -1;
         if (m > 0) {
             const int slot = head;
             saved_slot = slot;
             head = (head + 1) % m;
             nhist = std::min(nhist + 1, m);
-            THC_CUDA(cudaMemcpyAsync(hx.p + (long long)slot * len, xnew.p, sizeof(double) * len,
-                                     cudaMemcpyDeviceToDevice, st));
-            THC_CUDA(cudaMemcpyAsync(he.p + (long long)slot * len, step.p, sizeof(double) * len,
-                                     cudaMemcpyDeviceToDevice, st));
-            k_multidot<<<m, 256, 0, st>>>(he.p, step.p, len, dots.p);
-            count_launches(1);
-            THC_CUDA(cudaGetLastError());
-            std::vector<double> row(m);
-            THC_CUDA(cudaMemcpyAsync(row.data(), dots.p, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-            THC_CUDA(cudaStreamSynchronize(st));
-            for (int k = 0; k < nhist; ++k) {
-                B[(size_t)slot * m + k] = row[k];
-                B[(size_t)k * m + slot] = row[k];
-            }
-            std::vector<double> c;
-            std::vector<double> Bsub((size_t)nhist * nhist);
-            for (int i = 0; i < nhist; ++i)
-                for (int j = 0; j < nhist; ++j) Bsub[(size_t)i * nhist + j] = B[(size_t)i * m + j];
-            if (nhist >= 2 && diis_coefficients(Bsub, nhist, c)) {
-                THC_CUDA(cudaMemcpyAsync(dots.p, c.data(), sizeof(double) * nhist,
-                                         cudaMemcpyHostToDevice, st));
-                k_combine<<<nb(len), 256, 0, st>>>(hx.p, dots.p, nhist, len, x.p);
-                count_launches(1);
-                THC_CUDA(cudaGetLastError());
-            } else {
-                THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
-            }
+            THC_TRY(diis_store(slot, xnew.p, step.p));
+            THC_TRY(diis_extrapolate(xnew.p));
         } else {
             THC_CUDA(cudaMemcpyAsync(x.p, xnew.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
         }

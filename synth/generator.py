@@ -114,12 +114,14 @@ def random_amplitudes(P: int, o: int, v: int, seed: int,
     return np.ascontiguousarray(Zc), np.ascontiguousarray(t1)
 
 
-# The workloads: (o, v, P, G, K, seed).
+# The workloads, named by their sizes: (o, v, P, G, K, seed).
 CONFIGS = {
-    "c1": (5, 20, 60, 120, 60, 0),
-    "c2": (40, 200, 400, 1200, 600, 1),
-    "c3": (100, 600, 1000, 3500, 1500, 2),
-    "c5": (60, 300, 600, 1800, 900, 200),
+    "o5_v20_P60_G120_K60": (5, 20, 60, 120, 60, 0),
+    "o40_v200_P400_G1200_K600": (40, 200, 400, 1200, 600, 1),
+    "o100_v600_P1000_G3500_K1500": (100, 600, 1000, 3500, 1500, 2),
+    "o250_v2250_P2500_G12500_K7500": (250, 2250, 2500, 12500, 7500, 3),
+    # first held-out system of the learned-preconditioner protocol
+    "o60_v300_P600_G1800_K900": (60, 300, 600, 1800, 900, 200),
 }
 
 

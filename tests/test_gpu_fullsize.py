@@ -18,10 +18,10 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def c2():
+def o40_system():
     import __graft_entry__ as g
     g.build()
-    o, v, P, G, K, seed = CONFIGS["c2"]
+    o, v, P, G, K, seed = CONFIGS["o40_v200_P400_G1200_K600"]
     s = make_system(o, v, P, G, K, seed)
     from oracle import closed_shell as cs
     H = cs.Hamiltonian.from_inputs(s.eps_o, s.eps_v, s.L, s.x, s.z)
@@ -30,8 +30,8 @@ def c2():
     ctx.close()
 
 
-def test_fullsize_singles_only_state(c2):
-    s, H, ctx = c2
+def test_fullsize_singles_only_state(o40_system):
+    s, H, ctx = o40_system
     from oracle import closed_shell as cs, thc
     _, t1 = random_amplitudes(s.P, s.o, s.v, 77, t1_scale=0.02)
     Zc = np.zeros((s.P, s.P))
@@ -45,8 +45,8 @@ def test_fullsize_singles_only_state(c2):
     assert abs(E - cs.energy(H, t1, np.zeros((s.o, s.o, s.v, s.v)))) < 1e-9
 
 
-def test_fullsize_energy_and_structure(c2):
-    s, H, ctx = c2
+def test_fullsize_energy_and_structure(o40_system):
+    s, H, ctx = o40_system
     from oracle import closed_shell as cs, thc
     Zc, t1 = random_amplitudes(s.P, s.o, s.v, 78, t2_scale=0.01, t1_scale=0.01)
     sig = []

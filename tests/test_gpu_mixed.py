@@ -63,7 +63,7 @@ def test_mixed_alg7_routes(route):
 @pytest.mark.parametrize("tcp", [3, 0])
 def test_mixed_fullsize_error_against_fp64_gpu(tcp):
     import paper_2111_11473_gb300 as pkg
-    o, v, P, G, K, seed = CONFIGS["c2"]
+    o, v, P, G, K, seed = CONFIGS["o40_v200_P400_G1200_K600"]
     s = make_system(o, v, P, G, K, seed)
     Zc, t1 = random_amplitudes(P, o, v, 78, t2_scale=0.01, t1_scale=0.01)
     with context(s) as c64:

@@ -20,7 +20,7 @@ def _built():
 
 
 CASES = [
-    # o, v, P, G, K, seed: tiny; several 64-tiles with ragged tails; c1 shape
+    # o, v, P, G, K, seed: tiny; several 64-tiles with ragged tails; the o=5, v=20, P=60 shape
     (3, 7, 10, 14, 9, 5),
     (7, 37, 70, 90, 45, 11),
     (5, 20, 60, 120, 60, 0),
