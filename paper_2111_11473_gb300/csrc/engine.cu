@@ -189,23 +189,36 @@ Err Engine<T>::dress(const T* oo_, const T* ov_, const T* vv_, int nb, T* out_oo
     return Err{};
 }
 
-// Coulomb (J) and exchange (X) parts of the Fock matrix from nb vectors:
-// J_pq += sum_A tr(L^_oo^A) L^_pq^A,  X_pq += sum_A sum_k L^_pk^A L^_kq^A.
+// The T1-dressed Fock matrix F^ = h^ + 2 J(L^) - X(L^) (Eqs. 24-27 applied to the
+// canonical Fock operator f = diag(eps) with h backed out) written without
+// its large cancelling parts.  With t the n x n matrix holding t_i^a in block
+// (a, i), L^ = (1 - t) L (1 + t), and t t = 0:
+//   J(L^) = dress(J(L)) + sum_A delta^A L^^A,   delta^A = sum_ia t_i^a L_ia^A,
+//   X(L^) = dress(X(L)) + sum_A L^^A t L^^A,
+// so that  F^ = dress(f) + 2 sum_A delta^A L^^A - sum_A L^^A t L^^A  with
+// dress(f) = f + (eps_a - eps_i) t_i^a in block (a, i).  Every term but f is
+// of order t1, so the float32 engine keeps its relative precision where the
+// direct form subtracts Coulomb sums of order o times (pp|qq).
+// This routine accumulates, for the nb dressed vectors of a slab,
+//   J_pq += sum_A delta^A L^_pq^A,   X_pq += sum_A sum_ai L^_pa^A t_i^a L^_iq^A.
 template <typename T>
-Err Engine<T>::fock_slab(int nb, bool, T* Jo, T* Jov_, T* Jvo_, T* Jv, T* Xo, T* Xov_,
-                         T* Xvo_, T* Xv, const T* Loo_, const T* Lov_, const T* Lvo_,
-                         const T* Lvv_) {
-    THC_CUDA(traces(Loo_, o, nb, dtr.p, st));
-    View<T> d{dtr.p, 0, 1};
+Err Engine<T>::fock_slab(int nb, const T* Loo_, const T* Lov_, const T* Lvo_, const T* Lvv_) {
     const long long oo2 = (long long)o * o, ov = (long long)o * v, vv2 = (long long)v * v;
-    THC_TRY(mm(1, (int)oo2, nb, d, rm(Loo_, oo2), Jo, oo2, 1, 1));
-    THC_TRY(mm(1, (int)ov, nb, d, rm(Lov_, ov), Jov_, ov, 1, 1));
-    THC_TRY(mm(1, (int)ov, nb, d, rm(Lvo_, ov), Jvo_, ov, 1, 1));
-    THC_TRY(mm(1, (int)vv2, nb, d, rm(Lvv_, vv2), Jv, vv2, 1, 1));
-    THC_TRY(mm(o, o, o, rm(Loo_, o), rm(Loo_, o), Xo, o, 1, 1, nb, oo2, oo2, 0, true));
-    THC_TRY(mm(o, v, o, rm(Loo_, o), rm(Lov_, v), Xov_, v, 1, 1, nb, oo2, ov, 0, true));
-    THC_TRY(mm(v, o, o, rm(Lvo_, o), rm(Loo_, o), Xvo_, o, 1, 1, nb, ov, oo2, 0, true));
-    THC_TRY(mm(v, v, o, rm(Lvo_, o), rm(Lov_, v), Xv, v, 1, 1, nb, ov, ov, 0, true));
+    const T* tp = t1.p;
+    // delta^A = sum_ia L_ia^A t_i^a
+    THC_TRY(mm(nb, 1, (int)ov, rm(Lov_, ov), View<T>{tp, 1, 0}, dtr.p, 1, 1, 0));
+    View<T> d{dtr.p, 0, 1};
+    THC_TRY(mm(1, (int)oo2, nb, d, rm(Loo_, oo2), Joo.p, oo2, 1, 1));
+    THC_TRY(mm(1, (int)ov, nb, d, rm(Lov_, ov), Jov.p, ov, 1, 1));
+    THC_TRY(mm(1, (int)ov, nb, d, rm(Lvo_, ov), Jvo.p, ov, 1, 1));
+    THC_TRY(mm(1, (int)vv2, nb, d, rm(Lvv_, vv2), Jvv.p, vv2, 1, 1));
+    // W_o^A = L^_ov^A t1^T (o x o),  W_v^A = L^_vv^A t1^T (v x o)
+    THC_TRY(mm(o, o, v, rm(Lov_, v), tr(tp, v), Wfo.p, o, 1, 0, nb, ov, 0, oo2));
+    THC_TRY(mm(v, o, v, rm(Lvv_, v), tr(tp, v), Wfv.p, o, 1, 0, nb, vv2, 0, ov));
+    THC_TRY(mm(o, o, o, rm(Wfo.p, o), rm(Loo_, o), Xoo.p, o, 1, 1, nb, oo2, oo2, 0, true));
+    THC_TRY(mm(o, v, o, rm(Wfo.p, o), rm(Lov_, v), Xov.p, v, 1, 1, nb, oo2, ov, 0, true));
+    THC_TRY(mm(v, o, o, rm(Wfv.p, o), rm(Loo_, o), Xvo.p, o, 1, 1, nb, ov, oo2, 0, true));
+    THC_TRY(mm(v, v, o, rm(Wfv.p, o), rm(Lov_, v), Xvv.p, v, 1, 1, nb, ov, ov, 0, true));
     return Err{};
 }
 
@@ -318,9 +331,9 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(Abar.alloc((size_t)P * K));
     THC_TRY(Q.alloc((size_t)P * K));
     THC_TRY(Wq.alloc((size_t)P * K));
-    for (DBuf<T>* b : {&Joo, &Xoo, &Foo, &hh_oo}) THC_TRY(b->alloc((size_t)o * o));
-    for (DBuf<T>* b : {&Jov, &Xov, &Fov, &Jvo, &Xvo, &Fvo, &hh_vo}) THC_TRY(b->alloc(ov));
-    for (DBuf<T>* b : {&Jvv, &Xvv, &Fvv, &hh_vv}) THC_TRY(b->alloc((size_t)v * v));
+    for (DBuf<T>* b : {&Joo, &Xoo, &Foo}) THC_TRY(b->alloc((size_t)o * o));
+    for (DBuf<T>* b : {&Jov, &Xov, &Fov, &Jvo, &Xvo, &Fvo, &E1}) THC_TRY(b->alloc(ov));
+    for (DBuf<T>* b : {&Jvv, &Xvv, &Fvv}) THC_TRY(b->alloc((size_t)v * v));
     for (DBuf<T>* b : {&ST, &E9, &V9, &O9}) THC_TRY(b->alloc(PP));
     THC_TRY(M9.alloc((size_t)n * P));
     THC_TRY(FvoT.alloc(ov));
@@ -329,6 +342,8 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(Lh_vv.alloc(kbl * v * v));
     THC_TRY(Lh_vo.alloc(kbl * ov));
     THC_TRY(dtr.alloc(kbl));
+    THC_TRY(Wfo.alloc(kbl * o * o));
+    THC_TRY(Wfv.alloc(kbl * ov));
     THC_TRY(M1.alloc(kbl * o * P));
     THC_TRY(N1.alloc(kbl * v * P));
     THC_TRY(M2.alloc(kbl * v * P));
@@ -341,35 +356,24 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(D8.alloc(kbl * ov));
     THC_TRY(Mo.alloc((size_t)K * o * o));
 
-    // ---- core Hamiltonian  h = diag(eps) - (2 J - X)  from undressed blocks
-    THC_TRY(h.alloc(nn));
-    THC_TRY(hoo.alloc((size_t)o * o));
-    THC_TRY(hov.alloc(ov));
-    THC_TRY(hvo.alloc(ov));
-    THC_TRY(hvv.alloc((size_t)v * v));
-    for (DBuf<T>* b : {&Joo, &Jov, &Jvo, &Jvv, &Xoo, &Xov, &Xvo, &Xvv})
-        THC_CUDA(cudaMemsetAsync(b->p, 0, b->n * sizeof(T), st));
-    for (int A0 = 0; A0 < K; A0 += kb) {
-        int nb = std::min(kb, K - A0);
-        THC_CUDA(transpose_batched(Lov.p + A0 * ov, Lh_vo.p, nb, o, v, st));
-        THC_TRY(fock_slab(nb, false, Joo.p, Jov.p, Jvo.p, Jvv.p, Xoo.p, Xov.p, Xvo.p, Xvv.p,
-                          Loo.p + (long long)A0 * o * o, Lov.p + A0 * ov, Lh_vo.p,
-                          Lvv.p + (long long)A0 * v * v));
-    }
+    // ---- canonical Fock operator f = diag(eps): the reference is canonical
+    // Hartree-Fock, and the core Hamiltonian it implies (h = f - 2 J + X) is
+    // never formed (see fock_slab).
+    THC_TRY(foo.alloc((size_t)o * o));
+    THC_TRY(fvv.alloc((size_t)v * v));
+    THC_TRY(epsT.alloc(n));
     {
         std::vector<double> eps(n);
         THC_CUDA(cudaMemcpy(eps.data(), eps_o, sizeof(double) * o, cudaMemcpyDefault));
         THC_CUDA(cudaMemcpy(eps.data() + o, eps_v, sizeof(double) * v, cudaMemcpyDefault));
         eps_h = eps;
-        std::vector<T> foo((size_t)o * o, T(0)), fvv((size_t)v * v, T(0));
-        for (int i = 0; i < o; ++i) foo[(size_t)i * o + i] = (T)eps[i];
-        for (int a = 0; a < v; ++a) fvv[(size_t)a * v + a] = (T)eps[o + a];
-        THC_CUDA(cudaMemcpyAsync(hoo.p, foo.data(), sizeof(T) * o * o, cudaMemcpyHostToDevice, st));
-        THC_CUDA(cudaMemcpyAsync(hvv.p, fvv.data(), sizeof(T) * v * v, cudaMemcpyHostToDevice, st));
-        THC_CUDA(lincomb(hoo.p, (long long)o * o, 1, hoo.p, -2, Joo.p, 1, Xoo.p, st));
-        THC_CUDA(lincomb(hvv.p, (long long)v * v, 1, hvv.p, -2, Jvv.p, 1, Xvv.p, st));
-        THC_CUDA(lincomb(hov.p, ov, -2, Jov.p, 1, Xov.p, 0, (const T*)nullptr, st));
-        THC_CUDA(lincomb(hvo.p, ov, -2, Jvo.p, 1, Xvo.p, 0, (const T*)nullptr, st));
+        std::vector<T> fo((size_t)o * o, T(0)), fv((size_t)v * v, T(0)), et(n);
+        for (int i = 0; i < o; ++i) fo[(size_t)i * o + i] = (T)eps[i];
+        for (int a = 0; a < v; ++a) fv[(size_t)a * v + a] = (T)eps[o + a];
+        for (int p = 0; p < n; ++p) et[p] = (T)eps[p];
+        THC_CUDA(cudaMemcpyAsync(foo.p, fo.data(), sizeof(T) * o * o, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(fvv.p, fv.data(), sizeof(T) * v * v, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(epsT.p, et.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
         THC_CUDA(cudaStreamSynchronize(st));
     }
 
@@ -640,10 +644,6 @@ Err Engine<T>::residual_dev(bool want_energy) {
     for (DBuf<T>* b : {&xoo, &xvv, &Ccross, &Joo, &Jov, &Jvo, &Jvv, &Xoo, &Xov, &Xvo, &Xvv})
         THC_CUDA(cudaMemsetAsync(b->p, 0, b->n * sizeof(T), st));
 
-    // Dressed core Hamiltonian (one "vector" of the dressing routine).
-    seg_begin(THC_STEP_DRESS);
-    THC_TRY(dress(hoo.p, hov.p, hvv.p, 1, hh_oo.p, hh_vv.p, hh_vo.p));
-
     // ---- fused Cholesky-slab pass: Algs. 1, 2, 3, 8 and the Fock matrix
     for (int A0 = 0; A0 < K; A0 += kb) {
         const int nb = std::min(kb, K - A0);
@@ -651,8 +651,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
         seg_begin(THC_STEP_DRESS);
         THC_TRY(dress(Loo.p + A0 * oo2, Lov_s, Lvv.p + A0 * vv2, nb, Lh_oo.p, Lh_vv.p, Lh_vo.p));
         seg_begin(THC_STEP_FOCK);
-        THC_TRY(fock_slab(nb, true, Joo.p, Jov.p, Jvo.p, Jvv.p, Xoo.p, Xov.p, Xvo.p, Xvv.p,
-                          Lh_oo.p, Lov_s, Lh_vo.p, Lh_vv.p));
+        THC_TRY(fock_slab(nb, Lh_oo.p, Lov_s, Lh_vo.p, Lh_vv.p));
         seg_begin(THC_STEP_ALG1);
         // Alg. 1: Bbar^XY = sum_ik y_i^X l_ki y_k^Y, Btil^XY = sum_ac y_a^X l_ac y_c^Y,
         // C = v o Bbar - o o Btil, sigma += C T C^T.  Alg. 3: Ccross += Bbar o Btil.
@@ -689,11 +688,12 @@ Err Engine<T>::residual_dev(bool want_energy) {
     THC_TRY(mm(P, P, P, rm(ST.p, P), tr(Ccross.p, P), sgm, P, -1, 1));
     THC_TRY(mm(P, P, P, rm(Ccross.p, P), tr(ST.p, P), sgm, P, -1, 1));
 
-    // Dressed Fock matrix  F^ = h^ + 2 J - X
-    THC_CUDA(lincomb(Foo.p, oo2, 1, hh_oo.p, 2, Joo.p, -1, Xoo.p, st));
-    THC_CUDA(lincomb(Fov.p, ov, 1, hov.p, 2, Jov.p, -1, Xov.p, st));
-    THC_CUDA(lincomb(Fvo.p, ov, 1, hh_vo.p, 2, Jvo.p, -1, Xvo.p, st));
-    THC_CUDA(lincomb(Fvv.p, vv2, 1, hh_vv.p, 2, Jvv.p, -1, Xvv.p, st));
+    // Dressed Fock matrix  F^ = dress(f) + 2 J - X  (see fock_slab)
+    THC_CUDA(eps_t1(epsT.p, t1.p, o, v, E1.p, st));
+    THC_CUDA(lincomb(Foo.p, oo2, 1, foo.p, 2, Joo.p, -1, Xoo.p, st));
+    THC_CUDA(lincomb(Fov.p, ov, 2, Jov.p, -1, Xov.p, 0, (const T*)nullptr, st));
+    THC_CUDA(lincomb(Fvo.p, ov, 1, E1.p, 2, Jvo.p, -1, Xvo.p, st));
+    THC_CUDA(lincomb(Fvv.p, vv2, 1, fvv.p, 2, Jvv.p, -1, Xvv.p, st));
 
     // Alg. 9: E = o o (y_v^T Fb_vv y_v) - v o (y_o^T Fb_oo^T y_o), sigma += E B^T + B E^T
     THC_CUDA(lincomb(xoo.p, oo2, 1, Foo.p, 1, xoo.p, 0, (const T*)nullptr, st));

@@ -79,8 +79,8 @@ struct Engine {
     // Fixed data (storage type T unless noted).
     DBuf<T> y, x, z;                        // n x P, n x G, G x G
     DBuf<T> Loo, Lov, Lvv;                  // K x o x o, K x o x v, K x v x v (undressed)
-    DBuf<T> h;                              // n x n core Hamiltonian (blocks below)
-    DBuf<T> hoo, hov, hvo, hvv;
+    DBuf<T> foo, fvv;                       // diagonal Fock blocks diag(eps_o), diag(eps_v)
+    DBuf<T> epsT;                           // n orbital energies
     DBuf<T> oo, vv, S;                      // P x P
     DBuf<T> KRy, KRx;                       // (o v) x P, (o v) x G
     DBuf<T> Atil;                           // P x K   (Alg. 2 line 6 / Alg. 8 line 6)
@@ -103,9 +103,9 @@ struct Engine {
     Err check_timeout();
     std::vector<double> eps_h;              // orbital energies (host copy)
     DBuf<T> xoo, xvv, Ccross, Abar, Q;      // o x o, v x v, P x P, P x K, P x K
-    DBuf<T> Joo, Jov, Jvo, Jvv, Xoo, Xov, Xvo, Xvv;  // Coulomb / exchange Fock parts
+    DBuf<T> Joo, Jov, Jvo, Jvv, Xoo, Xov, Xvo, Xvv;  // t1 parts of the Fock matrix
     DBuf<T> Foo, Fov, Fvo, Fvv;             // dressed Fock blocks
-    DBuf<T> hh_oo, hh_vo, hh_vv;            // dressed core Hamiltonian blocks
+    DBuf<T> E1;                             // v x o: (eps_a - eps_i) t_i^a
     DBuf<T> ST, E9, V9, O9, M9, Wq;         // P x P and n x P work
     DBuf<T> FvoT, Ta0;
     DBuf<double> red;                       // reduction scratch
@@ -113,7 +113,7 @@ struct Engine {
     DBuf<unsigned long long> chk;           // symmetry / finiteness check results
 
     // Slab scratch.
-    DBuf<T> Lh_oo, Lh_vv, Lh_vo, dtr;
+    DBuf<T> Lh_oo, Lh_vv, Lh_vo, dtr, Wfo, Wfv;
     DBuf<T> M1, Bbar, N1, Btil, C1, D1, M2, M3, E, TA, W, M4, D8, M5, Mo;
 
     // Alg. 6 scratch.
@@ -146,9 +146,7 @@ struct Engine {
            long long sBb = 0, long long sCb = 0, bool reduce = false);
     Err dress(const T* oo_, const T* ov_, const T* vv_, int nb, T* out_oo, T* out_vv,
               T* out_vo);
-    Err fock_slab(int nb, bool dressed, T* Jo, T* Jov_, T* Jvo_, T* Jv, T* Xo, T* Xov_,
-                  T* Xvo_, T* Xv, const T* Loo_, const T* Lov_, const T* Lvo_,
-                  const T* Lvv_);
+    Err fock_slab(int nb, const T* Loo_, const T* Lov_, const T* Lvo_, const T* Lvv_);
     Err d_operator(const T* M, int nb, T* Dout);
     Err alg6(T* sgm);
     Err alg7(T* sgm);

@@ -114,6 +114,16 @@ __global__ void k_w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W,
 }
 
 template <typename T>
+__global__ void k_eps_t1(const T* eps, const T* t1, int o, int v, T* out) {
+    const long long tot = (long long)o * v;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(e / o), i = (int)(e % o);
+        out[e] = (eps[o + a] - eps[i]) * t1[(long long)i * v + a];
+    }
+}
+
+template <typename T>
 __global__ void k_traces(const T* M, int n, int nb, T* d) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nb) return;
@@ -731,6 +741,13 @@ cudaError_t w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P
 }
 
 template <typename T>
+cudaError_t eps_t1(const T* eps, const T* t1, int o, int v, T* out, cudaStream_t s) {
+    k_eps_t1<T><<<nblocks((long long)o * v), NT, 0, s>>>(eps, t1, o, v, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s) {
     k_traces<T><<<cdiv(nb, 128), 128, 0, s>>>(M, n, nb, d);
     count_launches(1);
@@ -863,6 +880,7 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
     template cudaError_t w_single<T>(const T*, int, const T*, const T*, T*, int, int,  \
                                      cudaStream_t);                                     \
     template cudaError_t traces<T>(const T*, int, int, T*, cudaStream_t);               \
+    template cudaError_t eps_t1<T>(const T*, const T*, int, int, T*, cudaStream_t);     \
     template cudaError_t lincomb<T>(T*, long long, double, const T*, double, const T*, \
                                     double, const T*, cudaStream_t);                    \
     template cudaError_t hadamard2<T>(T*, long long, const T*, const T*, const T*,     \

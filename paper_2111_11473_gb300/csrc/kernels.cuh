@@ -41,6 +41,11 @@ template <typename T>
 cudaError_t w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P,
                      int nb, cudaStream_t s);
 
+// out[a][i] = (eps[o + a] - eps[i]) t1[i][a]   (v x o; the orbital-energy part
+// of the T1-dressed diagonal Fock matrix, block (a, i)).
+template <typename T>
+cudaError_t eps_t1(const T* eps, const T* t1, int o, int v, T* out, cudaStream_t s);
+
 // d[a] = trace(M[a]) for nb n x n matrices.
 template <typename T>
 cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s);
