@@ -28,7 +28,6 @@ namespace {
 constexpr int BM = 128;          // UMMA M (rows of the accumulator)
 constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of bf16
 constexpr int UK = 16;           // K per tcgen05.mma for 16-bit inputs
-constexpr int STAGES = 3;
 constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -102,24 +101,40 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         : "memory");
 }
 
+// Shared-memory ring depth per tile width (a stage holds the 128 x 64 hi/lo
+// tiles of A and the BN x 64 hi/lo tiles of B).
+template <int BN>
+struct TcStages {
+    static constexpr int value = BN == 128 ? 3 : (BN == 64 ? 4 : 5);
+};
+
 template <int BN>
 struct TcSmem {
-    __nv_bfloat16 a_hi[STAGES][BM * BK];
-    __nv_bfloat16 a_lo[STAGES][BM * BK];
-    __nv_bfloat16 b_hi[STAGES][BN * BK];
-    __nv_bfloat16 b_lo[STAGES][BN * BK];
-    uint64_t full[STAGES];
-    uint64_t empty[STAGES];
-    uint64_t done;
+    static constexpr int ST = TcStages<BN>::value;
+    __nv_bfloat16 a_hi[ST][BM * BK];
+    __nv_bfloat16 a_lo[ST][BM * BK];
+    __nv_bfloat16 b_hi[ST][BN * BK];
+    __nv_bfloat16 b_lo[ST][BN * BK];
+    uint64_t full[ST];
+    uint64_t empty[ST];
+    uint64_t acc_full[2];     // accumulator buffer b holds a finished tile
+    uint64_t acc_empty[2];    // the epilogue has drained accumulator buffer b
+    float epi[4][32 * 33];    // per epilogue warp: a 32 x 32 tile, padded rows
+    uint64_t drain;
     uint32_t tmem;
     int fail;
 };
+
+constexpr int kEpiWarps = 4;
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;   // producer, MMA issuer, epilogue
 
 struct TcArgs {
     int M, N;              // real accumulator rows (UMMA M side) and columns
     int nbo;               // output batches
     int ksteps;            // 64-wide K steps per output batch
     int splits;
+    int mblocks, nblocks;
+    long long ntiles;      // mblocks * nblocks * nbo * splits
     float* C;              // output (or partials when splits > 1)
     long long crs, ccs, cbs;   // C(i, j) of batch b at C[b*cbs + i*crs + j*ccs]
     float alpha, beta;
@@ -128,34 +143,85 @@ struct TcArgs {
     int* err;
 };
 
+struct TileCoord {
+    int m0, n0, bo, split, k_lo, nk;
+};
+
+__device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, long long t, int BN) {
+    TileCoord c;
+    const int nbk = (int)(t % a.nblocks);
+    long long r = t / a.nblocks;
+    const int mbk = (int)(r % a.mblocks);
+    r /= a.mblocks;
+    c.bo = (int)(r / a.splits);
+    c.split = (int)(r % a.splits);
+    c.m0 = mbk * BM;
+    c.n0 = nbk * BN;
+    const int chunk = (a.ksteps + a.splits - 1) / a.splits;
+    c.k_lo = c.split * chunk;
+    c.nk = max(0, min(a.ksteps, c.k_lo + chunk) - c.k_lo);
+    return c;
+}
+
+// Bounded wait that also gives up once another role has failed.
+__device__ __forceinline__ bool mbar_wait_or_fail(uint64_t* bar, uint32_t parity,
+                                                  volatile int* fail) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity));
+        if (done) return true;
+        if (*fail) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch((int*)fail, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent warp-specialised product: warp 0 streams operand tiles with TMA,
+// warp 1 issues the MMAs into one of two tensor-memory accumulators, and
+// warps 2-5 drain the other accumulator to C, so that the epilogue of one
+// tile overlaps the main loop of the next.  Tiles are taken round-robin.
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
               const TcArgs args) {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     // 1024-byte alignment of the tile ring (required by the 128-byte swizzle)
-    TcSmem<BN>& sm = *reinterpret_cast<TcSmem<BN>*>(
-        (reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+    using Sm = TcSmem<BN>;
+    constexpr int ST = Sm::ST;
+    Sm& sm = *reinterpret_cast<Sm*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) &
+                                    ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-    const int bo = blockIdx.z / args.splits, split = blockIdx.z % args.splits;
-    const int chunk = (args.ksteps + args.splits - 1) / args.splits;
-    const int k_lo = split * chunk, k_hi = min(args.ksteps, k_lo + chunk);
-    const int nk = max(0, k_hi - k_lo);
-    constexpr uint32_t kCols = BN < 32 ? 32 : BN;
+    constexpr uint32_t kCols = 2 * BN < 32 ? 32 : 2 * BN;
+    volatile int* fail = &sm.fail;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], 1);
         }
-        mbar_init(&sm.done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm.acc_full[b], 1);
+            mbar_init(&sm.acc_empty[b], kEpiWarps);
+        }
+        mbar_init(&sm.drain, 1);
         sm.fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&sm.tmem)),
                      "r"(kCols));
@@ -164,117 +230,150 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = sm.tmem;
-
     const uint32_t a_bytes = BM * BK * 2, b_bytes = BN * BK * 2;
     const uint32_t stage_bytes = (args.nprod == 3 ? 2 : 1) * (a_bytes + b_bytes);
 
-    if (warp == 0 && lane == 0 && nk > 0) {
-        // TMA producer
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % STAGES;
-            if (i >= STAGES && !mbar_wait(&sm.empty[s], ((i / STAGES) - 1) & 1)) {
-                atomicExch(&sm.fail, 1);
-                break;
-            }
-            if (sm.fail) break;
-            const int kc = (k_lo + i) * BK;
-            mbar_expect_tx(&sm.full[s], stage_bytes);
-            const int ba = args.a_bcast ? 0 : bo, bb = args.b_bcast ? 0 : bo;
-            tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, m0, ba);
-            tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, n0, bb);
-            if (args.nprod == 3) {
-                tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, m0, ba);
-                tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, n0, bb);
-            }
-        }
-    } else if (warp == 1 && lane == 0 && nk > 0) {
-        // MMA issuer
-        const uint32_t idesc = instr_desc(BM, BN);
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % STAGES;
-            if (!mbar_wait(&sm.full[s], (i / STAGES) & 1)) {
-                atomicExch(&sm.fail, 1);
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t ah = smem_u32(sm.a_hi[s]), bh = smem_u32(sm.b_hi[s]);
-            const uint32_t al = smem_u32(sm.a_lo[s]), bl = smem_u32(sm.b_lo[s]);
-#pragma unroll
-            for (int kk = 0; kk < BK / UK; ++kk) {
-                const uint32_t off = kk * UK * 2;   // bytes along K inside the swizzle atom
-                const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-                mma_bf16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
-                if (args.nprod == 3) {
-                    mma_bf16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-                    mma_bf16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            long long it = 0;
+            long long last[ST];
+            for (int s = 0; s < ST; ++s) last[s] = -1;
+            for (long long t = blockIdx.x; t < args.ntiles && !*fail; t += gridDim.x) {
+                const TileCoord c = tile_coord(args, t, BN);
+                const int ba = args.a_bcast ? 0 : c.bo, bb = args.b_bcast ? 0 : c.bo;
+                for (int i = 0; i < c.nk; ++i, ++it) {
+                    const int s = (int)(it % ST);
+                    if (it >= ST && !mbar_wait_or_fail(&sm.empty[s], (uint32_t)(((it / ST) - 1) & 1), fail))
+                        break;
+                    const int kc = (c.k_lo + i) * BK;
+                    mbar_expect_tx(&sm.full[s], stage_bytes);
+                    tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, c.m0, ba);
+                    tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, c.n0, bb);
+                    if (args.nprod == 3) {
+                        tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, c.m0, ba);
+                        tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, c.n0, bb);
+                    }
+                    last[s] = it;
                 }
             }
-            mma_commit(&sm.empty[s]);
+            // Every load this thread issued has landed before the CTA exits
+            // (immediate unless a wait above gave up).
+            for (int s = 0; s < ST; ++s)
+                if (last[s] >= 0) mbar_wait(&sm.full[s], (uint32_t)((last[s] / ST) & 1));
         }
-        mma_commit(&sm.done);
-    }
-    __syncwarp();
-
-    // Epilogue: warp w owns accumulator rows 32w .. 32w+31.
-    if (nk > 0 && !mbar_wait(&sm.done, 0)) atomicExch(&sm.fail, 1);
-    __syncthreads();
-    const bool ok = sm.fail == 0;   // uniform across the block
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // The operand ring is idle now (every load was consumed by an MMA that
-    // completed before `done`): stage the 128 x BN accumulator tile there and
-    // write it out along whichever index of C is contiguous.
-    float* stage = reinterpret_cast<float*>(&sm.a_hi[0][0]);
-    constexpr int LDS_ = BN + 1;
-    float* Cb = args.C + (long long)bo * args.cbs +
-                (args.splits > 1 ? (long long)split * args.nbo * args.cbs : 0);
-    if (ok) {
-        const int rl = warp * 32 + lane;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = instr_desc(BM, BN);
+            long long it = 0;
+            int tl = 0;
+            for (long long t = blockIdx.x; t < args.ntiles && !*fail; t += gridDim.x, ++tl) {
+                const TileCoord c = tile_coord(args, t, BN);
+                const int buf = tl & 1;
+                if (tl >= 2 && !mbar_wait_or_fail(&sm.acc_empty[buf], (uint32_t)(((tl >> 1) - 1) & 1), fail))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t dst = tmem + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int i = 0; i < c.nk; ++i, ++it) {
+                    const int s = (int)(it % ST);
+                    if (!mbar_wait_or_fail(&sm.full[s], (uint32_t)((it / ST) & 1), fail)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t ah = smem_u32(sm.a_hi[s]), bh = smem_u32(sm.b_hi[s]);
+                    const uint32_t al = smem_u32(sm.a_lo[s]), bl = smem_u32(sm.b_lo[s]);
+#pragma unroll
+                    for (int kk = 0; kk < BK / UK; ++kk) {
+                        const uint32_t off = kk * UK * 2;   // bytes along K inside the swizzle atom
+                        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(dst, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
+                        if (args.nprod == 3) {
+                            mma_bf16(dst, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+                            mma_bf16(dst, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+                        }
+                    }
+                    mma_commit(&sm.empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&sm.acc_full[buf]);
+            }
+            // All MMAs this thread issued have completed before TMEM is freed.
+            mma_commit(&sm.drain);
+            mbar_wait(&sm.drain, 0);
+        }
+    } else {
+        // Epilogue: warp w reads accumulator lanes 32 (w % 4) .. 32 (w % 4) + 31
+        // in 32-column chunks; a row-major C is written through a shared-memory
+        // transpose so that every store instruction covers one 128-byte row.
+        const int q = warp & 3;
+        float* stg = sm.epi[q];
+        int tl = 0;
+        for (long long t = blockIdx.x; t < args.ntiles; t += gridDim.x, ++tl) {
+            const TileCoord c = tile_coord(args, t, BN);
+            const int buf = tl & 1;
+            if (!mbar_wait_or_fail(&sm.acc_full[buf], (uint32_t)((tl >> 1) & 1), fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            float* Cb = args.C + (long long)c.bo * args.cbs +
+                        (args.splits > 1 ? (long long)c.split * args.nbo * args.cbs : 0);
+            const int i_base = c.m0 + q * 32;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            if (nk > 0) {
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c0);
                 asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32"
-                    " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+                    " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
                       "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+                      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+                      "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            } else {
+                const int j0 = c.n0 + c0;
+                auto put = [&](float* p, float val) {
+                    if (args.splits > 1) *p = val;
+                    else *p = args.beta != 0.f ? fmaf(args.beta, *p, args.alpha * val) : args.alpha * val;
+                };
+                if (args.ccs == 1) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) r[j] = 0u;
+                    for (int j = 0; j < 32; ++j)
+                        stg[lane * 33 + j] = c.nk > 0 ? __uint_as_float(r[j]) : 0.f;
+                    __syncwarp();
+                    const int j = j0 + lane;
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int i = i_base + rr;
+                        if (i < args.M && j < args.N)
+                            put(Cb + (long long)i * args.crs + j, stg[rr * 33 + lane]);
+                    }
+                    __syncwarp();
+                } else {
+                    const int i = i_base + lane;
+                    if (i < args.M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j0 + j >= args.N) break;
+                            put(Cb + (long long)i * args.crs + (long long)(j0 + j) * args.ccs,
+                                c.nk > 0 ? __uint_as_float(r[j]) : 0.f);
+                        }
+                    }
+                }
             }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) stage[rl * LDS_ + c0 + j] = __uint_as_float(r[j]);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acc_empty[buf]);
         }
     }
     __syncthreads();
-    if (ok) {
-        auto put = [&](int i, int j, float v) {
-            float* c = Cb + (long long)(m0 + i) * args.crs + (long long)(n0 + j) * args.ccs;
-            if (args.splits > 1) *c = v;
-            else *c = args.beta != 0.f ? fmaf(args.beta, *c, args.alpha * v) : args.alpha * v;
-        };
-        if (args.ccs == 1) {
-            for (int i = warp; i < BM; i += 4) {
-                if (m0 + i >= args.M) break;
-                for (int j = lane; j < BN; j += 32)
-                    if (n0 + j < args.N) put(i, j, stage[i * LDS_ + j]);
-            }
-        } else {
-            for (int j = warp; j < BN; j += 4) {
-                if (n0 + j >= args.N) break;
-                for (int i = lane; i < BM; i += 32)
-                    if (m0 + i < args.M) put(i, j, stage[i * LDS_ + j]);
-            }
-        }
-    }
-    if (!ok && threadIdx.x == 0) atomicExch(args.err, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
+    if (sm.fail && threadIdx.x == 0) atomicExch(args.err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                      "r"(kCols));
 }
@@ -360,9 +459,11 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long Ktot
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+int g_sms = 0;
+std::once_flag g_sms_once;
+
 template <int BN>
-cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, int mblocks, int nblocks,
-                      cudaStream_t s) {
+cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) {
     const int smem = (int)sizeof(TcSmem<BN>) + 1024;
     static bool attr = false;
     if (!attr) {
@@ -371,8 +472,15 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, int mblocks, int
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid(nblocks, mblocks, a.nbo * a.splits);
-    k_gemm_tc<BN><<<grid, 128, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    std::call_once(g_sms_once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            g_sms = 0;
+    });
+    const long long sms = g_sms > 0 ? g_sms : 152;
+    const unsigned grid = (unsigned)std::min<long long>(a.ntiles, sms);
+    k_gemm_tc<BN><<<grid, kTcThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -460,6 +568,9 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
         while (splits > 1 && (size_t)(per * nbo * splits) > ws.partial_elems) --splits;
     }
     a.splits = splits;
+    a.mblocks = mblocks;
+    a.nblocks = nblocks;
+    a.ntiles = tiles * splits;
     if (splits > 1) {
         a.C = ws.partial;
         a.crs = Nr;
@@ -471,9 +582,9 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
         a.ccs = ccs;
         a.cbs = g.reduce ? 0 : g.sCb;
     }
-    if (BN == 32) e = launch_tc<32>(maps, a, mblocks, nblocks, s);
-    else if (BN == 64) e = launch_tc<64>(maps, a, mblocks, nblocks, s);
-    else e = launch_tc<128>(maps, a, mblocks, nblocks, s);
+    if (BN == 32) e = launch_tc<32>(maps, a, s);
+    else if (BN == 64) e = launch_tc<64>(maps, a, s);
+    else e = launch_tc<128>(maps, a, s);
     if (e != cudaSuccess) return e;
     if (splits > 1) {
         const long long total = (long long)Mr * Nr * nbo;
