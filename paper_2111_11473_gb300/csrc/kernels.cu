@@ -460,6 +460,32 @@ __device__ __forceinline__ float4 tri_lds4(unsigned tile, int r, int chunk) {
     return v;
 }
 
+// Packed float pairs for the FP32x2 FMA path (fma.rn.f32x2 issues two
+// float32 FMAs as one instruction; the FMA pipe rate is unchanged, the issue
+// slots are halved).
+__device__ __forceinline__ unsigned long long tri_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void tri_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long tri_mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long tri_fma2(unsigned long long a, unsigned long long b,
+                                                       unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 __global__ void __launch_bounds__(256, 1)
     k_triangle_f32_tma(float* H, const __grid_constant__ CUtensorMap tmE,
                        const __grid_constant__ CUtensorMap tmF,
@@ -500,13 +526,15 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0)
         for (; next < TSTG - 1 && next < nst; ++next) issue(next);
 
-    float acc[4][8][4];
+    // Accumulators as packed float pairs along Z: acc[j][y][zp] holds
+    // (Z, Z + 1) = (z_base + 2 zp, z_base + 2 zp + 1) of row (X_j, Y_y).
+    unsigned long long acc[4][8][2];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int y = 0; y < 8; ++y)
 #pragma unroll
-            for (int z = 0; z < 4; ++z) acc[j][y][z] = 0.f;
+            for (int zp = 0; zp < 2; ++zp) acc[j][y][zp] = 0ull;
 
     for (int k = 0; k < nst; ++k) {
         const int s = k % TSTG;
@@ -540,6 +568,14 @@ __global__ void __launch_bounds__(256, 1)
             const unsigned ey_t = tri_su32(sm.ey[s][ii]), ez_t = tri_su32(sm.ez[s][ii]);
             const unsigned fy_t = tri_su32(sm.fy[s][ii]), fz_t = tri_su32(sm.fz[s][ii]);
             const unsigned g_t = tri_su32(sm.g[s][ii]);
+            // G^YZ of the thread's 8 Y x 4 Z, loaded once for its four X rows.
+            unsigned long long g2[8][2];
+#pragma unroll
+            for (int y = 0; y < 8; ++y) {
+                const float4 g4 = tri_lds4(g_t, y_base + y, zc);
+                g2[y][0] = tri_pack(g4.x, g4.y);
+                g2[y][1] = tri_pack(g4.z, g4.w);
+            }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int xr = lx + 8 * j;
@@ -548,17 +584,18 @@ __global__ void __launch_bounds__(256, 1)
                 const float4 ez4 = tri_lds4(ez_t, xr, zc), fz4 = tri_lds4(fz_t, xr, zc);
                 const float ey[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
                 const float fy[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-                const float ez[4] = {ez4.x, ez4.y, ez4.z, ez4.w};
-                const float fz[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
+                const unsigned long long ez2[2] = {tri_pack(ez4.x, ez4.y), tri_pack(ez4.z, ez4.w)};
+                const unsigned long long fz2[2] = {tri_pack(fz4.x, fz4.y), tri_pack(fz4.z, fz4.w)};
 #pragma unroll
                 for (int y = 0; y < 8; ++y) {
-                    const float4 g4 = tri_lds4(g_t, y_base + y, zc);
-                    const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+                    const unsigned long long eb = tri_pack(ey[y], ey[y]);
+                    const unsigned long long fb = tri_pack(fy[y], fy[y]);
 #pragma unroll
-                    for (int z = 0; z < 4; ++z) {
-                        float t = ey[y] * fz[z];
-                        t = fmaf(ez[z], fy[y], t);
-                        acc[j][y][z] = fmaf(t, g[z], acc[j][y][z]);
+                    for (int zp = 0; zp < 2; ++zp) {
+                        // t = E^XY F^XZ + E^XZ F^XY, H += t G^YZ  (two Z at once)
+                        unsigned long long t = tri_mul2(eb, fz2[zp]);
+                        t = tri_fma2(ez2[zp], fb, t);
+                        acc[j][y][zp] = tri_fma2(t, g2[y][zp], acc[j][y][zp]);
                     }
                 }
             }
@@ -582,15 +619,18 @@ __global__ void __launch_bounds__(256, 1)
             const int Y = Y0 + y_base + y;
             if (Y >= P) continue;
             const int Zb = Z0 + zc * 4;
+            float a[4];
+            tri_unpack(acc[j][y][0], a[0], a[1]);
+            tri_unpack(acc[j][y][1], a[2], a[3]);
             float* h = H + ((long long)X * P + Y) * P + Zb;
             if (Zb + 3 < P) {
                 float4 v = *reinterpret_cast<float4*>(h);
-                v.x += acc[j][y][0]; v.y += acc[j][y][1]; v.z += acc[j][y][2]; v.w += acc[j][y][3];
+                v.x += a[0]; v.y += a[1]; v.z += a[2]; v.w += a[3];
                 *reinterpret_cast<float4*>(h) = v;
             } else {
 #pragma unroll
                 for (int z = 0; z < 4; ++z)
-                    if (Zb + z < P) h[z] += acc[j][y][z];
+                    if (Zb + z < P) h[z] += a[z];
             }
         }
     }
