@@ -36,9 +36,21 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(o=40, v=200, P=400, G=1200, K=600, seed=1)
-WORKLOAD_NAME = "THC-RR-CCSD o=40 v=200 P=400 G=1200 K=600 seed=1"
-METRIC = "residual evals/s (THC-RR-CCSD, o=40 v=200 P=400 G=1200 K=600)"
+DEFAULT_WORKLOAD = "o40_v200_P400_G1200_K600"
+WORKLOAD = WORKLOAD_NAME = METRIC = None
+
+
+def set_workload(name):
+    """Select one of synth.CONFIGS (named by size) as the benchmarked system."""
+    global WORKLOAD, WORKLOAD_NAME, METRIC
+    from synth import CONFIGS
+    o, v, P, G, K, seed = CONFIGS[name]
+    WORKLOAD = dict(o=o, v=v, P=P, G=G, K=K, seed=seed)
+    WORKLOAD_NAME = f"THC-RR-CCSD o={o} v={v} P={P} G={G} K={K} seed={seed}"
+    METRIC = f"residual evals/s (THC-RR-CCSD, o={o} v={v} P={P} G={G} K={K})"
+
+
+set_workload(DEFAULT_WORKLOAD)
 UNIT = "residual evals/s"
 
 
@@ -167,6 +179,13 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
+    if args.workload != DEFAULT_WORKLOAD:
+        # The oracle forms the 4-index amplitudes and integrals (o^2 v^2 and
+        # v^4 doubles): beyond the default size they do not fit host memory.
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the FP64 oracle forms 4-index tensors that do not fit host memory "
+                          "at this size"}), flush=True)
+        return 0
     import numpy as np
     from synth import random_amplitudes
     s = _system()
@@ -210,9 +229,26 @@ def _rate(ctx, Zc, t1, sig, sig1, stream, dev, steps=5, warmup=3):
     return 1e3 * steps / e0.elapsed_time(e1)
 
 
+def fp64_vs_mixed_iterations(pkg, s, stream, n_iter):
+    """Energy of the float64 and of the mixed-precision solve from zero,
+    iteration by iteration (each on its own trajectory), and their difference."""
+    out = {}
+    for name, prec in (("fp64", pkg.THC_PREC_FP64), ("mixed", pkg.THC_PREC_MIXED)):
+        with pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z, precision=prec,
+                         stream=stream) as c:
+            hist = []
+            c.solve(r_tol=0.0, max_iter=n_iter, history=hist, raise_on_failure=False)
+            out[name] = [h[0] for h in hist]
+            out[name + "_seconds"] = [h[2] for h in hist]
+    out["energy_diff_per_iteration"] = [m - f for f, m in zip(out["fp64"], out["mixed"])]
+    return out
+
+
 def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     """Solves from zero: float64, mixed precision, and mixed precision with the
-    learned preconditioner; time to 1e-6 Eh of the float64 converged energy."""
+    learned preconditioner; time to 1e-6 Eh of the float64 converged energy
+    (of the plain mixed solve's converged energy when the float64 solve is
+    skipped, at sizes where it would take too long)."""
     import numpy as np
     import torch
     from paper_2111_11473_gb300 import precond
@@ -222,10 +258,11 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     if prec != pkg.THC_PREC_FP64:
         fp64_ctx = pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z,
                                precision=pkg.THC_PREC_FP64, stream=stream)
-    f = precond.run_solve(fp64_ctx, None, None, r_tol=1e-8, max_iter=60)
-    e_ref = f["energy"]
-    f["evals_per_s"] = None
-    out["fp64"] = f
+    f = None
+    if not args.skip_fp64_solve:
+        f = precond.run_solve(fp64_ctx, None, None, r_tol=1e-8, max_iter=60)
+        f["evals_per_s"] = None
+        out["fp64"] = f
     if fp64_ctx is not ctx:
         fp64_ctx.close()
     # Mixed precision: residual rate on the bench state, then solves.
@@ -237,11 +274,14 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
     sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
     mrate = _rate(mctx, Zc, t1, sig, sig1, stream, dev)
+    e_ref = f["energy"] if f is not None else None
     # The mixed-precision residual has a floor near 5e-6 at this size (the
     # bf16x3 products' rounding): the mixed solves stop at |r| < 1e-5 once
     # the energy changes by less than 1e-8 Eh per iteration.
     m = precond.run_solve(mctx, e_ref, None, r_tol=1e-5, max_iter=60, stop_de=1e-8)
     m["evals_per_s"] = mrate
+    if e_ref is None:
+        e_ref = m["energy"]
     out["mixed"] = m
     # Learned preconditioner: pairs from small systems of the same family
     # (v = 5o, P = 10o, G = 30o, K = 15o), trained on the GPU.
@@ -267,8 +307,9 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     net.close()
     if mctx is not ctx:
         mctx.close()
-    t_ref = f["time_to_e_tol_s"]
+    t_ref = f["time_to_e_tol_s"] if f is not None else None
     out["e_ref"] = e_ref
+    out["e_ref_source"] = "float64 solve" if f is not None else "plain mixed-precision solve"
     out["speedup_time_to_1e-6_Eh_vs_fp64"] = {
         k: (t_ref / out[k]["time_to_e_tol_s"]
             if t_ref and out[k]["time_to_e_tol_s"] else None)
@@ -285,7 +326,15 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    help="system from synth.CONFIGS (named by size)")
+    ap.add_argument("--skip-fp64-solve", action="store_true",
+                    help="no float64 solve (sizes where it takes too long)")
+    ap.add_argument("--fp64-iters", type=int, default=0,
+                    help="also run this many float64 and mixed iterations from zero "
+                         "and report their energy difference per iteration")
     args = ap.parse_args()
+    set_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -400,9 +449,11 @@ def main():
 
     if not args.no_solve:
         line["solve"] = solve_variants(pkg, s, dev, stream, ctx, args, prec)
+    if args.fp64_iters > 0:
+        line["fp64_vs_mixed"] = fp64_vs_mixed_iterations(pkg, s, stream, args.fp64_iters)
     ctx.close()
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:
         sec = oracle_residual_seconds(s, Zc0, t10)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _threads(),
                                 "kind": "oracle",

@@ -159,7 +159,7 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
         // Large products go to the tensor cores; the rest stays on the CUDA
         // cores (also if the packed operands do not fit the workspace).
         if (tc_products > 0 && fl >= 3.0e7 && Kd >= 16) {
-            cudaError_t e = gemm_tc(g, tcws, tc_products, st);
+            cudaError_t e = gemm_tc(g, tcws, tc_products, st, &pcache);
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
         }
@@ -489,6 +489,12 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         tcws.partial = tcpart.p;
         tcws.partial_elems = tcpart.n;
         tcws.err = tcerr.p;
+        // Buffers that keep their contents for the context's lifetime: their
+        // bf16 hi/lo forms are packed once and reused by every residual.
+        if constexpr (std::is_same<T, float>::value) {
+            for (DBuf<T>* b : {&y, &x, &z, &oo, &vv, &S, &KRy, &KRx, &Atil, &B6, &U6, &Gall, &Kx})
+                if (b->p) pcache.add_constant(b->p, b->n);
+        }
     }
     THC_CUDA(cudaStreamSynchronize(st));
     return Err{};

@@ -100,6 +100,8 @@ struct Engine {
     DBuf<float> tcpart;                     // tensor-core split-K partials
     DBuf<int> tcerr;                        // bounded-wait expiry flag
     TcWorkspace tcws;
+    PackCache pcache;                       // packed constant operands (float engine)
+    ~Engine() { pcache.release(); }
     Err check_timeout();
     std::vector<double> eps_h;              // orbital energies (host copy)
     DBuf<T> xoo, xvv, Ccross, Abar, Q;      // o x o, v x v, P x P, P x K, P x K

@@ -381,34 +381,58 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // Pack a strided float32 operand into bf16 hi/lo, K-major, padded:
 // out[bo][r][kb*Kp + k] = split(src(b, r, k)), r < Rp, k < Kp, with
 // (bo, kb) = (b, 0) for batched products and (0, b) for batch-reduced ones.
-__global__ void k_pack(const float* src, long long rs, long long ks, long long bs, int R,
-                       int Kd, int nb, int Rp, int Kp, int reduce, __nv_bfloat16* hi,
-                       __nv_bfloat16* lo) {
-    __shared__ float tile[32][33];
+// A 32 (r) x 64 (k) tile goes through shared memory so that the global reads
+// run along whichever index of the source is contiguous, and every thread
+// then writes 8 consecutive k of one row as one 16-byte store of hi and lo.
+constexpr int PK_R = 32, PK_K = 64;
+
+__global__ void __launch_bounds__(256) k_pack(const float* src, long long rs, long long ks,
+                                              long long bs, int R, int Kd, int nb, int Rp, int Kp,
+                                              int reduce, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    __shared__ float tile[PK_R][PK_K + 1];
     const int b = blockIdx.z;
-    const int k0 = blockIdx.x * 32;
+    const int k0 = blockIdx.x * PK_K;
     const float* s = src + (long long)b * bs;
     const bool kfast = ks <= rs;
     const long long Ktot = reduce ? (long long)nb * Kp : Kp;
     const int bo = reduce ? 0 : b, kb = reduce ? b : 0;
-    for (int r0 = blockIdx.y * 32; r0 < Rp; r0 += gridDim.y * 32) {
-        for (int j = threadIdx.y; j < 32; j += 8) {
-            int r, k;
-            if (kfast) { r = r0 + j; k = k0 + threadIdx.x; }
-            else       { r = r0 + threadIdx.x; k = k0 + j; }
-            const float v = (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.f;
-            if (kfast) tile[j][threadIdx.x] = v;
-            else tile[threadIdx.x][j] = v;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int r0 = blockIdx.y * PK_R; r0 < Rp; r0 += gridDim.y * PK_R) {
+        if (kfast) {
+            // warp w reads rows w, w + 8, ...; lanes run along k (two halves of 32)
+            for (int rr = warp; rr < PK_R; rr += 8) {
+                const int r = r0 + rr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = k0 + h * 32 + lane;
+                    tile[rr][h * 32 + lane] =
+                        (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.f;
+                }
+            }
+        } else {
+            // warp w reads columns w, w + 8, ...; lanes run along r
+            for (int kk = warp; kk < PK_K; kk += 8) {
+                const int r = r0 + lane, k = k0 + kk;
+                tile[lane][kk] = (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.f;
+            }
         }
         __syncthreads();
-        for (int j = threadIdx.y; j < 32; j += 8) {
-            const int r = r0 + j, k = k0 + threadIdx.x;
-            if (r >= Rp || k >= Kp) continue;
-            const float v = tile[j][threadIdx.x];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
-            hi[o] = h;
-            if (lo) lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+        {
+            const int rr = t >> 3, oct = t & 7;   // 32 rows x 8 octets of k
+            const int r = r0 + rr, k = k0 + oct * 8;
+            if (r < Rp && k < Kp) {
+                union { __nv_bfloat16 b[8]; uint4 u; } vh, vl;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float v = tile[rr][oct * 8 + e];
+                    const __nv_bfloat16 hh = __float2bfloat16_rn(v);
+                    vh.b[e] = hh;
+                    vl.b[e] = __float2bfloat16_rn(v - __bfloat162float(hh));
+                }
+                const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
+                *reinterpret_cast<uint4*>(hi + o) = vh.u;
+                if (lo) *reinterpret_cast<uint4*>(lo + o) = vl.u;
+            }
         }
         __syncthreads();
     }
@@ -496,7 +520,67 @@ size_t gemm_tc_pack_elems(int M, int N, int K, int batch, bool reduce) {
     return (size_t)(2 * (Rm + Rn) * Kp * batch);
 }
 
-cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cudaStream_t s) {
+void PackCache::release() {
+    for (Entry& e : entries) cudaFree(e.hi);
+    entries.clear();
+    constant.clear();
+    bytes = 0;
+}
+
+namespace {
+
+// Pack one operand, or take it from the cache when its buffer is constant.
+// Returns the hi/lo pointers the tensor maps read.
+cudaError_t pack_operand(const float* p, long long rs, long long cs, long long bs, int R, int Kd,
+                         int nb_eff, int nb_grid, int Rp, int Kp, int reduce, int nprod,
+                         __nv_bfloat16* ws_hi, __nv_bfloat16* ws_lo, PackCache* cache,
+                         cudaStream_t s, __nv_bfloat16** out_hi, __nv_bfloat16** out_lo) {
+    const dim3 grid(cdiv(Kp, PK_K), std::min<unsigned>(cdiv(Rp, PK_R), 65535), nb_grid);
+    if (cache && cache->is_constant(p)) {
+        for (const PackCache::Entry& e : cache->entries)
+            if (e.p == p && e.rs == rs && e.cs == cs && e.bs == bs && e.R == R && e.Kd == Kd &&
+                e.nb == nb_eff && e.Rp == Rp && e.Kp == Kp && e.reduce == reduce &&
+                e.nprod == nprod) {
+                *out_hi = e.hi;
+                *out_lo = e.lo;
+                return cudaSuccess;
+            }
+        const long long Ktot = reduce ? (long long)nb_eff * Kp : Kp;
+        const size_t elems = (size_t)Rp * Ktot * (reduce ? 1 : nb_grid);
+        const size_t bytes = elems * 2 * (nprod == 3 ? 2 : 1);
+        if (cache->bytes + bytes <= cache->budget) {
+            __nv_bfloat16* buf = nullptr;
+            if (cudaMalloc(&buf, bytes) == cudaSuccess) {
+                PackCache::Entry e{p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, nprod, buf,
+                                   nprod == 3 ? buf + elems : nullptr};
+                k_pack<<<grid, 256, 0, s>>>(p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, e.hi,
+                                            e.lo);
+                count_launches(1);
+                cudaError_t err = cudaGetLastError();
+                if (err != cudaSuccess) {
+                    cudaFree(buf);
+                    return err;
+                }
+                cache->entries.push_back(e);
+                cache->bytes += bytes;
+                *out_hi = e.hi;
+                *out_lo = e.lo;
+                return cudaSuccess;
+            }
+            cudaGetLastError();   // allocation failure: pack into the workspace instead
+        }
+    }
+    k_pack<<<grid, 256, 0, s>>>(p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, ws_hi, ws_lo);
+    count_launches(1);
+    *out_hi = ws_hi;
+    *out_lo = ws_lo;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cudaStream_t s,
+                    PackCache* cache) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
@@ -529,17 +613,14 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
     __nv_bfloat16* b_hi = a_hi + needA;
     __nv_bfloat16* a_lo = nprod == 3 ? b_hi + needB : nullptr;
     __nv_bfloat16* b_lo = nprod == 3 ? a_lo + needA : nullptr;
-    {
-        dim3 blk(32, 8);
-        dim3 gA(cdiv(Kp, 32), std::min<unsigned>(cdiv(RpA, 32), 65535), a_bc ? 1 : nb);
-        dim3 gB(cdiv(Kp, 32), std::min<unsigned>(cdiv(RpB, 32), 65535), b_bc ? 1 : nb);
-        k_pack<<<gA, blk, 0, s>>>(va.p, va.rs, va.cs, sa, Mr, g.K, nb, (int)RpA, (int)Kp,
-                                  g.reduce ? 1 : 0, a_hi, a_lo);
-        k_pack<<<gB, blk, 0, s>>>(vb.p, vb.rs, vb.cs, sb, Nr, g.K, nb, (int)RpB, (int)Kp,
-                                  g.reduce ? 1 : 0, b_hi, b_lo);
-        count_launches(2);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    if ((e = pack_operand(va.p, va.rs, va.cs, sa, Mr, g.K, nb, a_bc ? 1 : nb, (int)RpA, (int)Kp,
+                          g.reduce ? 1 : 0, nprod, a_hi, a_lo, cache, s, &a_hi, &a_lo)) !=
+        cudaSuccess)
+        return e;
+    if ((e = pack_operand(vb.p, vb.rs, vb.cs, sb, Nr, g.K, nb, b_bc ? 1 : nb, (int)RpB, (int)Kp,
+                          g.reduce ? 1 : 0, nprod, b_hi, b_lo, cache, s, &b_hi, &b_lo)) !=
+        cudaSuccess)
+        return e;
     CUtensorMap maps[4];
     if ((e = make_map(&maps[0], a_hi, Ktot, RpA, nba, BM)) != cudaSuccess) return e;
     if ((e = make_map(&maps[1], nprod == 3 ? a_lo : a_hi, Ktot, RpA, nba, BM)) != cudaSuccess) return e;

@@ -3,6 +3,8 @@
 
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace thc {
@@ -15,12 +17,41 @@ struct TcWorkspace {
     int* err = nullptr;             // set to 1 by a kernel whose bounded wait expired
 };
 
+// Packed operands of buffers whose contents do not change (the inputs and
+// the intermediates formed once at init): each distinct (buffer, view,
+// shape) is packed on first use and reused afterwards.
+struct PackCache {
+    struct Range {
+        const float* lo;
+        const float* hi;
+    };
+    struct Entry {
+        const float* p;
+        long long rs, cs, bs;
+        int R, Kd, nb, Rp, Kp, reduce, nprod;
+        __nv_bfloat16* hi;
+        __nv_bfloat16* lo;
+    };
+    std::vector<Range> constant;   // registered [lo, hi) address ranges
+    std::vector<Entry> entries;
+    size_t bytes = 0;
+    size_t budget = 8ull << 30;    // packed bytes kept at most
+    void add_constant(const float* p, size_t n) { constant.push_back({p, p + n}); }
+    bool is_constant(const float* p) const {
+        for (const Range& r : constant)
+            if (p >= r.lo && p < r.hi) return true;
+        return false;
+    }
+    void release();
+};
+
 // Packed-operand elements one product of this shape needs (upper bound).
 size_t gemm_tc_pack_elems(int M, int N, int K, int batch, bool reduce);
 
 // C = alpha op(A) op(B) + beta C on the tensor cores; nprod = 3 runs
 // hi*hi + hi*lo + lo*hi, nprod = 1 runs hi*hi only.  Returns
 // cudaErrorMemoryAllocation (without launching) if the workspace is too small.
-cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cudaStream_t s);
+cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cudaStream_t s,
+                    PackCache* cache = nullptr);
 
 }  // namespace thc
