@@ -491,9 +491,13 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         tcws.err = tcerr.p;
         // Buffers that keep their contents for the context's lifetime: their
         // bf16 hi/lo forms are packed once and reused by every residual.
+        // The cache may take up to half of the memory left free after init.
         if constexpr (std::is_same<T, float>::value) {
             for (DBuf<T>* b : {&y, &x, &z, &oo, &vv, &S, &KRy, &KRx, &Atil, &B6, &U6, &Gall, &Kx})
                 if (b->p) pcache.add_constant(b->p, b->n);
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                pcache.budget = std::min<size_t>(free_b / 2, 96ull << 30);
         }
     }
     THC_CUDA(cudaStreamSynchronize(st));

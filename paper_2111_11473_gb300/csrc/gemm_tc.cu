@@ -529,14 +529,17 @@ void PackCache::release() {
 
 namespace {
 
-// Pack one operand, or take it from the cache when its buffer is constant.
-// Returns the hi/lo pointers the tensor maps read.
+// Pack one operand into the workspace, or (use_cache) take it from the cache
+// of constant packs, packing it there on first use.  A cached operand that
+// cannot be stored (budget or allocation) is an error, never a workspace
+// write: the workspace was sized without it.
 cudaError_t pack_operand(const float* p, long long rs, long long cs, long long bs, int R, int Kd,
                          int nb_eff, int nb_grid, int Rp, int Kp, int reduce, int nprod,
-                         __nv_bfloat16* ws_hi, __nv_bfloat16* ws_lo, PackCache* cache,
-                         cudaStream_t s, __nv_bfloat16** out_hi, __nv_bfloat16** out_lo) {
+                         __nv_bfloat16* ws_hi, __nv_bfloat16* ws_lo, bool use_cache,
+                         PackCache* cache, cudaStream_t s, __nv_bfloat16** out_hi,
+                         __nv_bfloat16** out_lo) {
     const dim3 grid(cdiv(Kp, PK_K), std::min<unsigned>(cdiv(Rp, PK_R), 65535), nb_grid);
-    if (cache && cache->is_constant(p)) {
+    if (use_cache) {
         for (const PackCache::Entry& e : cache->entries)
             if (e.p == p && e.rs == rs && e.cs == cs && e.bs == bs && e.R == R && e.Kd == Kd &&
                 e.nb == nb_eff && e.Rp == Rp && e.Kp == Kp && e.reduce == reduce &&
@@ -548,27 +551,26 @@ cudaError_t pack_operand(const float* p, long long rs, long long cs, long long b
         const long long Ktot = reduce ? (long long)nb_eff * Kp : Kp;
         const size_t elems = (size_t)Rp * Ktot * (reduce ? 1 : nb_grid);
         const size_t bytes = elems * 2 * (nprod == 3 ? 2 : 1);
-        if (cache->bytes + bytes <= cache->budget) {
-            __nv_bfloat16* buf = nullptr;
-            if (cudaMalloc(&buf, bytes) == cudaSuccess) {
-                PackCache::Entry e{p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, nprod, buf,
-                                   nprod == 3 ? buf + elems : nullptr};
-                k_pack<<<grid, 256, 0, s>>>(p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, e.hi,
-                                            e.lo);
-                count_launches(1);
-                cudaError_t err = cudaGetLastError();
-                if (err != cudaSuccess) {
-                    cudaFree(buf);
-                    return err;
-                }
-                cache->entries.push_back(e);
-                cache->bytes += bytes;
-                *out_hi = e.hi;
-                *out_lo = e.lo;
-                return cudaSuccess;
-            }
-            cudaGetLastError();   // allocation failure: pack into the workspace instead
+        if (cache->bytes + bytes > cache->budget) return cudaErrorMemoryAllocation;
+        __nv_bfloat16* buf = nullptr;
+        if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return cudaErrorMemoryAllocation;
         }
+        PackCache::Entry e{p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, nprod, buf,
+                           nprod == 3 ? buf + elems : nullptr};
+        k_pack<<<grid, 256, 0, s>>>(p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, e.hi, e.lo);
+        count_launches(1);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) {
+            cudaFree(buf);
+            return err;
+        }
+        cache->entries.push_back(e);
+        cache->bytes += bytes;
+        *out_hi = e.hi;
+        *out_lo = e.lo;
+        return cudaSuccess;
     }
     k_pack<<<grid, 256, 0, s>>>(p, rs, cs, bs, R, Kd, nb_eff, Rp, Kp, reduce, ws_hi, ws_lo);
     count_launches(1);
@@ -607,18 +609,35 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
     const bool b_bc = !g.reduce && nb > 1 && sb == 0;
     const int nba = a_bc ? 1 : nbo, nbb = b_bc ? 1 : nbo;
     const size_t needA = (size_t)(RpA * Ktot * nba), needB = (size_t)(RpB * Ktot * nbb);
-    const size_t need = (nprod == 3 ? 2 : 1) * (needA + needB);
+    // Operands served from the cache of constant packs take no workspace.
+    const int red = g.reduce ? 1 : 0;
+    const size_t bytesA = needA * 2 * (nprod == 3 ? 2 : 1);
+    const size_t bytesB = needB * 2 * (nprod == 3 ? 2 : 1);
+    const bool a_cached = cache && cache->serves(va.p, bytesA, va.rs, va.cs, sa, Mr, g.K, nb,
+                                                 (int)RpA, (int)Kp, red, nprod);
+    // B is checked against the budget left after A's (possibly new) entry.
+    bool b_cached = false;
+    if (cache) {
+        const size_t held = cache->bytes;
+        if (a_cached) cache->bytes += bytesA;
+        b_cached = cache->serves(vb.p, bytesB, vb.rs, vb.cs, sb, Nr, g.K, nb, (int)RpB, (int)Kp,
+                                 red, nprod);
+        cache->bytes = held;
+    }
+    const size_t need = (nprod == 3 ? 2 : 1) * ((a_cached ? 0 : needA) + (b_cached ? 0 : needB));
     if (need > ws.elems) return cudaErrorMemoryAllocation;
+    // Workspace layout [A hi | B hi | A lo | B lo], cached operands omitted.
+    const size_t wsA = a_cached ? 0 : needA, wsB = b_cached ? 0 : needB;
     __nv_bfloat16* a_hi = ws.buf;
-    __nv_bfloat16* b_hi = a_hi + needA;
-    __nv_bfloat16* a_lo = nprod == 3 ? b_hi + needB : nullptr;
-    __nv_bfloat16* b_lo = nprod == 3 ? a_lo + needA : nullptr;
+    __nv_bfloat16* b_hi = a_hi + wsA;
+    __nv_bfloat16* a_lo = nprod == 3 ? b_hi + wsB : nullptr;
+    __nv_bfloat16* b_lo = nprod == 3 ? a_lo + wsA : nullptr;
     if ((e = pack_operand(va.p, va.rs, va.cs, sa, Mr, g.K, nb, a_bc ? 1 : nb, (int)RpA, (int)Kp,
-                          g.reduce ? 1 : 0, nprod, a_hi, a_lo, cache, s, &a_hi, &a_lo)) !=
+                          red, nprod, a_hi, a_lo, a_cached, cache, s, &a_hi, &a_lo)) !=
         cudaSuccess)
         return e;
     if ((e = pack_operand(vb.p, vb.rs, vb.cs, sb, Nr, g.K, nb, b_bc ? 1 : nb, (int)RpB, (int)Kp,
-                          g.reduce ? 1 : 0, nprod, b_hi, b_lo, cache, s, &b_hi, &b_lo)) !=
+                          red, nprod, b_hi, b_lo, b_cached, cache, s, &b_hi, &b_lo)) !=
         cudaSuccess)
         return e;
     CUtensorMap maps[4];

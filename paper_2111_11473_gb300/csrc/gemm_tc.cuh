@@ -42,6 +42,16 @@ struct PackCache {
             if (p >= r.lo && p < r.hi) return true;
         return false;
     }
+    // True if this operand is (or, within the budget, will be) cached.
+    bool serves(const float* p, size_t packed_bytes, long long rs, long long cs, long long bs,
+                int R, int Kd, int nb, int Rp, int Kp, int reduce, int nprod) const {
+        if (!is_constant(p)) return false;
+        for (const Entry& e : entries)
+            if (e.p == p && e.rs == rs && e.cs == cs && e.bs == bs && e.R == R && e.Kd == Kd &&
+                e.nb == nb && e.Rp == Rp && e.Kp == Kp && e.reduce == reduce && e.nprod == nprod)
+                return true;
+        return bytes + packed_bytes <= budget;
+    }
     void release();
 };
 

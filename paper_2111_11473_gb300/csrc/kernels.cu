@@ -446,10 +446,6 @@ __device__ __forceinline__ void tri_tma(void* dst, const CUtensorMap* m, unsigne
         : "memory");
 }
 
-__device__ __forceinline__ float4 tri_ld4(const float* tile, int r, int chunk) {
-    return *reinterpret_cast<const float4*>(tile + r * TT + ((chunk ^ (r & 7)) << 2));
-}
-
 // Same load on a 32-bit shared-memory address (tile base in bytes).
 __device__ __forceinline__ float4 tri_lds4(unsigned tile, int r, int chunk) {
     float4 v;
