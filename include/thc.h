@@ -294,6 +294,19 @@ thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
                               const double* Zc, const double* t1,
                               double* energy, void* stream);
 
+/*
+ * thc_selftest_bounded_wait - exercise the bounded-wait path that every
+ * waiting kernel of this library uses (TMA and MMA pipelines, the triangle
+ * kernel's operand ring).  One thread waits on a shared-memory mbarrier that
+ * is completed beforehand only if `complete` is non-zero, with a budget of
+ * about a millisecond; on expiry the kernel raises a device flag and
+ * returns, as the production kernels do, and this call reports it.
+ * Returns THC_OK if the wait completed, THC_ERR_TIMEOUT if it expired (the
+ * device stays usable either way), THC_ERR_CUDA on a launch failure.
+ * stream: cudaStream_t or NULL.  No counterpart in the paper.
+ */
+thc_status thc_selftest_bounded_wait(int complete, void* stream);
+
 /* Text of the first error recorded on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx or thc_destroy.  ctx may be NULL, which
  * returns the last error of a failed thc_init or thc_energy_noalloc on this

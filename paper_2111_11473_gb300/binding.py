@@ -95,6 +95,7 @@ _SIGNATURES = {
     "thc_mlp_train": (C.c_int, [_VP, _DP, _DP, _DP, C.c_longlong, C.c_int, C.c_int, C.c_double,
                                 C.c_ulonglong, C.POINTER(C.c_double)]),
     "thc_mlp_destroy": (None, [_VP]),
+    "thc_selftest_bounded_wait": (C.c_int, [C.c_int, _VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }
@@ -119,6 +120,14 @@ def load_library(path: str = LIB_PATH):
 
 def exported_symbols():
     return sorted(_SIGNATURES)
+
+
+def selftest_bounded_wait(complete: bool, stream=None) -> str:
+    """Run the library's bounded-wait self-test; returns the status name
+    (THC_OK if the wait completed, THC_ERR_TIMEOUT if it expired)."""
+    lib = load_library()
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    return STATUS.get(lib.thc_selftest_bounded_wait(int(bool(complete)), _VP(st)), "?")
 
 
 def _is_torch(a):

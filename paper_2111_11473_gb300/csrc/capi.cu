@@ -315,6 +315,28 @@ void thc_mlp_destroy(thc_mlp* m) {
     delete m;
 }
 
+thc_status thc_selftest_bounded_wait(int complete, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    int* flag = nullptr;
+    int h = 0;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    // about 1 ms at 2 GHz
+    if (e == cudaSuccess) e = thc::wait_selftest(complete, 2000000LL, flag, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (flag) cudaFree(flag);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("thc_selftest_bounded_wait: ") + cudaGetErrorString(e);
+        return THC_ERR_CUDA;
+    }
+    if (h) {
+        g_init_error = "thc_selftest_bounded_wait: the bounded wait expired";
+        return THC_ERR_TIMEOUT;
+    }
+    return THC_OK;
+}
+
 const char* thc_last_error(const thc_ctx* c) {
     if (!c) return g_init_error.c_str();
     return c->err.c_str();

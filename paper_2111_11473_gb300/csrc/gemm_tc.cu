@@ -511,7 +511,39 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) 
 
 long long rup(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// Self-test of the bounded-wait path: thread 0 waits on an mbarrier that is
+// completed only if `complete` is set, with a budget of `cycles`; on expiry
+// it raises *flag, as every production wait does, and returns.
+__global__ void k_wait_selftest(int complete, long long cycles, int* flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (complete) mbar_arrive(&bar);
+    const uint32_t a = smem_u32(&bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(0u));
+        if (done) return;
+        if (clock64() - t0 > cycles) {
+            atomicExch(flag, 1);
+            return;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t wait_selftest(int complete, long long cycles, int* flag, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(complete, cycles, flag);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 size_t gemm_tc_pack_elems(int M, int N, int K, int batch, bool reduce) {
     // Worst case over the two orientations (both sides padded to 128).

@@ -55,6 +55,11 @@ struct PackCache {
     void release();
 };
 
+// Launch a single bounded wait on an mbarrier that is completed only if
+// `complete` is non-zero; *flag (device) is set to 1 if the wait expired
+// after `cycles` SM clocks.
+cudaError_t wait_selftest(int complete, long long cycles, int* flag, cudaStream_t s);
+
 // Packed-operand elements one product of this shape needs (upper bound).
 size_t gemm_tc_pack_elems(int M, int N, int K, int batch, bool reduce);
 

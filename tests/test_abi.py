@@ -30,8 +30,8 @@ def test_header_declares_the_abi():
                            "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",
                            "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
                            "thc_profile_enable", "thc_profile_read",
-                           "thc_residual", "thc_solve", "thc_solve_opts_default",
-                           "thc_solve_pairs", "thc_step_name"]
+                           "thc_residual", "thc_selftest_bounded_wait", "thc_solve",
+                           "thc_solve_opts_default", "thc_solve_pairs", "thc_step_name"]
 
 
 def test_library_exports_every_declared_symbol(lib):
