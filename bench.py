@@ -66,6 +66,12 @@ def _peaks():
 # 152 SMs x (FMA lanes per SM) x 2 flops x 2.07 GHz, with the lane counts
 # measured by an FMA-throughput probe (64-bit: 2 per SM per clock; 32-bit: 128).
 FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM bytes (read + write) of one triangle launch at o=40, v=200, P=400,
+# G=1200, from one ncu capture of the current kernels (summaries in
+# profiles/residual_fp64_o40_v200_P400_G1200_K600_launches.md and
+# profiles/triangle_f32_o40_v200_P400_G1200_K600.md).  Other sizes: null.
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 162.42e9 + 0.53e9, "mixed": 13.55e9 + 0.26e9}
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
@@ -330,6 +336,8 @@ def main():
                     help="system from synth.CONFIGS (named by size)")
     ap.add_argument("--skip-fp64-solve", action="store_true",
                     help="no float64 solve (sizes where it takes too long)")
+    ap.add_argument("--t2sq-route", type=int, default=0, choices=[0, 1, 2],
+                    help="Eqs. 32-33: 0 automatic, 1 Alg. 6 (O(N^4)), 2 Algs. 4-5 (O(N^5))")
     ap.add_argument("--fp64-iters", type=int, default=0,
                     help="also run this many float64 and mixed iterations from zero "
                          "and report their energy difference per iteration")
@@ -359,7 +367,7 @@ def main():
     s = _system(seed_offset=rank)
     prec = pkg.THC_PREC_FP64 if args.precision == "fp64" else pkg.THC_PREC_MIXED
     tens = [torch.from_numpy(a).to(dev) for a in (s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z)]
-    ctx = pkg.Context(*tens, precision=prec, stream=stream)
+    ctx = pkg.Context(*tens, precision=prec, stream=stream, t2sq_route=args.t2sq_route)
     # State: two Jacobi steps from zero (projected MP1 and one more step).
     Zc0, t10, _ = ctx.solve(max_iter=3, diis_n=0, raise_on_failure=False)
     Zc = torch.from_numpy(Zc0).to(dev)
@@ -418,15 +426,34 @@ def main():
     dom = max((k for k in steps), key=lambda k: steps[k]["ms_per_residual"])
     tri_ms, tri_fl, tri_n = prof["triangle"]
     fp64 = args.precision == "fp64"
-    peak_tri = FP64_ALU_TFLOPS if fp64 else FP32_ALU_TFLOPS
-    achieved = (tri_fl / max(1, tri_n)) / (tri_ms / max(1, tri_n) * 1e-3) / 1e12
-    roofline = {"kernel": "triangle (Alg. 6 line 11)", "bound": "alu",
-                "achieved": achieved, "peak": peak_tri, "unit": "TFLOP/s",
-                "frac": achieved / peak_tri, "traffic": None,
-                "peak_source": ("derived: 152 SMs x %s FMA lanes x 2 x 2.07 GHz"
-                                % ("2 fp64" if fp64 else "128 fp32")),
-                "share_of_step": tri_ms / max(1e-9, sum(v["ms_per_residual"] for v in steps.values())
-                                              * max(1, prof["residuals"]))}
+    total_ms = max(1e-9, sum(v["ms_per_residual"] for v in steps.values()) *
+                   max(1, prof["residuals"]))
+    if tri_n > 0:
+        peak_tri = FP64_ALU_TFLOPS if fp64 else FP32_ALU_TFLOPS
+        achieved = (tri_fl / tri_n) / (tri_ms / tri_n * 1e-3) / 1e12
+        roofline = {"kernel": "triangle (Alg. 6 line 11)", "bound": "alu",
+                    "achieved": achieved, "peak": peak_tri, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tri,
+                    "traffic": (TRIANGLE_TRAFFIC_BYTES[args.precision]
+                                if args.workload == DEFAULT_WORKLOAD else None),
+                    "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                    "peak_source": ("derived: 152 SMs x %s FMA lanes x 2 x 2.07 GHz"
+                                    % ("2 fp64" if fp64 else "128 fp32")),
+                    "share_of_step": tri_ms / total_ms}
+    else:
+        # Algs. 4-5 route: the dominant step is a group of batched products.
+        ms_d, fl_d, n_d = prof[dom]
+        achieved = fl_d / (ms_d * 1e-3) / 1e12
+        if fp64:
+            peak, bound, src = FP64_ALU_TFLOPS, "alu", "derived: 152 SMs x 2 fp64 FMA lanes x 2 x 2.07 GHz"
+        else:
+            # bf16x3: three bf16 products per algorithmic multiply-add
+            peak = _peaks().get("bf16_tflops", 1931.0) / 3.0
+            bound, src = "tensor", "measured bf16 burst peak / 3 (bf16x3 products)"
+        roofline = {"kernel": f"{dom} step (batched products)", "bound": bound,
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": src,
+                    "share_of_step": ms_d / total_ms}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -434,6 +461,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32+bf16x3",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
+                   "t2sq_route": args.t2sq_route,
                    "state": "solver iterate after two Jacobi steps from zero",
                    "l2": "inputs larger than L2 (Cholesky blocks 238 MB, grid factors 1.5 GB)",
                    "parallelism": f"{world} independent system(s), one per GPU"},

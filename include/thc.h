@@ -77,6 +77,12 @@ typedef struct {
                                 (ib|ja) matrix, (ov)^2 words, built once at init
                                 from the THC factors; automatic picks 2 when
                                 that matrix takes at most 16 GiB */
+    int t2sq_route;          /* T2^2 contributions to Omega^A and Omega^C
+                                (Eqs. 32-33): 0 = automatic, 1 = Alg. 6
+                                (O(N^4), triangle kernel on the CUDA cores),
+                                2 = Algs. 4 and 5 (O(N^5), batched products
+                                only); automatic compares the estimated time
+                                of both at the context's precision */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */

@@ -23,7 +23,7 @@ class ThcConfig(C.Structure):
                 ("n_g", C.c_int), ("n_k", C.c_int), ("precision", C.c_int),
                 ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double),
-                ("tc_products", C.c_int), ("alg7_route", C.c_int)]
+                ("tc_products", C.c_int), ("alg7_route", C.c_int), ("t2sq_route", C.c_int)]
 
 
 class ThcSolveOpts(C.Structure):
@@ -168,7 +168,7 @@ class Context:
 
     def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
                  k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10,
-                 tc_products=3, alg7_route=0):
+                 tc_products=3, alg7_route=0, t2sq_route=0):
         lib = load_library()
         o, v = len(eps_o), len(eps_v)
         n = o + v
@@ -185,6 +185,7 @@ class Context:
         cfg.lsq_rel_cutoff = lsq_rel_cutoff
         cfg.tc_products = tc_products
         cfg.alg7_route = alg7_route
+        cfg.t2sq_route = t2sq_route
         args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)), _Arg(L, (K, n, n)),
                 _Arg(x, (n, G)), _Arg(z, (G, G))]
         handle = _VP()

@@ -45,6 +45,8 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "tc_products must be 0, 1 or 3"};
     if (cfg->alg7_route < 0 || cfg->alg7_route > 2)
         return {THC_ERR_ARG, "alg7_route must be 0, 1 or 2"};
+    if (cfg->t2sq_route < 0 || cfg->t2sq_route > 2)
+        return {THC_ERR_ARG, "t2sq_route must be 0, 1 or 2"};
     return {};
 }
 

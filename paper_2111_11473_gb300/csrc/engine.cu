@@ -418,24 +418,67 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(U6.alloc((size_t)o * G * P));
     THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p, P, 1, 0, o, (long long)v * G, 0,
                (long long)G * P));
-    const size_t gall_bytes = (size_t)G * PP * sizeof(T);
-    gall_resident = cfg.workspace_bytes == 0 ? gall_bytes <= (size_t)48 << 30
-                                             : gall_bytes <= cfg.workspace_bytes / 4;
-    if (gall_resident) {
-        THC_TRY(Gall.alloc((size_t)G * PP));
-        THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0, G,
-                   0, P, PP));
-    } else {
-        THC_TRY(Gch.alloc((size_t)ic * PP));
+    // ---- Route for Eqs. 32-33: Alg. 6 (O(N^4), triangle on the CUDA cores)
+    //      or Algs. 4 and 5 (O(N^5), batched products).  Automatic: the
+    //      smaller estimated time, with the tensor-core products of the mixed
+    //      path taken at 300 TFLOP/s and its triangle at 32 TFLOP/s, and every
+    //      float64 operation at one rate.
+    {
+        const double dG = G, dP = P, dO = o, dV = v;
+        const double f6_tri = 5.0 * dG * dP * dP * dP;
+        const double f6_mm = 2.0 * dG * dP * dP * (dO + dV) + 6.0 * dO * dV * dP * dP +
+                             2.0 * dP * dP * dP * dO + 2.0 * dP * dO * dV * dP;
+        // per pair (i, j) of Alg. 4 and (j, a) of Alg. 5, products as issued by alg45
+        const double p4 = 2.0 * (dV * dV * dP + dV * dG * dV + dG * dG * dV + dO * dG * dG +
+                                 dO * dO * dG + dO * dP * dO + dP * dP * dO + dV * dP * dP +
+                                 dV * dV * dP + dP * dV * dV + dP * dP * dV);
+        const double p5 = 2.0 * (dO * dV * dP + dO * dG * dV + dG * dG * dO + dO * dG * dG +
+                                 dO * dV * dG + dV * dP * dO + dP * dP * dV + dO * dP * dP +
+                                 dO * dV * dP + dP * dV * dO + dP * dP * dV);
+        const double f45 = dO * dO * p4 + dO * dV * p5 + 2.0 * (dO + dV) * dV * dP * dP;
+        const bool mixed = !std::is_same<T, double>::value && cfg.tc_products > 0;
+        const double t6 = mixed ? f6_tri / 32e12 + f6_mm / 300e12 : f6_tri + f6_mm;
+        const double t45 = mixed ? f45 / 300e12 : f45;
+        t2sq_n5 = cfg.t2sq_route == 2 || (cfg.t2sq_route == 0 && t45 < t6);
     }
-    THC_TRY(A6.alloc(ov * P));
-    THC_TRY(C6.alloc((size_t)o * PP));
-    THC_TRY(D6.alloc((size_t)v * PP));
-    THC_TRY(Ech.alloc((size_t)ic * PP));
-    THC_TRY(Fch.alloc((size_t)ic * PP));
-    THC_TRY(H.alloc((size_t)P * PP));
-    THC_TRY(M6.alloc((size_t)P * o * P));
-    THC_TRY(I6.alloc((size_t)P * ov));
+    if (!t2sq_n5) {
+        const size_t gall_bytes = (size_t)G * PP * sizeof(T);
+        gall_resident = cfg.workspace_bytes == 0 ? gall_bytes <= (size_t)48 << 30
+                                                 : gall_bytes <= cfg.workspace_bytes / 4;
+        if (gall_resident) {
+            THC_TRY(Gall.alloc((size_t)G * PP));
+            THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0,
+                       G, 0, P, PP));
+        } else {
+            THC_TRY(Gch.alloc((size_t)ic * PP));
+        }
+        THC_TRY(A6.alloc(ov * P));
+        THC_TRY(C6.alloc((size_t)o * PP));
+        THC_TRY(D6.alloc((size_t)v * PP));
+        THC_TRY(Ech.alloc((size_t)ic * PP));
+        THC_TRY(Fch.alloc((size_t)ic * PP));
+        THC_TRY(H.alloc((size_t)P * PP));
+        THC_TRY(M6.alloc((size_t)P * o * P));
+        THC_TRY(I6.alloc((size_t)P * ov));
+    } else {
+        // Pairs per batched product: the G x G intermediates of one batch
+        // take at most 2 GiB.
+        const long long per = (long long)G * G * (long long)sizeof(T);
+        nb45 = (int)std::max<long long>(1, std::min<long long>(std::max(o, v), (2LL << 30) / per));
+        const long long nb = nb45, mx = std::max(o, v);
+        THC_TRY(Q4.alloc(ov * P));
+        THC_TRY(S5.alloc(ov * P));
+        THC_TRY(C45.alloc((size_t)nb * mx * v));
+        THC_TRY(M245.alloc((size_t)nb * mx * G));
+        THC_TRY(D45.alloc((size_t)nb * G * G));
+        THC_TRY(M345.alloc((size_t)nb * o * G));
+        THC_TRY(F45.alloc((size_t)nb * o * mx));
+        THC_TRY(M445.alloc((size_t)nb * mx * P));
+        THC_TRY(G45.alloc((size_t)nb * PP));
+        THC_TRY(M545.alloc((size_t)nb * mx * P));
+        THC_TRY(I45.alloc((size_t)nb * mx * v));
+        THC_TRY(R45.alloc((size_t)nb * P * v));
+    }
     // ---- Alg. 7 exchange route.  Dense route: Kx[(ia),(jb)] = (ib|ja)
     //      = sum_J B[(i,b),J] x_j^J x_a^J, one v x v block per (i, j).
     {
@@ -480,6 +523,17 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
             need = std::max(need, gemm_tc_pack_elems((int)std::min<long long>(sh.M, INT32_MAX),
                                                      (int)std::min<long long>(sh.N, INT32_MAX),
                                                      (int)sh.K, (int)sh.b, false));
+        if (t2sq_n5) {
+            const long long nb = nb45;
+            const Shape s45[] = {{v, v, P, nb}, {v, G, v, nb}, {G, G, v, nb}, {o, G, G, nb},
+                                 {o, o, G, nb}, {P, P, o, nb}, {v, P, P, nb}, {P, v, v, nb},
+                                 {P, P, v, nb}, {o, v, P, nb}, {o, G, v, nb}, {G, G, o, nb},
+                                 {o, v, G, nb}, {v, P, o, nb}, {o, P, P, nb}, {P, v, o, nb},
+                                 {v, P, P, o}, {o, P, P, v}};
+            for (const Shape& sh : s45)
+                need = std::max(need, gemm_tc_pack_elems((int)sh.M, (int)sh.N, (int)sh.K,
+                                                         (int)sh.b, false));
+        }
         tc_products = cfg.tc_products;
         THC_TRY(tcpack.alloc(need));
         THC_TRY(tcpart.alloc((size_t)std::max<long long>(8 * PP, 1 << 22)));
@@ -574,6 +628,88 @@ Err Engine<T>::alg6(T* sgm) {
                (long long)o * P));
     THC_TRY(mm(o, v, P, rm(M6.p, P), tr(yv, P), I6.p, v, 1, 0, P, (long long)o * P, 0, ov));
     THC_TRY(mm(P, P, (int)ov, rm(I6.p, ov), rm(KRy.p, P), sgm, P, 1, 1));
+    return Err{};
+}
+
+// Algs. 4 and 5: the T2^2 contributions to Omega^A (Eq. 32) and Omega^C
+// (Eq. 33) through per-pair two-index products, O(o^2 v G^2).  With the
+// Khatri-Rao rows W_i[a][Z] = y_i^Z y_a^Z (= U_a[i][Z]):
+//   Alg. 4, pair (i, j):  C = (W_i T) W_j^T = t_ij^cd,  D = x_v^T C x_v,
+//     E = z o D,  F = x_o E x_o^T = sum_cd t_ij^cd (kc|ld),
+//     H = T o (y_o^T F y_o),  I = y_v H y_v^T = sigma_ij^ab,
+//     sigma^XX' += sum_ab W_i[a][X] I_ab W_j[b][X'];
+//   Alg. 5, pair (j, a):  C = (U_a T) W_j^T = t_lj^ad,  D = x_o^T C x_v,
+//     E = z o D,  F = x_o E^T x_v^T = sum_ld t_lj^ad (lc|kd),
+//     H = T o (y_v^T F^T y_o),  I = y_o H y_v^T,
+//     sigma^XX' += sum_ib U_a[i][X] I_ib W_j[b][X'].
+// Each loop runs over one index with the other batched (nb45 pairs a launch).
+template <typename T>
+Err Engine<T>::alg45(T* sgm) {
+    const long long ov = (long long)o * v, PP = (long long)P * P, GG = (long long)G * G;
+    const long long vP = (long long)v * P, oP = (long long)o * P;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    const T* xo = x.p;
+    const T* xv = x.p + (long long)o * G;
+    const T* kr = KRy.p;
+    seg_begin(THC_STEP_ALG6_GEMM);
+    // Q_i = W_i T (v x P, for every i);  S_a = U_a T (o x P, for every a)
+    THC_TRY(mm(v, P, P, rm(kr, P), rm(Tc.p, P), Q4.p, P, 1, 0, o, vP, 0, vP));
+    THC_TRY(mm(o, P, P, View<T>{kr, vP, 1}, rm(Tc.p, P), S5.p, P, 1, 0, v, P, 0, oP));
+    // ---- Alg. 4: loop over i, batch over j
+    for (int i = 0; i < o; ++i) {
+        for (int j0 = 0; j0 < o; j0 += nb45) {
+            const int nb = std::min(nb45, o - j0);
+            const T* Wj = kr + (long long)j0 * vP;
+            THC_TRY(mm(v, v, P, rm(Q4.p + (long long)i * vP, P), tr(Wj, P), C45.p, v, 1, 0, nb,
+                       0, vP, (long long)v * v));
+            THC_TRY(mm(v, G, v, rm(C45.p, v), rm(xv, G), M245.p, G, 1, 0, nb, (long long)v * v, 0,
+                       (long long)v * G));
+            THC_TRY(mm(G, G, v, tr(xv, G), rm(M245.p, G), D45.p, G, 1, 0, nb, 0,
+                       (long long)v * G, GG));
+            THC_CUDA(hadamard_batched(D45.p, z.p, GG, nb, st));
+            THC_TRY(mm(o, G, G, rm(xo, G), rm(D45.p, G), M345.p, G, 1, 0, nb, 0, GG,
+                       (long long)o * G));
+            THC_TRY(mm(o, o, G, rm(M345.p, G), tr(xo, G), F45.p, o, 1, 0, nb, (long long)o * G, 0,
+                       (long long)o * o));
+            THC_TRY(mm(o, P, o, rm(F45.p, o), rm(yo, P), M445.p, P, 1, 0, nb, (long long)o * o, 0,
+                       oP));
+            THC_TRY(mm(P, P, o, tr(yo, P), rm(M445.p, P), G45.p, P, 1, 0, nb, 0, oP, PP));
+            THC_CUDA(hadamard_batched(G45.p, Tc.p, PP, nb, st));
+            THC_TRY(mm(v, P, P, rm(yv, P), rm(G45.p, P), M545.p, P, 1, 0, nb, 0, PP, vP));
+            THC_TRY(mm(v, v, P, rm(M545.p, P), tr(yv, P), I45.p, v, 1, 0, nb, vP, 0,
+                       (long long)v * v));
+            THC_TRY(mm(P, v, v, tr(kr + (long long)i * vP, P), rm(I45.p, v), R45.p, v, 1, 0, nb,
+                       0, (long long)v * v, vP));
+            THC_TRY(mm(P, P, v, rm(R45.p, v), rm(Wj, P), sgm, P, 1, 1, nb, vP, vP, 0, true));
+        }
+    }
+    // ---- Alg. 5: loop over j, batch over a
+    for (int j = 0; j < o; ++j) {
+        const T* Wj = kr + (long long)j * vP;
+        for (int a0 = 0; a0 < v; a0 += nb45) {
+            const int nb = std::min(nb45, v - a0);
+            THC_TRY(mm(o, v, P, rm(S5.p + (long long)a0 * oP, P), tr(Wj, P), C45.p, v, 1, 0, nb,
+                       oP, 0, ov));
+            THC_TRY(mm(o, G, v, rm(C45.p, v), rm(xv, G), M245.p, G, 1, 0, nb, ov, 0,
+                       (long long)o * G));
+            THC_TRY(mm(G, G, o, tr(xo, G), rm(M245.p, G), D45.p, G, 1, 0, nb, 0,
+                       (long long)o * G, GG));
+            THC_CUDA(hadamard_batched(D45.p, z.p, GG, nb, st));
+            THC_TRY(mm(o, G, G, rm(xo, G), tr(D45.p, G), M345.p, G, 1, 0, nb, 0, GG,
+                       (long long)o * G));
+            THC_TRY(mm(o, v, G, rm(M345.p, G), tr(xv, G), F45.p, v, 1, 0, nb, (long long)o * G, 0,
+                       ov));
+            THC_TRY(mm(v, P, o, tr(F45.p, v), rm(yo, P), M445.p, P, 1, 0, nb, ov, 0, vP));
+            THC_TRY(mm(P, P, v, tr(yv, P), rm(M445.p, P), G45.p, P, 1, 0, nb, 0, vP, PP));
+            THC_CUDA(hadamard_batched(G45.p, Tc.p, PP, nb, st));
+            THC_TRY(mm(o, P, P, rm(yo, P), rm(G45.p, P), M545.p, P, 1, 0, nb, 0, PP, oP));
+            THC_TRY(mm(o, v, P, rm(M545.p, P), tr(yv, P), I45.p, v, 1, 0, nb, oP, 0, ov));
+            THC_TRY(mm(P, v, o, View<T>{kr + (long long)a0 * P, 1, vP}, rm(I45.p, v), R45.p, v, 1,
+                       0, nb, P, ov, vP));
+            THC_TRY(mm(P, P, v, rm(R45.p, v), rm(Wj, P), sgm, P, 1, 1, nb, vP, 0, 0, true));
+        }
+    }
     return Err{};
 }
 
@@ -722,7 +858,7 @@ Err Engine<T>::residual_dev(bool want_energy) {
     THC_CUDA(lincomb(sg1, ov, 1, sg1, 1, D8.p, 1, FvoT.p, st));
 
     // Algs. 6 and 7 (T2^2 terms through the THC ovov integrals)
-    THC_TRY(alg6(sgm));
+    THC_TRY(t2sq_n5 ? alg45(sgm) : alg6(sgm));
     THC_TRY(alg7(sgm));
 
     seg_begin(THC_STEP_POST);

@@ -123,6 +123,11 @@ struct Engine {
     // Alg. 7 scratch.
     DBuf<T> R7, S7, C7, D7, Yv, M7, Yo, N7, E7, P7, G7;
     bool alg7_dense = false;
+    // Algs. 4 and 5 (O(N^5) route for Eqs. 32-33)
+    bool t2sq_n5 = false;
+    int nb45 = 0;                           // pairs per batched product
+    DBuf<T> Q4, S5;                         // o x v x P: W_i T;  v x o x P: U_a T
+    DBuf<T> C45, M245, D45, M345, F45, M445, G45, M545, I45, R45;
     DBuf<T> Kx;                             // (ov) x (ov): Kx[(ia),(jb)] = (ib|ja)
     DBuf<T> W7;                             // P x (ov)
 
@@ -151,6 +156,7 @@ struct Engine {
     Err fock_slab(int nb, const T* Loo_, const T* Lov_, const T* Lvo_, const T* Lvv_);
     Err d_operator(const T* M, int nb, T* Dout);
     Err alg6(T* sgm);
+    Err alg45(T* sgm);
     Err alg7(T* sgm);
 };
 

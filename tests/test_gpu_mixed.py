@@ -76,3 +76,16 @@ def test_mixed_fullsize_error_against_fp64_gpu(tcp):
           f"|dE| = {abs(E32 - E64):.2e} Eh")
     assert err < BOUND[tcp] * scale
     assert abs(E32 - E64) < 1e-6 * abs(E64)
+
+
+@pytest.mark.parametrize("route", [1, 2])
+def test_mixed_t2sq_routes_within_bound(route):
+    """Alg. 6 (triangle) and Algs. 4-5 (tensor-core products) in mixed precision."""
+    import paper_2111_11473_gb300 as pkg
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(8, 60, 120, 200, 80, 13)
+    with context(s, precision=pkg.THC_PREC_MIXED, t2sq_route=route) as ctx:
+        sig, sig1, E = ctx.residual(Zc, t1)
+    scale = max(np.abs(sig_ref).max(), np.abs(r1_ref).max())
+    err = max(np.abs(sig - sig_ref).max(), np.abs(sig1 - r1_ref).max())
+    assert err < BOUND[3] * scale
+    assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))

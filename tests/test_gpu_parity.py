@@ -120,3 +120,15 @@ def test_alg7_routes_match_oracle(route):
         sig, sig1, E = ctx.residual(Zc, t1)
     assert np.abs(sig - sig_ref).max() < RES_TOL
     assert np.abs(sig1 - r1_ref).max() < RES_TOL
+
+
+@pytest.mark.parametrize("case", [(3, 7, 10, 14, 9, 5), (7, 37, 70, 90, 45, 11)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_t2sq_n5_route_matches_oracle(case):
+    """Eqs. 32-33 through Algs. 4 and 5 (O(N^5), batched products) instead of Alg. 6."""
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(*case)
+    with context(s, t2sq_route=2) as ctx:
+        sig, sig1, E = ctx.residual(Zc, t1)
+    assert np.abs(sig - sig_ref).max() < RES_TOL
+    assert np.abs(sig1 - r1_ref).max() < RES_TOL
+    assert abs(E - E_ref) < 1e-9
