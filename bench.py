@@ -402,6 +402,19 @@ def main():
     ms_max = max_over_ranks(ms, dist, dev)
     value = whole_job_rate(world, ms_max)
 
+    # App. II density matrices of the bench state (one call, device buffers).
+    Doo = torch.empty((s.o, s.o), dtype=torch.float64, device=dev)
+    Dvv = torch.empty((s.v, s.v), dtype=torch.float64, device=dev)
+    ctx.mp2_density(Zc, out=(Doo, Dvv))
+    torch.cuda.synchronize(dev)
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    ctx.mp2_density(Zc, out=(Doo, Dvv))
+    d1.record(stream)
+    torch.cuda.synchronize(dev)
+    density_ms = d0.elapsed_time(d1)
+
     # End to end through the public API with pinned host buffers.
     Zh = torch.from_numpy(Zc0).pin_memory()
     t1h = torch.from_numpy(t10).pin_memory()
@@ -469,6 +482,7 @@ def main():
         "e2e": {"value": whole_job_rate(world, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": prof["kernel_launches"],
+        "mp2_density_ms": density_ms,
         "clocks": clocks,
         "roofline": roofline,
         "dominant_step": dom,

@@ -138,6 +138,19 @@ thc_status thc_residual(thc_ctx* ctx, const double* Zc, const double* t1,
 thc_status thc_energy(thc_ctx* ctx, const double* Zc, const double* t1,
                       double* energy);
 
+/*
+ * thc_mp2_density - one-particle density matrices of the doubles amplitudes
+ * encoded by the THC core Zc (App. II, Eqs. 47-48):
+ *   D_ij = -2 sum_kab t_ik^ab (2 t_jk^ab - t_jk^ba),
+ *   D_ab =  2 sum_ijc t_ij^ac (2 t_ij^bc - t_ji^bc),
+ * with t_ij^ab = sum_WX y_i^W y_a^W Zc^WX y_j^X y_b^X, evaluated in O(N^4)
+ * through the factorisation of Eqs. 49-56 (the MP2 natural-orbital density
+ * when Zc holds MP2 amplitudes).  Zc: P x P symmetric, row-major; D_oo:
+ * o x o and D_vv: v x v row-major outputs (host or device).  Replaces the
+ * context's stored t1 by zero.  Errors as thc_residual.
+ */
+thc_status thc_mp2_density(thc_ctx* ctx, const double* Zc, double* D_oo, double* D_vv);
+
 /* Learned preconditioner network (see thc_mlp_create). */
 typedef struct thc_mlp thc_mlp;
 

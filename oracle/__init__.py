@@ -16,4 +16,6 @@ spin_orbital  Independent spin-orbital CCSD (Stanton-Gauss intermediates)
               used to pin the closed-shell algebra.
 fci           Two-electron full CI (pins CCSD with one occupied orbital).
 solver        Jacobi + DIIS drivers for canonical and THC-projected CCSD.
+density       MP2-like one-particle density matrices (App. II, Eqs. 47-48).
+mlp           Float64 reference of the learned preconditioner's network.
 """

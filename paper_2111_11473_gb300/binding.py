@@ -77,6 +77,7 @@ _SIGNATURES = {
                            C.POINTER(_VP)]),
     "thc_residual": (C.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
     "thc_energy": (C.c_int, [_VP, _DP, _DP, _DP]),
+    "thc_mp2_density": (C.c_int, [_VP, _DP, _DP, _DP]),
     "thc_solve": (C.c_int, [_VP, C.POINTER(ThcSolveOpts), _DP, _DP, C.POINTER(ThcReport)]),
     "thc_profile_enable": (C.c_int, [_VP, C.c_int]),
     "thc_profile_read": (C.c_int, [_VP, C.POINTER(ThcProfile)]),
@@ -221,6 +222,16 @@ class Context:
         eptr = C.addressof(e) if want_energy else None
         self._check(self._lib.thc_residual(self._h, zc.ptr, tt.ptr, s.ptr, s1.ptr, eptr))
         return out[0], out[1], (e.value if want_energy else None)
+
+    def mp2_density(self, Zc, out=None):
+        """(D_oo, D_vv) of the amplitudes encoded by Zc (App. II, Eqs. 47-56)."""
+        zc = _Arg(Zc, (self.P, self.P))
+        if out is None:
+            out = (self._out(Zc, (self.o, self.o)), self._out(Zc, (self.v, self.v)))
+        a = _Arg(out[0], (self.o, self.o), writable=True)
+        b = _Arg(out[1], (self.v, self.v), writable=True)
+        self._check(self._lib.thc_mp2_density(self._h, zc.ptr, a.ptr, b.ptr))
+        return out[0], out[1]
 
     def energy(self, Zc, t1):
         zc = _Arg(Zc, (self.P, self.P))

@@ -141,6 +141,16 @@ thc_status thc_energy(thc_ctx* c, const double* Zc, const double* t1, double* en
     return THC_OK;
 }
 
+thc_status thc_mp2_density(thc_ctx* c, const double* Zc, double* D_oo, double* D_vv) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (!Zc || !D_oo || !D_vv) return fail(c, {THC_ERR_ARG, "NULL argument"});
+    thc::Err e = c->e64 ? c->e64->mp2_density(Zc, D_oo, D_vv)
+                        : c->e32->mp2_density(Zc, D_oo, D_vv);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
 thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
                      double* t1_inout, thc_report* report) {
     if (!c) return THC_ERR_ARG;

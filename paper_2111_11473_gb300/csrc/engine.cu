@@ -420,9 +420,10 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                (long long)G * P));
     // ---- Route for Eqs. 32-33: Alg. 6 (O(N^4), triangle on the CUDA cores)
     //      or Algs. 4 and 5 (O(N^5), batched products).  Automatic: the
-    //      smaller estimated time, with the tensor-core products of the mixed
-    //      path taken at 300 TFLOP/s and its triangle at 32 TFLOP/s, and every
-    //      float64 operation at one rate.
+    //      smaller estimated time from rates measured on GB300 at o=40
+    //      (mixed: triangle 32 TFLOP/s, Alg. 6 products 100, Algs. 4-5
+    //      products 35; float64: 0.85 for every operation) plus 10 us per
+    //      product launched (it decides at small sizes).
     {
         const double dG = G, dP = P, dO = o, dV = v;
         const double f6_tri = 5.0 * dG * dP * dP * dP;
@@ -437,8 +438,14 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                                  dO * dV * dP + dP * dV * dO + dP * dP * dV);
         const double f45 = dO * dO * p4 + dO * dV * p5 + 2.0 * (dO + dV) * dV * dP * dP;
         const bool mixed = !std::is_same<T, double>::value && cfg.tc_products > 0;
-        const double t6 = mixed ? f6_tri / 32e12 + f6_mm / 300e12 : f6_tri + f6_mm;
-        const double t45 = mixed ? f45 / 300e12 : f45;
+        const double n6 = 8.0 + 4.0 * std::ceil(dG / ic);
+        const double nb = std::max(1.0, std::min(std::max(dO, dV),
+                                                 std::floor(2.0 * (1LL << 30) /
+                                                            (dG * dG * sizeof(T)))));
+        const double n45 = 13.0 * dO * (std::ceil(dO / nb) + std::ceil(dV / nb)) + 2.0;
+        const double t6 = (mixed ? f6_tri / 32e12 + f6_mm / 100e12 : (f6_tri + f6_mm) / 0.85e12) +
+                          n6 * 10e-6;
+        const double t45 = (mixed ? f45 / 35e12 : f45 / 0.85e12) + n45 * 10e-6;
         t2sq_n5 = cfg.t2sq_route == 2 || (cfg.t2sq_route == 0 && t45 < t6);
     }
     if (!t2sq_n5) {
@@ -919,6 +926,83 @@ Err Engine<T>::energy(const double* Zc, const double* t1in, double* e_out) {
     THC_CUDA(cudaStreamSynchronize(st));
     const double etot = e[0] + e[1];
     THC_CUDA(cudaMemcpy(e_out, &etot, sizeof(double), cudaMemcpyDefault));
+    return Err{};
+}
+
+// App. II: D_ij = -2 sum_kab t_ik^ab (2 t_jk^ab - t_jk^ba) and
+// D_ab = 2 sum_ijc t_ij^ac (2 t_ij^bc - t_ji^bc) (Eqs. 47-48) for the THC
+// amplitudes t = y y T y y, in O(N^4) with o = y_o^T y_o, v = y_v^T y_v:
+//   Coulomb (Eqs. 53-54):  M = T (o o v) T,
+//     D_oo = -4 y_o (v o M) y_o^T,   D_vv = 4 y_v (o o M) y_v^T;
+//   exchange (Eqs. 55-56), per occupied i (virtual a) with A = T diag(y_i) v
+//   (T diag(y_a) o):  B = (o o A) T^T (resp. (v o A) T^T),
+//     c[Y] = sum_X v^XY B^XY (resp. o^XY B^XY),
+//     D_ij += 2 sum_Y c_i[Y] y_j^Y,   D_ab -= 2 sum_Y c_a[Y] y_b^Y.
+template <typename T>
+Err Engine<T>::mp2_density(const double* Zc, double* Doo_out, double* Dvv_out) {
+    const long long PP = (long long)P * P;
+    const T* yo = y.p;
+    const T* yv = y.p + (long long)o * P;
+    const int mx = std::max(o, v);
+    if (!dn_ones.p) {
+        const long long per = 2 * PP * (long long)sizeof(T);
+        const int nb = (int)std::max<long long>(1, std::min<long long>(mx, (2LL << 30) / per));
+        THC_TRY(dn_x1.alloc((size_t)nb * PP));
+        THC_TRY(dn_x2.alloc((size_t)nb * PP));
+        THC_TRY(dn_c.alloc((size_t)nb * P));
+        THC_TRY(dn_m1.alloc(PP));
+        THC_TRY(dn_m2.alloc(PP));
+        THC_TRY(dn_q.alloc((size_t)mx * P));
+        THC_TRY(dn_oo.alloc((size_t)o * o));
+        THC_TRY(dn_vv.alloc((size_t)v * v));
+        THC_TRY(dn_t1.alloc((size_t)o * v));
+        THC_TRY(dn_out.alloc((size_t)o * o + (size_t)v * v));
+        THC_TRY(dn_ones.alloc(P));
+        std::vector<T> one(P, T(1));
+        THC_CUDA(cudaMemcpyAsync(dn_ones.p, one.data(), sizeof(T) * P, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemsetAsync(dn_t1.p, 0, sizeof(T) * o * v, st));
+    }
+    const int nbmax = (int)(dn_c.n / P);
+    // the core (t1 = 0 here; the singles play no part in Eqs. 47-48)
+    std::vector<double> zero((size_t)o * v, 0.0);
+    THC_TRY(set_state(Zc, zero.data()));
+    // Coulomb parts
+    THC_TRY(mm(P, P, P, rm(Tc.p, P), rm(S.p, P), dn_m1.p, P, 1, 0));
+    THC_TRY(mm(P, P, P, rm(dn_m1.p, P), rm(Tc.p, P), dn_m2.p, P, 1, 0));
+    THC_CUDA(hadamard2(dn_m1.p, PP, vv.p, dn_m2.p, (const T*)nullptr, (const T*)nullptr, st));
+    THC_TRY(mm(o, P, P, rm(yo, P), rm(dn_m1.p, P), dn_q.p, P, 1, 0));
+    THC_TRY(mm(o, o, P, rm(dn_q.p, P), tr(yo, P), dn_oo.p, o, -4, 0));
+    THC_CUDA(hadamard2(dn_m1.p, PP, oo.p, dn_m2.p, (const T*)nullptr, (const T*)nullptr, st));
+    THC_TRY(mm(v, P, P, rm(yv, P), rm(dn_m1.p, P), dn_q.p, P, 1, 0));
+    THC_TRY(mm(v, v, P, rm(dn_q.p, P), tr(yv, P), dn_vv.p, v, 4, 0));
+    // exchange parts: pass 0 over occupied i, pass 1 over virtual a
+    for (int pass = 0; pass < 2; ++pass) {
+        const int R = pass == 0 ? o : v;
+        const T* yr = pass == 0 ? yo : yv;
+        const T* inner = pass == 0 ? vv.p : oo.p;    // A = T diag(y_r) inner
+        const T* mask = pass == 0 ? oo.p : vv.p;     // B = (mask o A) T^T
+        const T* wsum = pass == 0 ? vv.p : oo.p;     // c = sum_X wsum^XY B^XY
+        T* D = pass == 0 ? dn_oo.p : dn_vv.p;
+        const double sign = pass == 0 ? 2.0 : -2.0;
+        for (int r0 = 0; r0 < R; r0 += nbmax) {
+            const int nb = std::min(nbmax, R - r0);
+            // x1[b] = T diag(y_r0+b): T[W][X] y^X  (T symmetric, so this is T^T diag(y))
+            THC_CUDA(scale_rows(Tc.p, P, P, yr, r0, nb, dn_x1.p, st));
+            THC_TRY(mm(P, P, P, rm(dn_x1.p, P), rm(inner, P), dn_x2.p, P, 1, 0, nb, PP, 0, PP));
+            THC_CUDA(hadamard_batched(dn_x2.p, mask, PP, nb, st));
+            THC_TRY(mm(P, P, P, rm(dn_x2.p, P), tr(Tc.p, P), dn_x1.p, P, 1, 0, nb, PP, 0, PP));
+            THC_CUDA(hadamard_batched(dn_x1.p, wsum, PP, nb, st));
+            THC_TRY(mm(1, P, P, View<T>{dn_ones.p, 0, 1}, rm(dn_x1.p, P), dn_c.p, P, 1, 0, nb, 0,
+                       PP, P));
+            THC_TRY(mm(nb, R, P, rm(dn_c.p, P), tr(yr, P), D + (long long)r0 * R, R, sign, 1));
+        }
+    }
+    THC_CUDA(to_double(dn_oo.p, dn_out.p, (long long)o * o, st));
+    THC_CUDA(to_double(dn_vv.p, dn_out.p + (long long)o * o, (long long)v * v, st));
+    THC_CUDA(cudaMemcpyAsync(Doo_out, dn_out.p, sizeof(double) * o * o, cudaMemcpyDefault, st));
+    THC_CUDA(cudaMemcpyAsync(Dvv_out, dn_out.p + (long long)o * o, sizeof(double) * v * v,
+                             cudaMemcpyDefault, st));
+    THC_CUDA(cudaStreamSynchronize(st));
     return Err{};
 }
 

@@ -157,6 +157,11 @@ struct Engine {
     Err d_operator(const T* M, int nb, T* Dout);
     Err alg6(T* sgm);
     Err alg45(T* sgm);
+    // MP2-like one-particle density matrices of the amplitudes encoded by the
+    // THC core Zc (App. II, Eqs. 49-56); D_oo (o x o), D_vv (v x v) float64.
+    Err mp2_density(const double* Zc, double* Doo_out, double* Dvv_out);
+    DBuf<T> dn_x1, dn_x2, dn_c, dn_m1, dn_m2, dn_q, dn_ones, dn_oo, dn_vv, dn_t1;
+    DBuf<double> dn_out;
     Err alg7(T* sgm);
 };
 

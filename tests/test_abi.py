@@ -29,6 +29,7 @@ def test_header_declares_the_abi():
                            "thc_last_error", "thc_mlp_create", "thc_mlp_destroy",
                            "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",
                            "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
+                           "thc_mp2_density",
                            "thc_profile_enable", "thc_profile_read",
                            "thc_residual", "thc_selftest_bounded_wait", "thc_solve",
                            "thc_solve_opts_default", "thc_solve_pairs", "thc_step_name"]

@@ -89,3 +89,16 @@ def test_mixed_t2sq_routes_within_bound(route):
     err = max(np.abs(sig - sig_ref).max(), np.abs(sig1 - r1_ref).max())
     assert err < BOUND[3] * scale
     assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))
+
+
+def test_mixed_mp2_density_within_bound():
+    """App. II density matrices on the tensor cores (bf16x3) against Eqs. 47-48."""
+    import paper_2111_11473_gb300 as pkg
+    from oracle import density, thc
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(8, 60, 120, 200, 80, 13)
+    Doo_ref, Dvv_ref = density.mp2_density(thc.amplitudes(s.Y, Zc, 8))
+    with context(s, precision=pkg.THC_PREC_MIXED) as ctx:
+        Doo, Dvv = ctx.mp2_density(Zc)
+    scale = max(np.abs(Doo_ref).max(), np.abs(Dvv_ref).max())
+    assert np.abs(Doo - Doo_ref).max() < BOUND[3] * scale
+    assert np.abs(Dvv - Dvv_ref).max() < BOUND[3] * scale

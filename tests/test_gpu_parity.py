@@ -132,3 +132,17 @@ def test_t2sq_n5_route_matches_oracle(case):
     assert np.abs(sig - sig_ref).max() < RES_TOL
     assert np.abs(sig1 - r1_ref).max() < RES_TOL
     assert abs(E - E_ref) < 1e-9
+
+
+@pytest.mark.parametrize("case", [(3, 7, 10, 14, 9, 5), (7, 37, 70, 90, 45, 11)],
+                         ids=lambda c: "x".join(map(str, c)))
+def test_mp2_density_matches_oracle(case):
+    """App. II: THC-factorised density matrices (Eqs. 49-56) against Eqs. 47-48."""
+    from oracle import density, thc
+    s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(*case)
+    Doo_ref, Dvv_ref = density.mp2_density(thc.amplitudes(s.Y, Zc, case[0]))
+    with context(s) as ctx:
+        Doo, Dvv = ctx.mp2_density(Zc)
+    scale = max(np.abs(Doo_ref).max(), np.abs(Dvv_ref).max())
+    assert np.abs(Doo - Doo_ref).max() < 1e-12 * max(1.0, scale)
+    assert np.abs(Dvv - Dvv_ref).max() < 1e-12 * max(1.0, scale)

@@ -221,3 +221,34 @@ def test_planted_mistakes_are_caught(name, monkeypatch):
     r1, r2 = cs.residual(H, t1, t2)
     err = max(abs(r2 - q2).max(), abs(r1 - q1).max())
     assert err > 1e-6
+
+
+def test_mp2_density_matches_spin_orbital_and_traces():
+    """App. II Eqs. 47-48 against the spin-orbital density summed over spin;
+    the two blocks have opposite traces and are symmetric for symmetric t2."""
+    from oracle import density, spin_orbital as so
+    rng = np.random.default_rng(41)
+    o, v = 3, 5
+    t2 = rng.standard_normal((o, o, v, v)) * 0.1
+    t2 = 0.5 * (t2 + t2.transpose(1, 0, 3, 2))          # t_ij^ab = t_ji^ba
+    Doo, Dvv = density.mp2_density(t2)
+    _, T2 = so.to_spin_amplitudes(np.zeros((o, v)), t2)
+    Soo, Svv = density.spin_orbital_density(T2, 2 * o)
+    assert np.allclose(Doo, Soo[0::2, 0::2] + Soo[1::2, 1::2], atol=1e-14)
+    assert np.allclose(Dvv, Svv[0::2, 0::2] + Svv[1::2, 1::2], atol=1e-14)
+    assert np.allclose(Doo, Doo.T, atol=1e-14) and np.allclose(Dvv, Dvv.T, atol=1e-14)
+    assert abs(np.trace(Doo) + np.trace(Dvv)) < 1e-13
+
+
+def test_mp2_density_of_a_single_pair_amplitude():
+    """Brute force: one non-zero amplitude pair t_00^01 = t_00^10 = s gives
+    D_00 = -2 s^2 (2 - 1) * 2 terms and D_vv on the 2 x 2 block."""
+    from oracle import density
+    o, v, s = 1, 2, 0.3
+    t2 = np.zeros((o, o, v, v))
+    t2[0, 0, 0, 1] = t2[0, 0, 1, 0] = s
+    Doo, Dvv = density.mp2_density(t2)
+    # D_00 = -2 sum_ab t^ab (2 t^ab - t^ba) = -2 (s (2s - s) + s (2s - s)) = -4 s^2
+    assert Doo[0, 0] == pytest.approx(-4 * s * s)
+    # D_ab = 2 sum_c t^ac (2 t^bc - t^bc) = 2 sum_c t^ac t^bc  (i = j = 0)
+    assert np.allclose(Dvv, 2 * np.array([[s * s, 0], [0, s * s]]))
