@@ -314,6 +314,26 @@ thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
                               double* energy, void* stream);
 
 /*
+ * thc_cp_als - eigenvalue-weighted CP factorisation of the rank-reduced
+ * projectors (Eqs. 15-16, App. I): U_ia^P ~ sum_W y_i^W y_a^W tau^PW,
+ * minimising f = sum_P eps_P^2 sum_ia (U_ia^P - sum_W y_i^W y_a^W tau^PW)^2
+ * by `iters` sweeps of alternating least squares (y_o, then y_v, then tau;
+ * the y_o update is Eq. 16), float64 on the device.  The W x W normal
+ * equations are solved by Cholesky factorisation (App. I uses CG).
+ *   U: (n_occ n_vir) x n_rr row-major, row (i, a) = i n_vir + a
+ *   eps: n_rr projector eigenvalues (any sign)
+ *   y_o: n_occ x rank, y_v: n_vir x rank, tau: n_rr x rank, row-major; the
+ *        start point on entry, the result on return
+ *   objective: nullable host array of `iters` doubles, f after every sweep
+ * All arrays host or device; stream: cudaStream_t or NULL.  Returns
+ * THC_ERR_NUMERIC if a normal-equation matrix stays singular after a ridge
+ * of 1e-12 of its largest diagonal.  No context is needed.
+ */
+thc_status thc_cp_als(int n_occ, int n_vir, int n_rr, int rank, const double* U,
+                      const double* eps, double* y_o, double* y_v, double* tau, int iters,
+                      double* objective, void* stream);
+
+/*
  * thc_selftest_bounded_wait - exercise the bounded-wait path that every
  * waiting kernel of this library uses (TMA and MMA pipelines, the triangle
  * kernel's operand ring).  One thread waits on a shared-memory mbarrier that

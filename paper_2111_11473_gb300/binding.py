@@ -97,6 +97,8 @@ _SIGNATURES = {
                                 C.c_ulonglong, C.POINTER(C.c_double)]),
     "thc_mlp_destroy": (None, [_VP]),
     "thc_selftest_bounded_wait": (C.c_int, [C.c_int, _VP]),
+    "thc_cp_als": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP,
+                             C.c_int, _DP, _VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }
@@ -121,6 +123,29 @@ def load_library(path: str = LIB_PATH):
 
 def exported_symbols():
     return sorted(_SIGNATURES)
+
+
+def cp_als(U, eps, y_o, y_v, tau, iters, stream=None):
+    """Weighted CP-ALS of the projectors (thc_cp_als).  U: (o*v) x N, eps: N,
+    start factors y_o (o x W), y_v (v x W), tau (N x W); returns the updated
+    factors (new numpy arrays) and the objective after every sweep."""
+    lib = load_library()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    yo = np.array(y_o, dtype=np.float64, order="C", copy=True)
+    yv = np.array(y_v, dtype=np.float64, order="C", copy=True)
+    t = np.array(tau, dtype=np.float64, order="C", copy=True)
+    o, W = yo.shape
+    v, N = yv.shape[0], t.shape[0]
+    if U.shape != (o * v, N) or eps.shape != (N,) or yv.shape[1] != W or t.shape[1] != W:
+        raise ValueError("inconsistent CP-ALS shapes")
+    hist = np.zeros(max(1, iters))
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    status = lib.thc_cp_als(o, v, N, W, U.ctypes.data, eps.ctypes.data, yo.ctypes.data,
+                            yv.ctypes.data, t.ctypes.data, int(iters), hist.ctypes.data, _VP(st))
+    if status != 0:
+        raise ThcError(status, lib.thc_last_error(None).decode())
+    return yo, yv, t, list(hist[:iters])
 
 
 def selftest_bounded_wait(complete: bool, stream=None) -> str:

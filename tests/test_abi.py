@@ -24,7 +24,7 @@ def lib():
 
 
 def test_header_declares_the_abi():
-    assert _declared() == ["thc_config_default", "thc_destroy", "thc_energy",
+    assert _declared() == ["thc_config_default", "thc_cp_als", "thc_destroy", "thc_energy",
                            "thc_energy_noalloc", "thc_init",
                            "thc_last_error", "thc_mlp_create", "thc_mlp_destroy",
                            "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",

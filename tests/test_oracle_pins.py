@@ -252,3 +252,48 @@ def test_mp2_density_of_a_single_pair_amplitude():
     assert Doo[0, 0] == pytest.approx(-4 * s * s)
     # D_ab = 2 sum_c t^ac (2 t^bc - t^bc) = 2 sum_c t^ac t^bc  (i = j = 0)
     assert np.allclose(Dvv, 2 * np.array([[s * s, 0], [0, s * s]]))
+
+
+def _planted_cp(o, v, N, W, seed):
+    rng = np.random.default_rng(seed)
+    yo, yv, tau = rng.standard_normal((o, W)), rng.standard_normal((v, W)), rng.standard_normal((N, W))
+    U = (yo[:, None, :] * yv[None, :, :]).reshape(o * v, W) @ tau.T
+    eps = rng.uniform(0.2, 2.0, N) * rng.choice([-1.0, 1.0], N)
+    return U, eps, yo, yv, tau, rng
+
+
+def test_cp_als_updates_are_exact_minimisers():
+    """After each ALS update the gradient of the weighted objective (Eq. 15)
+    with respect to the updated factor vanishes (central differences)."""
+    from oracle import cp_als
+    U, eps, yo, yv, tau, rng = _planted_cp(4, 5, 6, 3, 7)
+    U = U + 0.3 * rng.standard_normal(U.shape)          # not exactly low rank
+    yo0, yv0, t0 = (a + 0.5 * rng.standard_normal(a.shape) for a in (yo, yv, tau))
+    new = cp_als.update_yo(U, eps, yo0, yv0, t0)
+    for upd, which in ((new, 0),):
+        h = 1e-6
+        for idx in np.ndindex(upd.shape):
+            d = np.zeros_like(upd); d[idx] = h
+            fp = cp_als.objective(U, eps, upd + d, yv0, t0)
+            fm = cp_als.objective(U, eps, upd - d, yv0, t0)
+            assert abs(fp - fm) / (2 * h) < 1e-6
+    nv = cp_als.update_yv(U, eps, new, yv0, t0)
+    nt = cp_als.update_tau(U, new, nv)
+    h = 1e-6
+    for idx in np.ndindex(nv.shape):
+        d = np.zeros_like(nv); d[idx] = h
+        g = (cp_als.objective(U, eps, new, nv + d, t0) - cp_als.objective(U, eps, new, nv - d, t0)) / (2 * h)
+        assert abs(g) < 1e-6
+    for idx in np.ndindex(nt.shape):
+        d = np.zeros_like(nt); d[idx] = h
+        g = (cp_als.objective(U, eps, new, nv, nt + d) - cp_als.objective(U, eps, new, nv, nt - d)) / (2 * h)
+        assert abs(g) < 1e-6
+
+
+def test_cp_als_recovers_a_planted_factorisation_monotonically():
+    from oracle import cp_als
+    U, eps, yo, yv, tau, rng = _planted_cp(6, 8, 7, 4, 11)
+    start = [a + 0.1 * rng.standard_normal(a.shape) for a in (yo, yv, tau)]
+    _, _, _, hist = cp_als.als(U, eps, *start, 60)
+    assert all(b <= a * (1 + 1e-12) + 1e-300 for a, b in zip(hist, hist[1:]))
+    assert hist[-1] < 1e-16 * max(1.0, float(np.sum(U ** 2)))
