@@ -247,8 +247,9 @@ thc_status thc_solve_pairs(thc_ctx* ctx, float* X, float* j, float* t, long long
  * Per-step device timing (CUDA events recorded on the context's stream
  * around every step of thc_residual while profiling is on).  flops counts
  * the algorithmic floating-point operations the step issued (2 per
- * multiply-add of every contraction; 5 per (I,X,Y,Z) term of the triangle
- * kernel), so flops / ms is the achieved rate of that step.
+ * multiply-add of every contraction; 5 per (I,X,Y,Z) term of the float32
+ * triangle kernel, 3.5 for the float64 one, which shares t between the
+ * mirror terms (Y,Z) and (Z,Y)), so flops / ms is the achieved rate of that step.
  */
 enum {
     THC_STEP_DRESS = 0,      /* T1 dressing of the Cholesky vectors (Eqs. 25-27) */

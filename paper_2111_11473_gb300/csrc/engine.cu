@@ -625,7 +625,11 @@ Err Engine<T>::alg6(T* sgm) {
         }
         // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
         seg_begin(THC_STEP_TRIANGLE);
-        if (prof.on) prof.flops[THC_STEP_TRIANGLE] += 5.0 * nI * (double)P * P * P;
+        // 5 flops per (I, X, Y, Z); the float64 kernel shares t between the
+        // mirror outputs (Y, Z) and (Z, Y): 7 flops per pair
+        if (prof.on)
+            prof.flops[THC_STEP_TRIANGLE] +=
+                (std::is_same<T, double>::value ? 3.5 : 5.0) * nI * (double)P * P * P;
         THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st, tcerr.p));
         seg_end();
     }

@@ -277,6 +277,128 @@ __global__ void __launch_bounds__(256) k_triangle(T* H, const T* E, const T* F,
 // G_I[Y-tile][Z-tile] in shared memory through a 3-stage cp.async pipeline.
 // Each thread issues 3 FMA-pipe instructions per (I, X, Y, Z); G is read by
 // warp-wide broadcast, E and F by conflict-free 128-bit loads (row pad 4).
+// Float64 triangle kernel over pairs of mirror (Y, Z) tiles.
+// t^XYZ = E^XY F^XZ + E^XZ F^XY is symmetric in (Y, Z), so one t feeds both
+// H^XYZ += t G^YZ and H^XZY += t G^ZY: 7 flops per two outputs (two FP64
+// FMA-pipe operations per output instead of three).  A block owns 4 X and the
+// tiles (Y0, Z0), (Z0, Y0) with Y0 <= Z0; on a diagonal pair (Y0 = Z0) both
+// accumulators land on the same tile, count every element twice, and are
+// halved and added one after the other.
+constexpr int SIST = 2;
+
+__global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double* E,
+                                                        const double* F, const double* G,
+                                                        int P, int nI) {
+    __shared__ double sG1[SIST][TYZ][TYZ + 1];   // G^YZ, rows Y
+    __shared__ double sG2[SIST][TYZ][TYZ + 1];   // G^ZY, rows Z
+    __shared__ double sEy[SIST][TXB][TYZ], sEz[SIST][TXB][TYZ];
+    __shared__ double sFy[SIST][TXB][TYZ], sFz[SIST][TXB][TYZ];
+    const int nb = (P + TYZ - 1) / TYZ;
+    int pidx = blockIdx.x, Yb = 0;
+    while (pidx >= nb - Yb) {
+        pidx -= nb - Yb;
+        ++Yb;
+    }
+    const int Zb = Yb + pidx;
+    const int Y0 = Yb * TYZ, Z0 = Zb * TYZ, X0 = blockIdx.y * TXB;
+    const bool diag = Yb == Zb;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const long long PP = (long long)P * P;
+    double a1[TXB][2][2], a2[TXB][2][2];
+#pragma unroll
+    for (int x = 0; x < TXB; ++x)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) a1[x][i][j] = a2[x][i][j] = 0;
+    for (int I0 = 0; I0 < nI; I0 += SIST) {
+        for (int e = tid; e < SIST * TYZ * TYZ; e += 256) {
+            const int st = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
+            const int I = I0 + st;
+            const bool ok = I < nI;
+            sG1[st][r][c] = (ok && Y0 + r < P && Z0 + c < P)
+                                ? G[I * PP + (long long)(Y0 + r) * P + Z0 + c] : 0.0;
+            sG2[st][r][c] = (ok && Z0 + r < P && Y0 + c < P)
+                                ? G[I * PP + (long long)(Z0 + r) * P + Y0 + c] : 0.0;
+        }
+        for (int e = tid; e < SIST * TXB * TYZ; e += 256) {
+            const int st = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
+            const int I = I0 + st, X = X0 + x;
+            const bool okx = I < nI && X < P;
+            const long long base = I * PP + (long long)X * P;
+            sEy[st][x][c] = (okx && Y0 + c < P) ? E[base + Y0 + c] : 0.0;
+            sEz[st][x][c] = (okx && Z0 + c < P) ? E[base + Z0 + c] : 0.0;
+            sFy[st][x][c] = (okx && Y0 + c < P) ? F[base + Y0 + c] : 0.0;
+            sFz[st][x][c] = (okx && Z0 + c < P) ? F[base + Z0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int st = 0; st < SIST; ++st) {
+            double g1[2][2], g2[2][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    g1[i][j] = sG1[st][ty + 16 * i][tx + 16 * j];   // G^(Y_i, Z_j)
+                    g2[i][j] = sG2[st][tx + 16 * j][ty + 16 * i];   // G^(Z_j, Y_i)
+                }
+#pragma unroll
+            for (int x = 0; x < TXB; ++x) {
+                double ey[2], fy[2], ez[2], fz[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    ey[i] = sEy[st][x][ty + 16 * i];
+                    fy[i] = sFy[st][x][ty + 16 * i];
+                    ez[i] = sEz[st][x][tx + 16 * i];
+                    fz[i] = sFz[st][x][tx + 16 * i];
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        double t = ey[i] * fz[j];
+                        t = fma(ez[j], fy[i], t);
+                        a1[x][i][j] = fma(t, g1[i][j], a1[x][i][j]);
+                        a2[x][i][j] = fma(t, g2[i][j], a2[x][i][j]);
+                    }
+            }
+        }
+        __syncthreads();
+    }
+    const double scale = diag ? 0.5 : 1.0;
+#pragma unroll
+    for (int x = 0; x < TXB; ++x) {
+        const int X = X0 + x;
+        if (X >= P) continue;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int Y = Y0 + ty + 16 * i;
+            if (Y >= P) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int Z = Z0 + tx + 16 * j;
+                if (Z < P) H[((long long)X * P + Y) * P + Z] += scale * a1[x][i][j];
+            }
+        }
+    }
+    if (diag) __syncthreads();   // a2 targets overlap other threads' a1 targets
+#pragma unroll
+    for (int x = 0; x < TXB; ++x) {
+        const int X = X0 + x;
+        if (X >= P) continue;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int Y = Y0 + ty + 16 * i;
+            if (Y >= P) continue;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int Z = Z0 + tx + 16 * j;
+                if (Z < P) H[((long long)X * P + Z) * P + Y] += scale * a2[x][i][j];
+            }
+        }
+    }
+}
+
 constexpr int TT = 32, TROW = 2 * TT + 4, TGROW = TT + 4, TSTAGES = 3;
 
 struct TriStage {
@@ -866,8 +988,14 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
         count_launches(1);
         return cudaGetLastError();
     }
-    dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
-    k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+    if constexpr (std::is_same<T, double>::value) {
+        const unsigned nb = cdiv(P, TYZ);
+        dim3 grid(nb * (nb + 1) / 2, cdiv(P, TXB));
+        k_triangle_sym64<<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+    } else {
+        dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
+        k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
