@@ -247,11 +247,18 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     st = s;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
     {
-        // Cholesky slab: as many vectors as 2 GiB of per-vector scratch holds
-        // (six P x P intermediates dominate), at least 16.
+        // Cholesky slab: as many vectors as the per-vector scratch budget holds
+        // (six P x P intermediates dominate), at least 16.  The budget is a
+        // tenth of the free device memory, between 2 and 16 GiB: fewer, longer
+        // slabs mean fewer launches of the slab pass's many small products.
         const long long per = 6LL * cfg.n_p * cfg.n_p + 2LL * cfg.n_vir * cfg.n_vir +
                               8LL * (cfg.n_occ + cfg.n_vir) * cfg.n_p;
-        const long long fit = (2LL << 30) / (per * (long long)sizeof(T));
+        size_t free_b = 0, total_b = 0;
+        long long budget = 2LL << 30;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            budget = std::max<long long>(budget, std::min<long long>(16LL << 30,
+                                                                     (long long)(free_b / 10)));
+        const long long fit = budget / (per * (long long)sizeof(T));
         kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, cfg.n_k)
                             : (int)std::max<long long>(1, std::min<long long>(
                                   cfg.n_k, std::max<long long>(16, fit)));
