@@ -266,7 +266,7 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
                                precision=pkg.THC_PREC_FP64, stream=stream)
     f = None
     if not args.skip_fp64_solve:
-        f = precond.run_solve(fp64_ctx, None, None, r_tol=1e-8, max_iter=60)
+        f = precond.run_solve(fp64_ctx, None, None, r_tol=args.fp64_rtol, max_iter=60)
         f["evals_per_s"] = None
         out["fp64"] = f
     if fp64_ctx is not ctx:
@@ -336,6 +336,8 @@ def main():
                     help="system from synth.CONFIGS (named by size)")
     ap.add_argument("--skip-fp64-solve", action="store_true",
                     help="no float64 solve (sizes where it takes too long)")
+    ap.add_argument("--fp64-rtol", type=float, default=1e-8,
+                    help="residual tolerance of the float64 reference solve")
     ap.add_argument("--t2sq-route", type=int, default=0, choices=[0, 1, 2],
                     help="Eqs. 32-33: 0 automatic, 1 Alg. 6 (O(N^4)), 2 Algs. 4-5 (O(N^5))")
     ap.add_argument("--fp64-iters", type=int, default=0,

@@ -124,16 +124,6 @@ __global__ void k_eps_t1(const T* eps, const T* t1, int o, int v, T* out) {
 }
 
 template <typename T>
-__global__ void k_traces(const T* M, int n, int nb, T* d) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nb) return;
-    const T* m = M + (long long)a * n * n;
-    T acc = 0;
-    for (int k = 0; k < n; ++k) acc += m[(long long)k * n + k];
-    d[a] = acc;
-}
-
-template <typename T>
 __global__ void k_lincomb(T* out, long long n, double a, const T* x, double b,
                           const T* y, double c, const T* z) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -906,13 +896,6 @@ cudaError_t eps_t1(const T* eps, const T* t1, int o, int v, T* out, cudaStream_t
 }
 
 template <typename T>
-cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s) {
-    k_traces<T><<<cdiv(nb, 128), 128, 0, s>>>(M, n, nb, d);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t lincomb(T* out, long long n, double a, const T* x, double b, const T* y,
                     double c, const T* z, cudaStream_t s) {
     k_lincomb<T><<<nblocks(n), NT, 0, s>>>(out, n, a, x, b, y, c, z);
@@ -1043,7 +1026,6 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
                                         cudaStream_t);                                  \
     template cudaError_t w_single<T>(const T*, int, const T*, const T*, T*, int, int,  \
                                      cudaStream_t);                                     \
-    template cudaError_t traces<T>(const T*, int, int, T*, cudaStream_t);               \
     template cudaError_t eps_t1<T>(const T*, const T*, int, int, T*, cudaStream_t);     \
     template cudaError_t lincomb<T>(T*, long long, double, const T*, double, const T*, \
                                     double, const T*, cudaStream_t);                    \

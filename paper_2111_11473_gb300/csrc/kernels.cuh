@@ -46,10 +46,6 @@ cudaError_t w_single(const T* TA, int ldta, const T* Tc, const T* E, T* W, int P
 template <typename T>
 cudaError_t eps_t1(const T* eps, const T* t1, int o, int v, T* out, cudaStream_t s);
 
-// d[a] = trace(M[a]) for nb n x n matrices.
-template <typename T>
-cudaError_t traces(const T* M, int n, int nb, T* d, cudaStream_t s);
-
 // out = a*x + b*y + c*z element-wise (z may be null).
 template <typename T>
 cudaError_t lincomb(T* out, long long n, double a, const T* x, double b,
