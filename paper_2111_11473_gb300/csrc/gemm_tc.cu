@@ -192,7 +192,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // warp 1 issues the MMAs into one of two tensor-memory accumulators, and
 // warps 2-5 drain the other accumulator to C, so that the epilogue of one
 // tile overlaps the main loop of the next.  Tiles are taken round-robin.
-template <int BN>
+template <int BN, bool RMW>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
@@ -336,31 +336,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 const int j0 = c.n0 + c0;
-                auto put = [&](float* p, float val) {
-                    if (args.splits > 1) *p = val;
-                    else *p = args.beta != 0.f ? fmaf(args.beta, *p, args.alpha * val) : args.alpha * val;
-                };
+                // RMW (beta != 0, no split): the 32 old values of C are loaded
+                // before any is used, so that their latencies overlap.
+                constexpr bool rmw = RMW;
                 if (args.ccs == 1) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         stg[lane * 33 + j] = c.nk > 0 ? __uint_as_float(r[j]) : 0.f;
                     __syncwarp();
                     const int j = j0 + lane;
+                    const bool jok = j < args.N;
+                    float old[32];
+                    if constexpr (rmw) {
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int i = i_base + rr;
+                            old[rr] = (jok && i < args.M) ? Cb[(long long)i * args.crs + j] : 0.f;
+                        }
+                    }
+                    if constexpr (rmw) {
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int i = i_base + rr;
+                            if (i < args.M && jok)
+                                Cb[(long long)i * args.crs + j] =
+                                    fmaf(args.beta, old[rr], args.alpha * stg[rr * 33 + lane]);
+                        }
+                    } else {
 #pragma unroll 4
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const int i = i_base + rr;
-                        if (i < args.M && j < args.N)
-                            put(Cb + (long long)i * args.crs + j, stg[rr * 33 + lane]);
+                        for (int rr = 0; rr < 32; ++rr) {
+                            const int i = i_base + rr;
+                            if (i < args.M && jok) {
+                                const float val = stg[rr * 33 + lane];
+                                Cb[(long long)i * args.crs + j] =
+                                    args.splits > 1 ? val : args.alpha * val;
+                            }
+                        }
                     }
                     __syncwarp();
                 } else {
                     const int i = i_base + lane;
                     if (i < args.M) {
+                        float old[32];
+                        if constexpr (rmw) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                old[j] = (j0 + j < args.N)
+                                             ? Cb[(long long)i * args.crs + (long long)(j0 + j) * args.ccs]
+                                             : 0.f;
+                        }
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            if (j0 + j >= args.N) break;
-                            put(Cb + (long long)i * args.crs + (long long)(j0 + j) * args.ccs,
-                                c.nk > 0 ? __uint_as_float(r[j]) : 0.f);
+                            if (j0 + j < args.N) {
+                                const float val = c.nk > 0 ? __uint_as_float(r[j]) : 0.f;
+                                float* p = Cb + (long long)i * args.crs + (long long)(j0 + j) * args.ccs;
+                                if constexpr (rmw) *p = fmaf(args.beta, old[j], args.alpha * val);
+                                else *p = args.splits > 1 ? val : args.alpha * val;
+                            }
                         }
                     }
                 }
@@ -491,8 +523,11 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) 
     const int smem = (int)sizeof(TcSmem<BN>) + 1024;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN>,
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_tc<BN, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -504,7 +539,10 @@ cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) 
     });
     const long long sms = g_sms > 0 ? g_sms : 152;
     const unsigned grid = (unsigned)std::min<long long>(a.ntiles, sms);
-    k_gemm_tc<BN><<<grid, kTcThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    if (a.splits == 1 && a.beta != 0.f)
+        k_gemm_tc<BN, true><<<grid, kTcThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
+    else
+        k_gemm_tc<BN, false><<<grid, kTcThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);
     count_launches(1);
     return cudaGetLastError();
 }
