@@ -335,6 +335,20 @@ thc_status thc_cp_als(int n_occ, int n_vir, int n_rr, int rank, const double* U,
                       double* objective, void* stream);
 
 /*
+ * thc_selftest_gemm - randomised check of the tensor-core product (tcgen05,
+ * bf16 hi/lo) against the CUDA-core product on the same float32 operands:
+ * `cases` random shapes (M, N <= 700, K <= 900, batch <= 4), transposed and
+ * plain operands, separate / shared / batch-reduced batches, split-K, beta
+ * 0 or 0.5, three or one bf16 products.  *max_rel_err (nullable) = largest
+ * bf16x3 difference relative to max(1, max|C|); *failures (nullable) =
+ * cases outside the bound of their arithmetic (bf16x3: 2e-5 sqrt(K+1),
+ * bf16: 2e-2 sqrt(K+1), times sqrt(batch) when batch-reduced).  Returns
+ * THC_ERR_NUMERIC if any case fails.  Diagnostic; no counterpart in the paper.
+ */
+thc_status thc_selftest_gemm(int cases, unsigned long long seed, double* max_rel_err,
+                             int* failures, void* stream);
+
+/*
  * thc_selftest_bounded_wait - exercise the bounded-wait path that every
  * waiting kernel of this library uses (TMA and MMA pipelines, the triangle
  * kernel's operand ring).  One thread waits on a shared-memory mbarrier that

@@ -97,6 +97,8 @@ _SIGNATURES = {
                                 C.c_ulonglong, C.POINTER(C.c_double)]),
     "thc_mlp_destroy": (None, [_VP]),
     "thc_selftest_bounded_wait": (C.c_int, [C.c_int, _VP]),
+    "thc_selftest_gemm": (C.c_int, [C.c_int, C.c_ulonglong, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_int), _VP]),
     "thc_cp_als": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP,
                              C.c_int, _DP, _VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
@@ -146,6 +148,17 @@ def cp_als(U, eps, y_o, y_v, tau, iters, stream=None):
     if status != 0:
         raise ThcError(status, lib.thc_last_error(None).decode())
     return yo, yv, t, list(hist[:iters])
+
+
+def selftest_gemm(cases=64, seed=0, stream=None):
+    """Randomised tensor-core vs CUDA-core product check; returns
+    (status name, max bf16x3 relative difference, failures)."""
+    lib = load_library()
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    mr = C.c_double(0)
+    nf = C.c_int(0)
+    status = lib.thc_selftest_gemm(int(cases), int(seed), C.byref(mr), C.byref(nf), _VP(st))
+    return STATUS.get(status, "?"), mr.value, nf.value
 
 
 def selftest_bounded_wait(complete: bool, stream=None) -> str:

@@ -327,6 +327,25 @@ void thc_mlp_destroy(thc_mlp* m) {
     delete m;
 }
 
+thc_status thc_selftest_gemm(int cases, unsigned long long seed, double* max_rel_err,
+                             int* failures, void* stream) {
+    if (cases < 0) return THC_ERR_ARG;
+    double mr = 0;
+    int nf = 0;
+    cudaError_t e = thc::gemm_tc_selftest(cases, seed, &mr, &nf, (cudaStream_t)stream);
+    if (max_rel_err) *max_rel_err = mr;
+    if (failures) *failures = nf;
+    if (e != cudaSuccess) {
+        g_init_error = std::string("thc_selftest_gemm: ") + cudaGetErrorString(e);
+        return THC_ERR_CUDA;
+    }
+    if (nf) {
+        g_init_error = "thc_selftest_gemm: " + std::to_string(nf) + " case(s) outside the bound";
+        return THC_ERR_NUMERIC;
+    }
+    return THC_OK;
+}
+
 thc_status thc_selftest_bounded_wait(int complete, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     int* flag = nullptr;

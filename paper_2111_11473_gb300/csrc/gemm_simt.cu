@@ -3,8 +3,8 @@
 // This is the float64 contraction engine of the library (tcgen05 has no
 // float64 kind) and the float32 reference path.  Every operand is a strided
 // view, so transposes, shared (stride-0) batch operands and column slices of
-// row-major arrays need no copies.  Tile 64 x 64 x 16, 256 threads, a 4 x 4
-// register tile per thread, double-buffered shared memory.
+// row-major arrays need no copies.  Tiles of 64 or 80 per side (chosen per
+// product to pad least) x 16, 256 threads, double-buffered shared memory.
 #include <algorithm>
 
 #include <atomic>
@@ -21,73 +21,72 @@ void count_launches(int n) { g_launches += n; }
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
-template <typename T>
+template <typename T, int BM, int BN>
 struct Smem {
     T a[2][BK][BM + 1];
     T b[2][BK][BN + 1];
 };
 
-template <typename T>
-__device__ __forceinline__ void load_tiles(const Gemm<T>& g, int b, int k0,
-                                           int m0, int n0, T (&ra)[4],
-                                           T (&rb)[4], bool a_kfast,
+// Element e of a BM x BK (or BN x BK) tile for thread t: e = t + 256 j,
+// coalesced along whichever index of the operand is contiguous.
+template <typename T, int BM, int BN>
+__device__ __forceinline__ void load_tiles(const Gemm<T>& g, int b, int k0, int m0, int n0,
+                                           T (&ra)[BM / 16], T (&rb)[BN / 16], bool a_kfast,
                                            bool b_kfast) {
     const int t = threadIdx.x;
     const T* A = g.A.p + (long long)b * g.sAb;
     const T* B = g.B.p + (long long)b * g.sBb;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int m, k;
-        if (a_kfast) { k = t & 15; m = (t >> 4) + 16 * j; }
-        else         { m = t & 63; k = (t >> 6) + 4 * j; }
-        int gm = m0 + m, gk = k0 + k;
+    for (int j = 0; j < BM / 16; ++j) {
+        const int e = t + NT * j;
+        const int m = a_kfast ? e / BK : e % BM, k = a_kfast ? e % BK : e / BM;
+        const int gm = m0 + m, gk = k0 + k;
         ra[j] = (gm < g.M && gk < g.K) ? A[gm * g.A.rs + gk * g.A.cs] : T(0);
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int n, k;
-        if (b_kfast) { k = t & 15; n = (t >> 4) + 16 * j; }
-        else         { n = t & 63; k = (t >> 6) + 4 * j; }
-        int gn = n0 + n, gk = k0 + k;
+    for (int j = 0; j < BN / 16; ++j) {
+        const int e = t + NT * j;
+        const int n = b_kfast ? e / BK : e % BN, k = b_kfast ? e % BK : e / BN;
+        const int gn = n0 + n, gk = k0 + k;
         rb[j] = (gn < g.N && gk < g.K) ? B[gk * g.B.rs + gn * g.B.cs] : T(0);
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void store_tiles(Smem<T>& sm, int buf, const T (&ra)[4],
-                                            const T (&rb)[4], bool a_kfast,
-                                            bool b_kfast) {
+template <typename T, int BM, int BN>
+__device__ __forceinline__ void store_tiles(Smem<T, BM, BN>& sm, int buf, const T (&ra)[BM / 16],
+                                            const T (&rb)[BN / 16], bool a_kfast, bool b_kfast) {
     const int t = threadIdx.x;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int m, k;
-        if (a_kfast) { k = t & 15; m = (t >> 4) + 16 * j; }
-        else         { m = t & 63; k = (t >> 6) + 4 * j; }
+    for (int j = 0; j < BM / 16; ++j) {
+        const int e = t + NT * j;
+        const int m = a_kfast ? e / BK : e % BM, k = a_kfast ? e % BK : e / BM;
         sm.a[buf][k][m] = ra[j];
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int n, k;
-        if (b_kfast) { k = t & 15; n = (t >> 4) + 16 * j; }
-        else         { n = t & 63; k = (t >> 6) + 4 * j; }
+    for (int j = 0; j < BN / 16; ++j) {
+        const int e = t + NT * j;
+        const int n = b_kfast ? e / BK : e % BN, k = b_kfast ? e % BK : e / BN;
         sm.b[buf][k][n] = rb[j];
     }
 }
 
-template <typename T>
+// BM x BN x 16 tiles (BM, BN in {64, 80}), 256 threads, a (BM/16) x (BN/16)
+// register tile per thread, double-buffered shared memory.
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(NT) gemm_kernel(const Gemm<T> g) {
-    __shared__ Smem<T> sm;
+    __shared__ Smem<T, BM, BN> sm;
+    constexpr int RI = BM / 16, RJ = BN / 16;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const bool a_kfast = (g.A.cs == 1) || (g.A.rs != 1 && g.A.cs < g.A.rs);
     const bool b_kfast = (g.B.rs == 1) || (g.B.cs != 1 && g.B.rs < g.B.cs);
-    T acc[4][4];
+    T acc[RI][RJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int j = 0; j < RJ; ++j) acc[i][j] = T(0);
 
     // blockIdx.z = (batch index, split index); a split owns a contiguous
     // range of the (batch, k-tile) steps it accumulates.
@@ -99,11 +98,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const Gemm<T> g) {
     const int chunk = (nsteps + g.splits - 1) / g.splits;
     const int s_lo = split * chunk;
     const int s_hi = min(nsteps, s_lo + chunk);
-    T ra[4], rb[4];
+    T ra[RI], rb[RJ];
     if (s_lo < s_hi) {
-        load_tiles(g, b_lo + s_lo / ktiles, (s_lo % ktiles) * BK, m0, n0, ra, rb,
-                   a_kfast, b_kfast);
-        store_tiles(sm, 0, ra, rb, a_kfast, b_kfast);
+        load_tiles<T, BM, BN>(g, b_lo + s_lo / ktiles, (s_lo % ktiles) * BK, m0, n0, ra, rb,
+                              a_kfast, b_kfast);
+        store_tiles<T, BM, BN>(sm, 0, ra, rb, a_kfast, b_kfast);
     }
     __syncthreads();
     for (int step = s_lo; step < s_hi; ++step) {
@@ -111,32 +110,32 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const Gemm<T> g) {
         const bool more = step + 1 < s_hi;
         if (more) {
             int nb = b_lo + (step + 1) / ktiles, nk = ((step + 1) % ktiles) * BK;
-            load_tiles(g, nb, nk, m0, n0, ra, rb, a_kfast, b_kfast);
+            load_tiles<T, BM, BN>(g, nb, nk, m0, n0, ra, rb, a_kfast, b_kfast);
         }
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            T a[4], b[4];
+            T a[RI], b[RJ];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sm.a[buf][kk][ty + 16 * i];
+            for (int i = 0; i < RI; ++i) a[i] = sm.a[buf][kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sm.b[buf][kk][tx + 16 * j];
+            for (int j = 0; j < RJ; ++j) b[j] = sm.b[buf][kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RI; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < RJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
-        if (more) store_tiles(sm, buf ^ 1, ra, rb, a_kfast, b_kfast);
+        if (more) store_tiles<T, BM, BN>(sm, buf ^ 1, ra, rb, a_kfast, b_kfast);
         __syncthreads();
     }
     if (g.splits > 1) {
         // Raw partial sums; gemm_splitk_reduce applies alpha and beta.
         T* Wp = g.ws + (long long)blockIdx.z * g.M * g.N;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < RI; ++i) {
             int m = m0 + ty + 16 * i;
             if (m >= g.M) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < RJ; ++j) {
                 int n = n0 + tx + 16 * j;
                 if (n < g.N) Wp[(long long)m * g.N + n] = acc[i][j];
             }
@@ -146,11 +145,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const Gemm<T> g) {
     T* C = g.C + (g.reduce ? 0 : (long long)bz * g.sCb);
     const T alpha = T(g.alpha), beta = T(g.beta);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
         int m = m0 + ty + 16 * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < RJ; ++j) {
             int n = n0 + tx + 16 * j;
             if (n >= g.N) continue;
             T* c = C + (long long)m * g.ldc + n;
@@ -182,12 +181,42 @@ __global__ void gemm_splitk_reduce(const Gemm<T> g) {
 
 constexpr int kTargetBlocks = 2 * 152;
 
+// Tile edges (64 or 80 per side): the pair that pads the product least
+// (e.g. 400 = 5 x 80 instead of 7 x 64 = 448), among those that still give
+// two waves of blocks, directly or through split-K (ksteps 16-deep steps
+// allow up to ksteps / 16 splits); 64 x 64 when none does or on a tie.
+void tile_edges(long long M, long long N, long long nb, long long ksteps, int* BM, int* BN) {
+    *BM = 64;
+    *BN = 64;
+    long long best = (long long)cdiv(M, 64) * 64 * cdiv(N, 64) * 64;
+    for (int bm : {64, 80})
+        for (int bn : {64, 80}) {
+            const long long tiles = (long long)cdiv(M, bm) * cdiv(N, bn) * nb;
+            const long long area = (long long)cdiv(M, bm) * bm * cdiv(N, bn) * bn;
+            const long long reach = tiles * std::max(1LL, ksteps >= 32 ? ksteps / 16 : 1);
+            if (reach >= 2 * 152 && area < best) {
+                best = area;
+                *BM = bm;
+                *BN = bn;
+            }
+        }
+}
+
+template <typename T, int BM, int BN>
+cudaError_t run(const Gemm<T>& g, dim3 grid, cudaStream_t s) {
+    gemm_kernel<T, BM, BN><<<grid, NT, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch(Gemm<T> g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     if (g.K <= 0) {
         g.K = 0;   // C = beta C
     }
+    int BM = 64, BN = 64;
+    tile_edges(g.M, g.N, g.reduce ? 1 : g.batch,
+               (long long)(g.reduce ? g.batch : 1) * ((g.K + BK - 1) / BK), &BM, &BN);
     const long long tiles = (long long)cdiv(g.N, BN) * cdiv(g.M, BM) * (g.reduce ? 1 : g.batch);
     const long long ksteps = (long long)(g.reduce ? g.batch : 1) * ((g.K + BK - 1) / BK);
     int splits = 1;
@@ -201,7 +230,12 @@ cudaError_t launch(Gemm<T> g, cudaStream_t s) {
     g.splits = splits;
     dim3 grid(cdiv(g.N, BN), cdiv(g.M, BM), (g.reduce ? 1 : g.batch) * splits);
     if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidValue;
-    gemm_kernel<T><<<grid, NT, 0, s>>>(g);
+    cudaError_t e;
+    if (BM == 64 && BN == 64) e = run<T, 64, 64>(g, grid, s);
+    else if (BM == 64) e = run<T, 64, 80>(g, grid, s);
+    else if (BN == 64) e = run<T, 80, 64>(g, grid, s);
+    else e = run<T, 80, 80>(g, grid, s);
+    if (e != cudaSuccess) return e;
     count_launches(splits > 1 ? 2 : 1);
     if (splits > 1) {
         long long total = (long long)g.M * g.N * (g.reduce ? 1 : g.batch);

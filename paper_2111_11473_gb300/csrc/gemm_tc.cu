@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -765,6 +766,133 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
         count_launches(1);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+
+// ---------------------------------------------------------------------------
+// Randomised self-test: tensor-core products against the CUDA-core products
+// of the same float32 operands over random shapes, orientations, batch modes
+// (separate, shared operand, batch-reduced), split-K and beta.
+namespace {
+
+unsigned long long st_next(unsigned long long& s) {
+    s ^= s << 13;
+    s ^= s >> 7;
+    s ^= s << 17;
+    return s;
+}
+
+__global__ void k_fill_uniform(float* p, long long n, unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        p[i] = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 0.5f;
+    }
+}
+
+__global__ void k_max_abs_diff(const float* a, const float* b, long long n, float* out) {
+    float m = 0.f, s = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        m = fmaxf(m, fabsf(a[i] - b[i]));
+        s = fmaxf(s, fabsf(b[i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+        s = fmaxf(s, __shfl_down_sync(0xffffffffu, s, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+        atomicMax(reinterpret_cast<int*>(out + 1), __float_as_int(s));
+    }
+}
+
+}  // namespace
+
+cudaError_t gemm_tc_selftest(int cases, unsigned long long seed, double* max_rel,
+                             int* failures, cudaStream_t st) {
+    *max_rel = 0;
+    *failures = 0;
+    const long long cap = 1LL << 22;   // elements per operand buffer
+    float *A = nullptr, *B = nullptr, *C1 = nullptr, *C2 = nullptr, *red = nullptr, *simt = nullptr;
+    TcWorkspace ws{};
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void**)&A, cap * 4);
+    al((void**)&B, cap * 4);
+    al((void**)&C1, cap * 4);
+    al((void**)&C2, cap * 4);
+    al((void**)&red, 8);
+    al((void**)&simt, cap * 4);
+    ws.elems = (size_t)1 << 25;
+    al((void**)&ws.buf, ws.elems * 2);
+    ws.partial_elems = (size_t)1 << 24;
+    al((void**)&ws.partial, ws.partial_elems * 4);
+    al((void**)&ws.err, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.err, 0, 4, st);
+    unsigned long long s = seed * 2654435761ULL + 1;
+    for (int c = 0; c < cases && e == cudaSuccess; ++c) {
+        Gemm<float> g;
+        g.M = 1 + (int)(st_next(s) % 700);
+        g.N = 1 + (int)(st_next(s) % 700);
+        g.K = 1 + (int)(st_next(s) % 900);
+        g.batch = 1 + (int)(st_next(s) % 4);
+        const int mode = (int)(st_next(s) % 4);   // 0 separate, 1 shared A, 2 shared B, 3 reduce
+        g.reduce = mode == 3 && g.batch > 1;
+        const bool ta = st_next(s) & 1, tb = st_next(s) & 1;
+        const int nprod = (st_next(s) % 3 == 0) ? 1 : 3;
+        g.beta = (st_next(s) & 1) ? 0.5 : 0.0;
+        g.alpha = 1.25;
+        while ((long long)g.batch * g.M * g.K > cap || (long long)g.batch * g.K * g.N > cap ||
+               (long long)g.batch * g.M * g.N > cap)
+            g.K = std::max(1, g.K / 2), g.M = std::max(1, g.M * 3 / 4);
+        const long long sa = (long long)g.M * g.K, sb = (long long)g.K * g.N,
+                        sc = (long long)g.M * g.N;
+        g.A = ta ? View<float>{A, 1, g.M} : View<float>{A, g.K, 1};
+        g.B = tb ? View<float>{B, 1, g.K} : View<float>{B, g.N, 1};
+        g.sAb = mode == 1 ? 0 : sa;
+        g.sBb = mode == 2 ? 0 : sb;
+        g.ldc = g.N;
+        g.sCb = sc;
+        const long long nC = (g.reduce ? 1 : g.batch) * sc;
+        k_fill_uniform<<<256, 256, 0, st>>>(A, g.batch * sa, st_next(s));
+        k_fill_uniform<<<256, 256, 0, st>>>(B, g.batch * sb, st_next(s));
+        k_fill_uniform<<<256, 256, 0, st>>>(C1, nC, st_next(s));
+        count_launches(3);
+        if ((e = cudaMemcpyAsync(C2, C1, nC * 4, cudaMemcpyDeviceToDevice, st))) break;
+        Gemm<float> h = g;
+        g.C = C1;
+        h.C = C2;
+        h.ws = simt;
+        h.ws_elems = cap;
+        if ((e = gemm_tc(g, ws, nprod, st))) break;
+        if ((e = gemm_simt(h, st))) break;
+        if ((e = cudaMemsetAsync(red, 0, 8, st))) break;
+        k_max_abs_diff<<<256, 256, 0, st>>>(C1, C2, nC, red);
+        count_launches(1);
+        float hr[2] = {0, 0};
+        int herr = 0;
+        if ((e = cudaMemcpyAsync(hr, red, 8, cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaMemcpyAsync(&herr, ws.err, 4, cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaStreamSynchronize(st))) break;
+        // bf16x3: about 3 x 2^-17 per product, float32 sums over K terms;
+        // bf16x1: 2^-8 per factor
+        const double scale = std::max(1.0f, hr[1]);
+        const double rel = hr[0] / scale;
+        const double bound = (nprod == 3 ? 2e-5 : 2e-2) * std::sqrt((double)g.K + 1) *
+                             (g.reduce ? std::sqrt((double)g.batch) : 1.0);
+        *max_rel = std::max(*max_rel, nprod == 3 ? rel : 0.0);
+        if (herr || !(rel <= bound)) ++*failures;
+    }
+    for (void* p : {(void*)A, (void*)B, (void*)C1, (void*)C2, (void*)red, (void*)simt,
+                    (void*)ws.buf, (void*)ws.partial, (void*)ws.err})
+        if (p) cudaFree(p);
     return e;
 }
 

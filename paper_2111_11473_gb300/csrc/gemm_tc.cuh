@@ -55,6 +55,14 @@ struct PackCache {
     void release();
 };
 
+// Randomised comparison of gemm_tc with gemm_simt on the same float32 data:
+// `cases` random shapes (M, N <= 700, K <= 900, batch <= 4), orientations,
+// batch modes, beta and product counts.  *max_rel = the largest bf16x3
+// difference relative to max(1, max |C|); *failures counts cases outside
+// the arithmetic's bound (or with an expired wait).
+cudaError_t gemm_tc_selftest(int cases, unsigned long long seed, double* max_rel, int* failures,
+                             cudaStream_t st);
+
 // Launch a single bounded wait on an mbarrier that is completed only if
 // `complete` is non-zero; *flag (device) is set to 1 if the wait expired
 // after `cycles` SM clocks.

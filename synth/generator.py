@@ -125,6 +125,13 @@ CONFIGS = {
 }
 
 
-def config_system(name: str) -> System:
+def config_system(name: str, max_bytes: float = 64e9) -> System:
+    """The named workload.  Refuses systems whose float64 Cholesky array
+    (K n^2 doubles) exceeds max_bytes: the 2500-basis shape needs 375 GB
+    and n^2 G K = 1.2e18 flops to form."""
     o, v, P, G, K, seed = CONFIGS[name]
+    need = 8.0 * K * (o + v) ** 2
+    if need > max_bytes:
+        raise MemoryError(f"{name}: the Cholesky array takes {need / 1e9:.0f} GB "
+                          f"(limit {max_bytes / 1e9:.0f} GB)")
     return make_system(o, v, P, G, K, seed)

@@ -33,3 +33,14 @@ def test_expired_wait_is_reported_and_device_stays_usable():
     assert np.abs(sig - sig_ref).max() < 1e-10
     assert abs(E - E_ref) < 1e-9
     assert binding.selftest_bounded_wait(True) == "THC_OK"
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tensor_core_product_randomised(seed):
+    """tcgen05 bf16 hi/lo products against the CUDA-core products over random
+    shapes, orientations, batch modes, split-K and beta (64 cases a seed)."""
+    from paper_2111_11473_gb300 import binding
+    status, max_rel, failures = binding.selftest_gemm(cases=64, seed=seed)
+    print(f"\nseed {seed}: max bf16x3 relative difference {max_rel:.2e}, failures {failures}")
+    assert status == "THC_OK" and failures == 0
+    assert max_rel < 1e-3
