@@ -276,13 +276,60 @@ __global__ void __launch_bounds__(256) k_triangle(T* H, const T* E, const T* F,
 // halved and added one after the other.
 constexpr int SIST = 2;
 
+struct TriSym64Stage {
+    double g1[SIST][TYZ][TYZ + 1];   // G^YZ, rows Y
+    double g2[SIST][TYZ][TYZ + 1];   // G^ZY, rows Z
+    double ey[SIST][TXB][TYZ], ez[SIST][TXB][TYZ];
+    double fy[SIST][TXB][TYZ], fz[SIST][TXB][TYZ];
+};
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 8 : 0));
+}
+
+// Stage grid points I0 .. I0 + SIST - 1 of the block's tiles (zeros outside).
+__device__ __forceinline__ void sym64_load(TriSym64Stage& st, const double* E, const double* F,
+                                           const double* G, int P, int nI, int I0, int X0,
+                                           int Y0, int Z0) {
+    const long long PP = (long long)P * P;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < SIST * TYZ * TYZ; e += 256) {
+        const int s = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
+        const int I = I0 + s;
+        const bool ok1 = I < nI && Y0 + r < P && Z0 + c < P;
+        const bool ok2 = I < nI && Z0 + r < P && Y0 + c < P;
+        cp_async8(&st.g1[s][r][c], ok1 ? G + I * PP + (long long)(Y0 + r) * P + Z0 + c : G, ok1);
+        cp_async8(&st.g2[s][r][c], ok2 ? G + I * PP + (long long)(Z0 + r) * P + Y0 + c : G, ok2);
+    }
+    for (int e = tid; e < SIST * TXB * TYZ; e += 256) {
+        const int s = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
+        const int I = I0 + s, X = X0 + x;
+        const bool okx = I < nI && X < P;
+        const long long base = I * PP + (long long)X * P;
+        const bool oy = okx && Y0 + c < P, oz = okx && Z0 + c < P;
+        cp_async8(&st.ey[s][x][c], oy ? E + base + Y0 + c : E, oy);
+        cp_async8(&st.ez[s][x][c], oz ? E + base + Z0 + c : E, oz);
+        cp_async8(&st.fy[s][x][c], oy ? F + base + Y0 + c : F, oy);
+        cp_async8(&st.fz[s][x][c], oz ? F + base + Z0 + c : F, oz);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Float64 triangle kernel over pairs of mirror (Y, Z) tiles.
+// t^XYZ = E^XY F^XZ + E^XZ F^XY is symmetric in (Y, Z), so one t feeds both
+// H^XYZ += t G^YZ and H^XZY += t G^ZY: 7 flops per two outputs (two FP64
+// FMA-pipe operations per output instead of three).  A block owns 4 X and the
+// tiles (Y0, Z0), (Z0, Y0) with Y0 <= Z0; on a diagonal pair (Y0 = Z0) both
+// accumulators land on the same tile, count every element twice, and are
+// halved and added one after the other.  Operands of the next pair of grid
+// points are staged with cp.async while the current pair is computed.
 __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double* E,
                                                         const double* F, const double* G,
                                                         int P, int nI) {
-    __shared__ double sG1[SIST][TYZ][TYZ + 1];   // G^YZ, rows Y
-    __shared__ double sG2[SIST][TYZ][TYZ + 1];   // G^ZY, rows Z
-    __shared__ double sEy[SIST][TXB][TYZ], sEz[SIST][TXB][TYZ];
-    __shared__ double sFy[SIST][TXB][TYZ], sFz[SIST][TXB][TYZ];
+    extern __shared__ __align__(16) unsigned char sym64_raw[];
+    TriSym64Stage* stg = reinterpret_cast<TriSym64Stage*>(sym64_raw);
     const int nb = (P + TYZ - 1) / TYZ;
     int pidx = blockIdx.x, Yb = 0;
     while (pidx >= nb - Yb) {
@@ -293,7 +340,6 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
     const int Y0 = Yb * TYZ, Z0 = Zb * TYZ, X0 = blockIdx.y * TXB;
     const bool diag = Yb == Zb;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const long long PP = (long long)P * P;
     double a1[TXB][2][2], a2[TXB][2][2];
 #pragma unroll
     for (int x = 0; x < TXB; ++x)
@@ -301,25 +347,15 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
         for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int j = 0; j < 2; ++j) a1[x][i][j] = a2[x][i][j] = 0;
-    for (int I0 = 0; I0 < nI; I0 += SIST) {
-        for (int e = tid; e < SIST * TYZ * TYZ; e += 256) {
-            const int st = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
-            const int I = I0 + st;
-            const bool ok = I < nI;
-            sG1[st][r][c] = (ok && Y0 + r < P && Z0 + c < P)
-                                ? G[I * PP + (long long)(Y0 + r) * P + Z0 + c] : 0.0;
-            sG2[st][r][c] = (ok && Z0 + r < P && Y0 + c < P)
-                                ? G[I * PP + (long long)(Z0 + r) * P + Y0 + c] : 0.0;
-        }
-        for (int e = tid; e < SIST * TXB * TYZ; e += 256) {
-            const int st = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
-            const int I = I0 + st, X = X0 + x;
-            const bool okx = I < nI && X < P;
-            const long long base = I * PP + (long long)X * P;
-            sEy[st][x][c] = (okx && Y0 + c < P) ? E[base + Y0 + c] : 0.0;
-            sEz[st][x][c] = (okx && Z0 + c < P) ? E[base + Z0 + c] : 0.0;
-            sFy[st][x][c] = (okx && Y0 + c < P) ? F[base + Y0 + c] : 0.0;
-            sFz[st][x][c] = (okx && Z0 + c < P) ? F[base + Z0 + c] : 0.0;
+    const int nsteps = (nI + SIST - 1) / SIST;
+    if (nsteps > 0) sym64_load(stg[0], E, F, G, P, nI, 0, X0, Y0, Z0);
+    for (int k = 0; k < nsteps; ++k) {
+        const TriSym64Stage& cur = stg[k & 1];
+        if (k + 1 < nsteps) {
+            sym64_load(stg[(k + 1) & 1], E, F, G, P, nI, (k + 1) * SIST, X0, Y0, Z0);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
 #pragma unroll
@@ -329,18 +365,18 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    g1[i][j] = sG1[st][ty + 16 * i][tx + 16 * j];   // G^(Y_i, Z_j)
-                    g2[i][j] = sG2[st][tx + 16 * j][ty + 16 * i];   // G^(Z_j, Y_i)
+                    g1[i][j] = cur.g1[st][ty + 16 * i][tx + 16 * j];   // G^(Y_i, Z_j)
+                    g2[i][j] = cur.g2[st][tx + 16 * j][ty + 16 * i];   // G^(Z_j, Y_i)
                 }
 #pragma unroll
             for (int x = 0; x < TXB; ++x) {
                 double ey[2], fy[2], ez[2], fz[2];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    ey[i] = sEy[st][x][ty + 16 * i];
-                    fy[i] = sFy[st][x][ty + 16 * i];
-                    ez[i] = sEz[st][x][tx + 16 * i];
-                    fz[i] = sFz[st][x][tx + 16 * i];
+                    ey[i] = cur.ey[st][x][ty + 16 * i];
+                    fy[i] = cur.fy[st][x][ty + 16 * i];
+                    ez[i] = cur.ez[st][x][tx + 16 * i];
+                    fz[i] = cur.fz[st][x][tx + 16 * i];
                 }
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
@@ -353,7 +389,7 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
                     }
             }
         }
-        __syncthreads();
+        __syncthreads();   // the buffer is refilled two steps later
     }
     const double scale = diag ? 0.5 : 1.0;
 #pragma unroll
@@ -974,7 +1010,15 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
     if constexpr (std::is_same<T, double>::value) {
         const unsigned nb = cdiv(P, TYZ);
         dim3 grid(nb * (nb + 1) / 2, cdiv(P, TXB));
-        k_triangle_sym64<<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+        const int smem = (int)(2 * sizeof(TriSym64Stage));
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_triangle_sym64,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_triangle_sym64<<<grid, 256, smem, s>>>(H, E, F, G, P, nI);
     } else {
         dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
         k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
