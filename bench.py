@@ -71,7 +71,7 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # G=1200, from one ncu capture of the current kernels (summaries in
 # profiles/residual_fp64_o40_v200_P400_G1200_K600_launches.md and
 # profiles/triangle_f32_o40_v200_P400_G1200_K600.md).  Other sizes: null.
-TRIANGLE_TRAFFIC_BYTES = {"fp64": None, "mixed": 13.55e9 + 0.26e9}
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 115.88e9 + 0.52e9, "mixed": 13.55e9 + 0.26e9}
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
@@ -153,10 +153,36 @@ def whole_job_rate(world, ms_max):
     return world * 1e3 / ms_max
 
 
-def _system(seed_offset=0):
-    from synth import make_system
+# Systems whose float64 Cholesky vectors exceed this many bytes are generated
+# on the GPU and handed to the library a slab at a time.
+HOST_L_LIMIT = 64e9
+
+
+def _system(seed_offset=0, device=None):
+    from synth import make_device_system, make_system
     w = WORKLOAD
-    return make_system(w["o"], w["v"], w["P"], w["G"], w["K"], w["seed"] + seed_offset)
+    args = (w["o"], w["v"], w["P"], w["G"], w["K"], w["seed"] + seed_offset)
+    if 8.0 * w["K"] * (w["o"] + w["v"]) ** 2 > HOST_L_LIMIT:
+        return make_device_system(*args, device=device)
+    return make_system(*args)
+
+
+def _context(pkg, s, dev=None, **kw):
+    """A library context for s: from its Cholesky array, or (device-generated
+    systems) from its slabs through thc_load_cholesky."""
+    import torch
+    if s.L is not None:
+        if dev is None:
+            return pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z, **kw)
+        tens = [torch.from_numpy(a).to(dev) for a in (s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z)]
+        return pkg.Context(*tens, **kw)
+    ctx = pkg.Context(s.eps_o, s.eps_v, s.Y, None, s.x, s.z, n_k=s.K, **kw)
+    for k0, Lk in s.cholesky_slabs(nk=32):
+        ctx.load_cholesky(k0, Lk)
+        del Lk
+    torch.cuda.empty_cache()
+    ctx.finish_init()
+    return ctx
 
 
 def oracle_residual_seconds(s, Zc, t1):
@@ -240,8 +266,7 @@ def fp64_vs_mixed_iterations(pkg, s, stream, n_iter):
     iteration by iteration (each on its own trajectory), and their difference."""
     out = {}
     for name, prec in (("fp64", pkg.THC_PREC_FP64), ("mixed", pkg.THC_PREC_MIXED)):
-        with pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z, precision=prec,
-                         stream=stream) as c:
+        with _context(pkg, s, precision=prec, stream=stream) as c:
             hist = []
             c.solve(r_tol=0.0, max_iter=n_iter, history=hist, raise_on_failure=False)
             out[name] = [h[0] for h in hist]
@@ -250,41 +275,45 @@ def fp64_vs_mixed_iterations(pkg, s, stream, n_iter):
     return out
 
 
-def solve_variants(pkg, s, dev, stream, ctx, args, prec):
+def solve_variants(pkg, s, dev, stream, ctx, args, prec, rate=None):
     """Solves from zero: float64, mixed precision, and mixed precision with the
     learned preconditioner; time to 1e-6 Eh of the float64 converged energy
     (of the plain mixed solve's converged energy when the float64 solve is
-    skipped, at sizes where it would take too long)."""
+    skipped, at sizes where it would take too long).  ``rate`` is the mixed
+    residual rate when ctx is the mixed context and it was measured already."""
     import numpy as np
     import torch
     from paper_2111_11473_gb300 import precond
     from synth import make_system
     out = {}
-    fp64_ctx = ctx
-    if prec != pkg.THC_PREC_FP64:
-        fp64_ctx = pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z,
-                               precision=pkg.THC_PREC_FP64, stream=stream)
     f = None
     if not args.skip_fp64_solve:
-        f = precond.run_solve(fp64_ctx, None, None, r_tol=args.fp64_rtol, max_iter=60)
+        fp64_ctx = ctx if prec == pkg.THC_PREC_FP64 else _context(
+            pkg, s, precision=pkg.THC_PREC_FP64, stream=stream)
+        f = precond.run_solve(fp64_ctx, None, None, r_tol=args.fp64_rtol,
+                              max_iter=args.max_iter)
         f["evals_per_s"] = None
         out["fp64"] = f
-    if fp64_ctx is not ctx:
-        fp64_ctx.close()
+        if fp64_ctx is not ctx:
+            fp64_ctx.close()
     # Mixed precision: residual rate on the bench state, then solves.
-    mctx = ctx if prec == pkg.THC_PREC_MIXED else pkg.Context(
-        s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z, precision=pkg.THC_PREC_MIXED, stream=stream)
-    Zc0, t10, _ = mctx.solve(max_iter=3, diis_n=0, raise_on_failure=False)
-    Zc = torch.from_numpy(Zc0).to(dev)
-    t1 = torch.from_numpy(t10).to(dev)
-    sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
-    sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
-    mrate = _rate(mctx, Zc, t1, sig, sig1, stream, dev)
+    mctx = ctx if prec == pkg.THC_PREC_MIXED else _context(
+        pkg, s, precision=pkg.THC_PREC_MIXED, stream=stream)
+    if rate is not None and mctx is ctx:
+        mrate = rate
+    else:
+        Zc0, t10, _ = mctx.solve(max_iter=3, diis_n=0, raise_on_failure=False)
+        Zc = torch.from_numpy(Zc0).to(dev)
+        t1 = torch.from_numpy(t10).to(dev)
+        sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
+        sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
+        mrate = _rate(mctx, Zc, t1, sig, sig1, stream, dev)
     e_ref = f["energy"] if f is not None else None
-    # The mixed-precision residual has a floor near 5e-6 at this size (the
-    # bf16x3 products' rounding): the mixed solves stop at |r| < 1e-5 once
-    # the energy changes by less than 1e-8 Eh per iteration.
-    m = precond.run_solve(mctx, e_ref, None, r_tol=1e-5, max_iter=60, stop_de=1e-8)
+    # The mixed-precision residual has a floor near 5e-6 at o=40 (the bf16x3
+    # products' rounding): the mixed solves stop at |r| < solve_rtol (1e-5)
+    # once the energy changes by less than 1e-8 Eh per iteration.
+    m = precond.run_solve(mctx, e_ref, None, r_tol=args.solve_rtol, max_iter=args.max_iter,
+                          stop_de=1e-8)
     m["evals_per_s"] = mrate
     if e_ref is None:
         e_ref = m["energy"]
@@ -295,8 +324,7 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     Xs, js, ts = [], [], []
     for k, o in enumerate((8, 10, 12, 14, 16, 18)):
         ss = make_system(o, 5 * o, 10 * o, 30 * o, 15 * o, 100 + k)
-        with pkg.Context(ss.eps_o, ss.eps_v, ss.Y, ss.L, ss.x, ss.z,
-                         precision=pkg.THC_PREC_MIXED, stream=stream) as c:
+        with _context(pkg, ss, precision=pkg.THC_PREC_MIXED, stream=stream) as c:
             X, j, t, _ = precond.collect_pairs(c, seed=k)
         Xs.append(X)
         js.append(j)
@@ -304,7 +332,8 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec):
     X, j, t = (np.concatenate(a) for a in (Xs, js, ts))
     net, loss, jacobi = precond.train(X, j, t, epochs=20)
     train_s = time.perf_counter() - t0
-    lrn = precond.run_solve(mctx, e_ref, net, r_tol=1e-5, max_iter=60, stop_de=1e-8)
+    lrn = precond.run_solve(mctx, e_ref, net, r_tol=args.solve_rtol, max_iter=args.max_iter,
+                            stop_de=1e-8)
     lrn["evals_per_s"] = mrate
     lrn["training"] = {"systems": "o = 8..18, v = 5o, P = 10o, G = 30o, K = 15o, seeds 100-105",
                        "pairs": int(len(j)), "loss": loss, "loss_plain_jacobi": jacobi,
@@ -338,6 +367,9 @@ def main():
                     help="no float64 solve (sizes where it takes too long)")
     ap.add_argument("--fp64-rtol", type=float, default=1e-8,
                     help="residual tolerance of the float64 reference solve")
+    ap.add_argument("--solve-rtol", type=float, default=1e-5,
+                    help="residual tolerance of the mixed-precision solves")
+    ap.add_argument("--max-iter", type=int, default=60, help="iteration cap of every solve")
     ap.add_argument("--t2sq-route", type=int, default=0, choices=[0, 1, 2],
                     help="Eqs. 32-33: 0 automatic, 1 Alg. 6 (O(N^4)), 2 Algs. 4-5 (O(N^5))")
     ap.add_argument("--fp64-iters", type=int, default=0,
@@ -366,10 +398,11 @@ def main():
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    s = _system(seed_offset=rank)
+    s = _system(seed_offset=rank, device=dev)
     prec = pkg.THC_PREC_FP64 if args.precision == "fp64" else pkg.THC_PREC_MIXED
-    tens = [torch.from_numpy(a).to(dev) for a in (s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z)]
-    ctx = pkg.Context(*tens, precision=prec, stream=stream, t2sq_route=args.t2sq_route)
+    t_init = time.perf_counter()
+    ctx = _context(pkg, s, dev, precision=prec, stream=stream, t2sq_route=args.t2sq_route)
+    init_s = time.perf_counter() - t_init
     # State: two Jacobi steps from zero (projected MP1 and one more step).
     Zc0, t10, _ = ctx.solve(max_iter=3, diis_n=0, raise_on_failure=False)
     Zc = torch.from_numpy(Zc0).to(dev)
@@ -478,7 +511,9 @@ def main():
         "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
                    "t2sq_route": args.t2sq_route,
                    "state": "solver iterate after two Jacobi steps from zero",
-                   "l2": "inputs larger than L2 (Cholesky blocks 238 MB, grid factors 1.5 GB)",
+                   "l2": "inputs larger than L2 (Cholesky blocks %.3g GB)" % (
+                       s.K * (s.o * s.o + s.o * s.v + s.v * (s.v + 1) / 2) *
+                       (8 if fp64 else 4) / 1e9),
                    "parallelism": f"{world} independent system(s), one per GPU"},
         "energy": energy,
         "e2e": {"value": whole_job_rate(world, 1e3 * e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -491,8 +526,9 @@ def main():
         "steps_breakdown": steps,
     }
 
+    line["init_s"] = init_s
     if not args.no_solve:
-        line["solve"] = solve_variants(pkg, s, dev, stream, ctx, args, prec)
+        line["solve"] = solve_variants(pkg, s, dev, stream, ctx, args, prec, rate=1e3 / ms)
     if args.fp64_iters > 0:
         line["fp64_vs_mixed"] = fp64_vs_mixed_iterations(pkg, s, stream, args.fp64_iters)
     ctx.close()

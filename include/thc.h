@@ -83,6 +83,13 @@ typedef struct {
                                 2 = Algs. 4 and 5 (O(N^5), batched products
                                 only); automatic compares the estimated time
                                 of both at the context's precision */
+    int x_block6;            /* amplitude-THC indices X per Alg. 6 block: H,
+                                C_i, D_a, E and F are formed for one block of
+                                X rows at a time (G_I^YZ is shared); 0 = auto:
+                                all P rows when H (P^3 words), D_a and C_i fit
+                                a quarter of the free memory (at most 48 GiB),
+                                else the fewest blocks that do, rounded up to
+                                32 rows */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */
@@ -97,7 +104,10 @@ thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p,
  *                   recovered from it and the Cholesky integrals)
  *   eps_vir  v      virtual orbital energies
  *   Y        n x P  amplitude collocation factors y_p^W (Eq. 7, Eq. 23)
- *   L        K x n x n  Cholesky vectors L_pq^A, symmetric in pq (Eq. 24)
+ *   L        K x n x n  Cholesky vectors L_pq^A, symmetric in pq (Eq. 24);
+ *                   NULL = supplied later by thc_load_cholesky (systems whose
+ *                   float64 vectors do not fit one array), after which
+ *                   thc_init_finish completes the initialisation
  *   x        n x G  ERI-THC collocation x_p^I (Eq. 17)
  *   z        G x G  ERI-THC core z^IJ, symmetric (Eq. 17)
  *   stream   cudaStream_t to run on, or NULL for the legacy default stream
@@ -105,14 +115,38 @@ thc_status thc_config_default(thc_config* cfg, int n_occ, int n_vir, int n_p,
  * Precomputes o^XY, v^XY (Alg. 1 lines 1-2), the metric S = o*v (Eq. 10)
  * and the orthonormal working basis of Eq. 22 (generalised eigenbasis of
  * the orbital-energy Fock block in the metric).  Inputs are copied; the
- * caller keeps ownership.  Errors: THC_ERR_ARG for non-positive sizes or
- * asymmetric z, THC_ERR_OOM, THC_ERR_CUDA, THC_ERR_NUMERIC if the metric has
- * no positive eigenvalue.  On failure *out is NULL.
+ * caller keeps ownership.  Only the lower triangle (q <= p) of each
+ * vector's virtual-virtual block is read; it is stored packed.  Errors:
+ * THC_ERR_ARG for non-positive sizes or asymmetric z, THC_ERR_OOM,
+ * THC_ERR_CUDA, THC_ERR_NUMERIC if the metric has no positive eigenvalue.
+ * On failure *out is NULL.
  */
 thc_status thc_init(const thc_config* cfg, const double* eps_occ,
                     const double* eps_vir, const double* Y, const double* L,
                     const double* x, const double* z, void* stream,
                     thc_ctx** out);
+
+/*
+ * thc_load_cholesky - Cholesky vectors k0 .. k0 + nk - 1 of a context made
+ * by thc_init with L = NULL.
+ *
+ *   L   nk x n x n float64, row-major, symmetric in the last two indices
+ *       (host or device; copied before the call returns)
+ *
+ * Vectors may arrive in any order and any number of calls; a vector loaded
+ * twice keeps the second copy.  Errors: THC_ERR_ARG if the range leaves
+ * 0 .. K - 1, L is NULL or the context is not waiting for vectors.
+ */
+thc_status thc_load_cholesky(thc_ctx* ctx, int k0, int nk, const double* L);
+
+/*
+ * thc_init_finish - the parts of thc_init that need the Cholesky vectors
+ * (energy weight of the core, Alg. 6 and 7 fixed parts, workspaces).  Every
+ * other call on the context returns THC_ERR_ARG until it has succeeded.
+ * Errors: THC_ERR_ARG if a vector is missing or nothing is pending, and as
+ * thc_init.
+ */
+thc_status thc_init_finish(thc_ctx* ctx);
 
 /*
  * thc_residual - one evaluation of the projected residual (Algs. 1-10).

@@ -23,7 +23,8 @@ class ThcConfig(C.Structure):
                 ("n_g", C.c_int), ("n_k", C.c_int), ("precision", C.c_int),
                 ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double),
-                ("tc_products", C.c_int), ("alg7_route", C.c_int), ("t2sq_route", C.c_int)]
+                ("tc_products", C.c_int), ("alg7_route", C.c_int), ("t2sq_route", C.c_int),
+                ("x_block6", C.c_int)]
 
 
 class ThcSolveOpts(C.Structure):
@@ -75,6 +76,8 @@ _SIGNATURES = {
     "thc_solve_opts_default": (C.c_int, [C.POINTER(ThcSolveOpts)]),
     "thc_init": (C.c_int, [C.POINTER(ThcConfig), _DP, _DP, _DP, _DP, _DP, _DP, _VP,
                            C.POINTER(_VP)]),
+    "thc_load_cholesky": (C.c_int, [_VP, C.c_int, C.c_int, _DP]),
+    "thc_init_finish": (C.c_int, [_VP]),
     "thc_residual": (C.c_int, [_VP, _DP, _DP, _DP, _DP, _DP]),
     "thc_energy": (C.c_int, [_VP, _DP, _DP, _DP]),
     "thc_mp2_density": (C.c_int, [_VP, _DP, _DP, _DP]),
@@ -207,13 +210,17 @@ class Context:
 
     def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
                  k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10,
-                 tc_products=3, alg7_route=0, t2sq_route=0):
+                 tc_products=3, alg7_route=0, t2sq_route=0, x_block6=0, n_k=None):
+        """L = None (with n_k = K) leaves the Cholesky vectors to
+        load_cholesky() and finish_init()."""
         lib = load_library()
         o, v = len(eps_o), len(eps_v)
         n = o + v
         P = Y.shape[1]
         G = x.shape[1]
-        K = L.shape[0]
+        if L is None and n_k is None:
+            raise ValueError("n_k is required when L is None")
+        K = L.shape[0] if L is not None else int(n_k)
         cfg = ThcConfig()
         st = lib.thc_config_default(C.byref(cfg), o, v, P, G, K)
         if st != 0:
@@ -225,18 +232,30 @@ class Context:
         cfg.tc_products = tc_products
         cfg.alg7_route = alg7_route
         cfg.t2sq_route = t2sq_route
-        args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)), _Arg(L, (K, n, n)),
+        cfg.x_block6 = x_block6
+        args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)),
+                _Arg(L, (K, n, n)) if L is not None else None,
                 _Arg(x, (n, G)), _Arg(z, (G, G))]
         handle = _VP()
         stream_ptr = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
-        st = lib.thc_init(C.byref(cfg), *[a.ptr for a in args], _VP(stream_ptr),
-                          C.byref(handle))
+        st = lib.thc_init(C.byref(cfg), *[a.ptr if a is not None else None for a in args],
+                          _VP(stream_ptr), C.byref(handle))
         if st != 0:
             raise ThcError(st, lib.thc_last_error(None).decode())
         self._lib = lib
         self._h = handle
         self.o, self.v, self.P, self.G, self.K = o, v, P, G, K
         self.precision = precision
+
+    def load_cholesky(self, k0, L):
+        """Cholesky vectors k0 .. k0 + len(L) - 1 (float64, nk x n x n)."""
+        n = self.o + self.v
+        nk = L.shape[0]
+        a = _Arg(L, (nk, n, n))
+        self._check(self._lib.thc_load_cholesky(self._h, int(k0), int(nk), a.ptr))
+
+    def finish_init(self):
+        self._check(self._lib.thc_init_finish(self._h))
 
     def _check(self, st):
         if st != 0:

@@ -39,7 +39,7 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "every dimension must be positive"};
     if (cfg->precision != THC_PREC_FP64 && cfg->precision != THC_PREC_MIXED)
         return {THC_ERR_ARG, "unknown precision policy"};
-    if (cfg->k_slab < 0 || cfg->i_chunk < 0 || cfg->x_block < 0)
+    if (cfg->k_slab < 0 || cfg->i_chunk < 0 || cfg->x_block < 0 || cfg->x_block6 < 0)
         return {THC_ERR_ARG, "blocking sizes must be >= 0"};
     if (cfg->tc_products != 0 && cfg->tc_products != 1 && cfg->tc_products != 3)
         return {THC_ERR_ARG, "tc_products must be 0, 1 or 3"};
@@ -47,6 +47,15 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "alg7_route must be 0, 1 or 2"};
     if (cfg->t2sq_route < 0 || cfg->t2sq_route > 2)
         return {THC_ERR_ARG, "t2sq_route must be 0, 1 or 2"};
+    return {};
+}
+
+// Calls that evaluate anything need the Cholesky vectors in place.
+thc::Err ready(const thc_ctx* c) {
+    const bool pend = c->e64 ? c->e64->pending : c->e32->pending;
+    if (pend)
+        return {THC_ERR_ARG, "the context waits for its Cholesky vectors (thc_load_cholesky, "
+                             "thc_init_finish)"};
     return {};
 }
 
@@ -95,7 +104,7 @@ thc_status thc_init(const thc_config* cfg, const double* eps_occ, const double* 
     if (!out) { g_init_error = "out is NULL"; return THC_ERR_ARG; }
     *out = nullptr;
     thc::Err e = check_config(cfg);
-    if (e.ok() && (!eps_occ || !eps_vir || !Y || !L || !x || !z))
+    if (e.ok() && (!eps_occ || !eps_vir || !Y || !x || !z))
         e = {THC_ERR_ARG, "an input pointer is NULL"};
     if (!e.ok()) { g_init_error = e.msg; return e.code; }
     thc_ctx* c = new (std::nothrow) thc_ctx;
@@ -121,10 +130,27 @@ thc_status thc_init(const thc_config* cfg, const double* eps_occ, const double* 
     return THC_OK;
 }
 
+thc_status thc_load_cholesky(thc_ctx* c, int k0, int nk, const double* L) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    thc::Err e = c->e64 ? c->e64->load_cholesky(k0, nk, L) : c->e32->load_cholesky(k0, nk, L);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+thc_status thc_init_finish(thc_ctx* c) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    thc::Err e = c->e64 ? c->e64->init_finish() : c->e32->init_finish();
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
 thc_status thc_residual(thc_ctx* c, const double* Zc, const double* t1, double* sigmaZ,
                         double* sigma1, double* energy) {
     if (!c) return THC_ERR_ARG;
     c->err.clear();
+    if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!Zc || !t1 || !sigmaZ || !sigma1) return fail(c, {THC_ERR_ARG, "NULL argument"});
     thc::Err e = c->e64 ? c->e64->residual(Zc, t1, sigmaZ, sigma1, energy)
                : c->e32->residual(Zc, t1, sigmaZ, sigma1, energy);
@@ -135,6 +161,7 @@ thc_status thc_residual(thc_ctx* c, const double* Zc, const double* t1, double* 
 thc_status thc_energy(thc_ctx* c, const double* Zc, const double* t1, double* energy) {
     if (!c) return THC_ERR_ARG;
     c->err.clear();
+    if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!Zc || !t1 || !energy) return fail(c, {THC_ERR_ARG, "NULL argument"});
     thc::Err e = c->e64 ? c->e64->energy(Zc, t1, energy) : c->e32->energy(Zc, t1, energy);
     if (!e.ok()) return fail(c, e);
@@ -144,6 +171,7 @@ thc_status thc_energy(thc_ctx* c, const double* Zc, const double* t1, double* en
 thc_status thc_mp2_density(thc_ctx* c, const double* Zc, double* D_oo, double* D_vv) {
     if (!c) return THC_ERR_ARG;
     c->err.clear();
+    if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!Zc || !D_oo || !D_vv) return fail(c, {THC_ERR_ARG, "NULL argument"});
     thc::Err e = c->e64 ? c->e64->mp2_density(Zc, D_oo, D_vv)
                         : c->e32->mp2_density(Zc, D_oo, D_vv);
@@ -155,6 +183,7 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
                      double* t1_inout, thc_report* report) {
     if (!c) return THC_ERR_ARG;
     c->err.clear();
+    if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!opts || !Zc_inout || !t1_inout) return fail(c, {THC_ERR_ARG, "NULL argument"});
     if (!c->solver) {
         c->solver.reset(new thc::Solver());

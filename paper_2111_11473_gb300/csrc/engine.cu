@@ -176,16 +176,17 @@ Err Engine<T>::dress(const T* oo_, const T* ov_, const T* vv_, int nb, T* out_oo
     THC_CUDA(cudaMemcpyAsync(out_oo, oo_, sizeof(T) * nb * o * o, cudaMemcpyDeviceToDevice, st));
     THC_TRY(mm(o, o, v, rm(ov_, v), tr(tp, v), out_oo, o, 1, 1, nb, (long long)o * v, 0,
                (long long)o * o));
-    // L^_vv = L_vv - t1^T L_ov
-    THC_CUDA(cudaMemcpyAsync(out_vv, vv_, sizeof(T) * nb * v * v, cudaMemcpyDeviceToDevice, st));
-    THC_TRY(mm(v, v, o, tr(tp, v), rm(ov_, v), out_vv, v, -1, 1, nb, 0, (long long)o * v,
-               (long long)v * v));
+    // L_vv from its packed lower triangles (vv_), still undressed
+    THC_CUDA(unpack_vv(vv_, nb, v, out_vv, st));
     // L^_vo = L_ov^T + L_vv t1^T - t1^T L^_oo
     THC_CUDA(transpose_batched(ov_, out_vo, nb, o, v, st));
-    THC_TRY(mm(v, o, v, rm(vv_, v), tr(tp, v), out_vo, o, 1, 1, nb, (long long)v * v, 0,
+    THC_TRY(mm(v, o, v, rm(out_vv, v), tr(tp, v), out_vo, o, 1, 1, nb, (long long)v * v, 0,
                (long long)v * o));
     THC_TRY(mm(v, o, o, tr(tp, v), rm(out_oo, o), out_vo, o, -1, 1, nb, 0, (long long)o * o,
                (long long)v * o));
+    // L^_vv = L_vv - t1^T L_ov
+    THC_TRY(mm(v, v, o, tr(tp, v), rm(ov_, v), out_vv, v, -1, 1, nb, 0, (long long)o * v,
+               (long long)v * v));
     return Err{};
 }
 
@@ -244,7 +245,18 @@ template <typename T>
 Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* eps_v,
                     const double* Yh, const double* Lh, const double* xh, const double* zh,
                     cudaStream_t s) {
+    THC_TRY(init_begin(cfg, eps_o, eps_v, Yh, xh, zh, s));
+    if (!Lh) return Err{};   // the caller supplies the Cholesky vectors
+    THC_TRY(load_cholesky(0, K, Lh));
+    return init_finish();
+}
+
+template <typename T>
+Err Engine<T>::init_begin(const thc_config& cfg, const double* eps_o, const double* eps_v,
+                          const double* Yh, const double* xh, const double* zh,
+                          cudaStream_t s) {
     st = s;
+    cfg0 = cfg;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
     {
         // Cholesky slab: as many vectors as the per-vector scratch budget holds
@@ -263,14 +275,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                             : (int)std::max<long long>(1, std::min<long long>(
                                   cfg.n_k, std::max<long long>(16, fit)));
     }
-    // Alg. 6 grid chunk: as many grid points as 4 GB of E/F chunk buffers hold,
-    // so that H is read and written once per chunk.
-    ic = cfg.i_chunk > 0
-             ? std::min(cfg.i_chunk, G)
-             : (int)std::max<long long>(1, std::min<long long>(
-                   G, (4LL << 30) / (2LL * P * P * (long long)sizeof(T))));
-    xb = cfg.x_block > 0 ? std::min(cfg.x_block, P) : std::min(P, 32);
-    const long long ov = (long long)o * v, PP = (long long)P * P, nn = (long long)n * n;
+    const long long ov = (long long)o * v, vt = (long long)v * (v + 1) / 2;
 
     THC_TRY(flag.alloc(1));
     THC_TRY(chk.alloc(3));
@@ -293,30 +298,80 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(load(zh, z.p, (long long)G * G));
     THC_TRY(Loo.alloc((size_t)K * o * o));
     THC_TRY(Lov.alloc((size_t)K * ov));
-    THC_TRY(Lvv.alloc((size_t)K * v * v));
+    THC_TRY(Lvv.alloc((size_t)K * vt));
+
+    // ---- canonical Fock operator f = diag(eps): the reference is canonical
+    // Hartree-Fock, and the core Hamiltonian it implies (h = f - 2 J + X) is
+    // never formed (see fock_slab).
+    THC_TRY(foo.alloc((size_t)o * o));
+    THC_TRY(fvv.alloc((size_t)v * v));
+    THC_TRY(epsT.alloc(n));
     {
-        // Stage L in slabs of kb vectors and split it into its blocks.
-        DBuf<double> stage;
-        DBuf<T> stageT;
-        THC_TRY(stage.alloc((size_t)kb * nn));
-        if (!std::is_same<T, double>::value) THC_TRY(stageT.alloc((size_t)kb * nn));
-        for (int A0 = 0; A0 < K; A0 += kb) {
-            int nb = std::min(kb, K - A0);
-            THC_CUDA(cudaMemcpyAsync(stage.p, Lh + (long long)A0 * nn,
-                                     sizeof(double) * nb * nn, cudaMemcpyDefault, st));
-            const T* src;
-            if constexpr (std::is_same<T, double>::value) {
-                src = stage.p;
-            } else {
-                THC_CUDA(convert(stage.p, stageT.p, nb * nn, st));
-                src = stageT.p;
-            }
-            Blocks<T> b{Loo.p + (long long)A0 * o * o, Lov.p + (long long)A0 * ov, nullptr,
-                        Lvv.p + (long long)A0 * v * v};
-            THC_CUDA(split_blocks(src, nb, o, v, b, st));
-        }
+        std::vector<double> eps(n);
+        THC_CUDA(cudaMemcpy(eps.data(), eps_o, sizeof(double) * o, cudaMemcpyDefault));
+        THC_CUDA(cudaMemcpy(eps.data() + o, eps_v, sizeof(double) * v, cudaMemcpyDefault));
+        eps_h = eps;
+        std::vector<T> fo((size_t)o * o, T(0)), fv((size_t)v * v, T(0)), et(n);
+        for (int i = 0; i < o; ++i) fo[(size_t)i * o + i] = (T)eps[i];
+        for (int a = 0; a < v; ++a) fv[(size_t)a * v + a] = (T)eps[o + a];
+        for (int p = 0; p < n; ++p) et[p] = (T)eps[p];
+        THC_CUDA(cudaMemcpyAsync(foo.p, fo.data(), sizeof(T) * o * o, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(fvv.p, fv.data(), sizeof(T) * v * v, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(epsT.p, et.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
         THC_CUDA(cudaStreamSynchronize(st));
     }
+    loaded.assign((size_t)K, 0);
+    pending = true;
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::load_cholesky(int k0, int nk, const double* Lh) {
+    if (!pending) return Err{THC_ERR_ARG, "the Cholesky vectors are already set"};
+    if (!Lh || k0 < 0 || nk <= 0 || (long long)k0 + nk > K)
+        return Err{THC_ERR_ARG, "Cholesky vector range outside 0 .. K - 1"};
+    const long long ov = (long long)o * v, nn = (long long)n * n,
+                    vt = (long long)v * (v + 1) / 2;
+    if (!lstage.p) {
+        THC_TRY(lstage.alloc((size_t)kb * nn));
+        if (!std::is_same<T, double>::value) THC_TRY(lstageT.alloc((size_t)kb * nn));
+    }
+    // Stage kb vectors at a time and split them into their blocks (the vv
+    // block as its lower triangle).
+    for (int a = 0; a < nk; a += kb) {
+        const int nb = std::min(kb, nk - a);
+        const long long A0 = (long long)k0 + a;
+        THC_CUDA(cudaMemcpyAsync(lstage.p, Lh + (long long)a * nn, sizeof(double) * nb * nn,
+                                 cudaMemcpyDefault, st));
+        const T* src;
+        if constexpr (std::is_same<T, double>::value) {
+            src = lstage.p;
+        } else {
+            THC_CUDA(convert(lstage.p, lstageT.p, nb * nn, st));
+            src = lstageT.p;
+        }
+        Blocks<T> b;
+        b.oo = Loo.p + A0 * o * o;
+        b.ov = Lov.p + A0 * ov;
+        b.vvp = Lvv.p + A0 * vt;
+        THC_CUDA(split_blocks(src, nb, o, v, b, st));
+    }
+    THC_CUDA(cudaStreamSynchronize(st));   // the caller may reuse its buffer
+    for (int k = k0; k < k0 + nk; ++k) loaded[k] = 1;
+    return Err{};
+}
+
+template <typename T>
+Err Engine<T>::init_finish() {
+    if (!pending) return Err{THC_ERR_ARG, "no initialisation is pending"};
+    for (int k = 0; k < K; ++k)
+        if (!loaded[k])
+            return Err{THC_ERR_ARG, "Cholesky vector " + std::to_string(k) + " was not loaded"};
+    lstage.release();
+    lstageT.release();
+    const thc_config& cfg = cfg0;
+    const long long ov = (long long)o * v, PP = (long long)P * P;
+    const long long TB = (long long)sizeof(T);
 
     // ---- scratch
     const long long kbl = kb;
@@ -363,27 +418,6 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(D8.alloc(kbl * ov));
     THC_TRY(Mo.alloc((size_t)K * o * o));
 
-    // ---- canonical Fock operator f = diag(eps): the reference is canonical
-    // Hartree-Fock, and the core Hamiltonian it implies (h = f - 2 J + X) is
-    // never formed (see fock_slab).
-    THC_TRY(foo.alloc((size_t)o * o));
-    THC_TRY(fvv.alloc((size_t)v * v));
-    THC_TRY(epsT.alloc(n));
-    {
-        std::vector<double> eps(n);
-        THC_CUDA(cudaMemcpy(eps.data(), eps_o, sizeof(double) * o, cudaMemcpyDefault));
-        THC_CUDA(cudaMemcpy(eps.data() + o, eps_v, sizeof(double) * v, cudaMemcpyDefault));
-        eps_h = eps;
-        std::vector<T> fo((size_t)o * o, T(0)), fv((size_t)v * v, T(0)), et(n);
-        for (int i = 0; i < o; ++i) fo[(size_t)i * o + i] = (T)eps[i];
-        for (int a = 0; a < v; ++a) fv[(size_t)a * v + a] = (T)eps[o + a];
-        for (int p = 0; p < n; ++p) et[p] = (T)eps[p];
-        THC_CUDA(cudaMemcpyAsync(foo.p, fo.data(), sizeof(T) * o * o, cudaMemcpyHostToDevice, st));
-        THC_CUDA(cudaMemcpyAsync(fvv.p, fv.data(), sizeof(T) * v * v, cudaMemcpyHostToDevice, st));
-        THC_CUDA(cudaMemcpyAsync(epsT.p, et.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
-        THC_CUDA(cudaStreamSynchronize(st));
-    }
-
     // ---- amplitude-factor products
     const T* yo = y.p;
     const T* yv = y.p + (long long)o * P;
@@ -425,6 +459,58 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     THC_TRY(U6.alloc((size_t)o * G * P));
     THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p, P, 1, 0, o, (long long)v * G, 0,
                (long long)G * P));
+    // ---- Alg. 7 exchange route.  Dense route: Kx[(ia),(jb)] = (ib|ja)
+    //      = sum_J B[(i,b),J] x_j^J x_a^J, one v x v block per (i, j).
+    {
+        const double kx_bytes = (double)ov * ov * sizeof(T);
+        alg7_dense = cfg.alg7_route == 2 ||
+                     (cfg.alg7_route == 0 && kx_bytes <= 16.0 * (1LL << 30));
+        if (alg7_dense) {
+            THC_TRY(Kx.alloc((size_t)ov * ov));
+            THC_TRY(W7.alloc((size_t)P * ov));
+            for (int i = 0; i < o; ++i)
+                THC_TRY(mm(v, v, G, rm(KRx.p, G), tr(B6.p + (long long)i * v * G, G),
+                           Kx.p + (long long)i * v * ov, ov, 1, 0, o, (long long)v * G, 0, v));
+        }
+    }
+    // B is needed only to build U (and Kx); x o x only on the dense route
+    // (C^XI of the blocked route comes from its per-X intermediates).
+    THC_CUDA(cudaStreamSynchronize(st));
+    B6.release();
+    if (!alg7_dense) KRx.release();
+
+    // ---- Alg. 6 blocking.  G_I^YZ is resident when it fits; otherwise it
+    //      is rebuilt per grid chunk (and per X block).  X blocks: H (x6 P^2),
+    //      its packed copy for the post-products, D_a and C_i (x6 P each per
+    //      orbital) take at most a quarter of the free memory (48 GiB at
+    //      most); all P rows in one block when they fit, else the fewest
+    //      blocks that do, rounded up to the triangle kernel's 32-row tile.
+    const size_t gall_bytes = (size_t)G * PP * sizeof(T);
+    const bool gall_fits = cfg.workspace_bytes == 0 ? gall_bytes <= (size_t)48 << 30
+                                                    : gall_bytes <= cfg.workspace_bytes / 4;
+    {
+        size_t free_b = 0, total_b = 0;
+        long long budget6 = cfg.workspace_bytes > 0 ? (long long)(cfg.workspace_bytes / 4)
+                                                    : 48LL << 30;
+        if (cfg.workspace_bytes == 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            budget6 = std::min<long long>(budget6, (long long)(free_b / 4));
+        const long long perX = (2 * PP + (long long)(o + v) * P) * TB;
+        if (cfg.x_block6 > 0) {
+            x6 = std::min(cfg.x_block6, P);
+        } else if (perX * P <= budget6) {
+            x6 = P;
+        } else {
+            const long long nblk = (perX * P + budget6 - 1) / std::max<long long>(budget6, 1);
+            x6 = (int)std::min<long long>(P, ((P + nblk - 1) / nblk + 31) / 32 * 32);
+        }
+        // Grid points per chunk: the E and F chunks take at most 4 GB, and so
+        // does G's chunk when it is rebuilt.
+        long long icl = (4LL << 30) / (2LL * x6 * P * TB);
+        if (!gall_fits) icl = std::min<long long>(icl, (4LL << 30) / (PP * TB));
+        ic = cfg.i_chunk > 0 ? std::min(cfg.i_chunk, G)
+                             : (int)std::max<long long>(1, std::min<long long>(G, icl));
+    }
+    const int nblk6 = (P + x6 - 1) / x6;
     // ---- Route for Eqs. 32-33: Alg. 6 (O(N^4), triangle on the CUDA cores)
     //      or Algs. 4 and 5 (O(N^5), batched products).  Automatic: the
     //      smaller estimated time from rates measured on GB300 at o=40
@@ -435,7 +521,8 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         const double dG = G, dP = P, dO = o, dV = v;
         const double f6_tri = 5.0 * dG * dP * dP * dP;
         const double f6_mm = 2.0 * dG * dP * dP * (dO + dV) + 6.0 * dO * dV * dP * dP +
-                             2.0 * dP * dP * dP * dO + 2.0 * dP * dO * dV * dP;
+                             2.0 * dP * dP * dP * dO + 2.0 * dP * dO * dV * dP +
+                             (gall_fits ? 0.0 : 2.0 * dG * dP * dP * dO * (nblk6 - 1));
         // per pair (i, j) of Alg. 4 and (j, a) of Alg. 5, products as issued by alg45
         const double p4 = 2.0 * (dV * dV * dP + dV * dG * dV + dG * dG * dV + dO * dG * dG +
                                  dO * dO * dG + dO * dP * dO + dP * dP * dO + dV * dP * dP +
@@ -445,7 +532,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                                  dO * dV * dP + dP * dV * dO + dP * dP * dV);
         const double f45 = dO * dO * p4 + dO * dV * p5 + 2.0 * (dO + dV) * dV * dP * dP;
         const bool mixed = !std::is_same<T, double>::value && cfg.tc_products > 0;
-        const double n6 = 8.0 + 4.0 * std::ceil(dG / ic);
+        const double n6 = 8.0 * nblk6 + 4.0 * std::ceil(dG / ic) * nblk6;
         const double nb = std::max(1.0, std::min(std::max(dO, dV),
                                                  std::floor(2.0 * (1LL << 30) /
                                                             (dG * dG * sizeof(T)))));
@@ -456,9 +543,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         t2sq_n5 = cfg.t2sq_route == 2 || (cfg.t2sq_route == 0 && t45 < t6);
     }
     if (!t2sq_n5) {
-        const size_t gall_bytes = (size_t)G * PP * sizeof(T);
-        gall_resident = cfg.workspace_bytes == 0 ? gall_bytes <= (size_t)48 << 30
-                                                 : gall_bytes <= cfg.workspace_bytes / 4;
+        gall_resident = gall_fits;
         if (gall_resident) {
             THC_TRY(Gall.alloc((size_t)G * PP));
             THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0,
@@ -466,14 +551,15 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         } else {
             THC_TRY(Gch.alloc((size_t)ic * PP));
         }
+        const long long xP = (long long)x6 * P;
         THC_TRY(A6.alloc(ov * P));
-        THC_TRY(C6.alloc((size_t)o * PP));
-        THC_TRY(D6.alloc((size_t)v * PP));
-        THC_TRY(Ech.alloc((size_t)ic * PP));
-        THC_TRY(Fch.alloc((size_t)ic * PP));
-        THC_TRY(H.alloc((size_t)P * PP));
-        THC_TRY(M6.alloc((size_t)P * o * P));
-        THC_TRY(I6.alloc((size_t)P * ov));
+        THC_TRY(C6.alloc((size_t)o * xP));
+        THC_TRY(D6.alloc((size_t)v * xP));
+        THC_TRY(Ech.alloc((size_t)ic * xP));
+        THC_TRY(Fch.alloc((size_t)ic * xP));
+        THC_TRY(H.alloc((size_t)x6 * PP));
+        THC_TRY(M6.alloc((size_t)x6 * o * P));
+        THC_TRY(I6.alloc((size_t)x6 * ov));
     } else {
         // Pairs per batched product: the G x G intermediates of one batch
         // take at most 2 GiB.
@@ -493,21 +579,11 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         THC_TRY(I45.alloc((size_t)nb * mx * v));
         THC_TRY(R45.alloc((size_t)nb * P * v));
     }
-    // ---- Alg. 7 exchange route.  Dense route: Kx[(ia),(jb)] = (ib|ja)
-    //      = sum_J B[(i,b),J] x_j^J x_a^J, one v x v block per (i, j).
-    {
-        const double kx_bytes = (double)ov * ov * sizeof(T);
-        alg7_dense = cfg.alg7_route == 2 ||
-                     (cfg.alg7_route == 0 && kx_bytes <= 16.0 * (1LL << 30));
-        if (alg7_dense) {
-            THC_TRY(Kx.alloc((size_t)ov * ov));
-            THC_TRY(W7.alloc((size_t)P * ov));
-            for (int i = 0; i < o; ++i)
-                THC_TRY(mm(v, v, G, rm(KRx.p, G), tr(B6.p + (long long)i * v * G, G),
-                           Kx.p + (long long)i * v * ov, ov, 1, 0, o, (long long)v * G, 0, v));
-        }
-    }
-    // ---- Alg. 7 scratch
+    // ---- Alg. 7 scratch; X block: the G x G intermediates take at most
+    //      8 GiB (32 X's at most).
+    xb = cfg.x_block > 0 ? std::min(cfg.x_block, P)
+                         : (int)std::max<long long>(1, std::min<long long>(
+                               std::min(P, 32), (8LL << 30) / ((long long)G * G * TB)));
     THC_TRY(R7.alloc((size_t)P * ov));
     THC_TRY(S7.alloc((size_t)P * ov));
     THC_TRY(C7.alloc((size_t)P * G));
@@ -524,14 +600,23 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
     if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
         // Packed-operand workspace: the largest product of the residual.
         struct Shape { long long M, N, K, b; };
-        const long long PP2 = (long long)P * P;
-        const Shape shapes[] = {
+        const long long xP = (long long)x6 * P;
+        std::vector<Shape> shapes = {
             {P, P, (long long)kb * P, 1}, {(long long)P * kb, P, P, 1}, {P, P, o, kb},
             {P, P, v, kb}, {v, P, v, kb}, {o, G, v, xb}, {G, G, o, xb}, {o, G, G, xb},
-            {o, v, G, xb}, {xb, P, ov, 1}, {P, G, ov, 1}, {P, G, G, 1}, {P, P, G, 1},
-            {P, ov, P, 1}, {o, P, P, xb}, {o, v, P, xb}, {ov, P, P, 1}, {P, P, v, o},
-            {P, P, o, v}, {ic, PP2, o, 1}, {ic, PP2, v, 1}, {o, P, P, P}, {o, v, P, P},
-            {P, P, ov, 1}, {P, P, K, 1}};
+            {o, v, G, xb}, {xb, P, ov, 1}, {G, P, G, 1}, {P, P, G, 1},
+            {P, ov, P, 1}, {o, P, P, xb}, {o, v, P, xb}, {ov, P, P, 1}, {P, P, K, 1}};
+        if (alg7_dense) {
+            shapes.push_back({P, G, ov, 1});
+            shapes.push_back({P, ov, ov, 1});
+            shapes.push_back({P, P, ov, 1});
+        }
+        if (!t2sq_n5) {
+            for (const Shape& sh : std::initializer_list<Shape>{
+                     {x6, P, v, o}, {x6, P, o, v}, {ic, xP, o, 1}, {ic, xP, v, 1},
+                     {o, P, P, x6}, {o, v, P, x6}, {x6, P, ov, 1}})
+                shapes.push_back(sh);
+        }
         size_t need = 0;
         for (const Shape& sh : shapes)
             need = std::max(need, gemm_tc_pack_elems((int)std::min<long long>(sh.M, INT32_MAX),
@@ -561,7 +646,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         // bf16 hi/lo forms are packed once and reused by every residual.
         // The cache may take up to half of the memory left free after init.
         if constexpr (std::is_same<T, float>::value) {
-            for (DBuf<T>* b : {&y, &x, &z, &oo, &vv, &S, &KRy, &KRx, &Atil, &B6, &U6, &Gall, &Kx})
+            for (DBuf<T>* b : {&y, &x, &z, &oo, &vv, &S, &KRy, &KRx, &Atil, &U6, &Gall, &Kx})
                 if (b->p) pcache.add_constant(b->p, b->n);
             size_t free_b = 0, total_b = 0;
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
@@ -569,6 +654,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
         }
     }
     THC_CUDA(cudaStreamSynchronize(st));
+    pending = false;
     return Err{};
 }
 
@@ -609,43 +695,53 @@ Err Engine<T>::alg6(T* sgm) {
     const T* yo = y.p;
     const T* yv = y.p + (long long)o * P;
     seg_begin(THC_STEP_ALG6_GEMM);
-    // A_ia^X = sum_Y y_i^Y y_a^Y T^XY  (line 1), C_i^XY (line 4), D_a^XY (line 5)
+    // A_ia^X = sum_Y y_i^Y y_a^Y T^XY  (line 1)
     THC_TRY(mm((int)ov, P, P, rm(KRy.p, P), rm(Tc.p, P), A6.p, P, 1, 0));
-    THC_TRY(mm(P, P, v, tr(yv, P), rm(A6.p, P), C6.p, P, 1, 0, o, 0, (long long)v * P, PP));
-    THC_TRY(mm(P, P, o, tr(yo, P), View<T>{A6.p, (long long)v * P, 1}, D6.p, P, 1, 0, v, 0, P,
-               PP));
-    THC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(T) * P * PP, st));
-    for (int I0 = 0; I0 < G; I0 += ic) {
-        const int nI = std::min(ic, G - I0);
+    // Blocks of x6 amplitude indices X: every line from 4 on is local to the
+    // X rows of C_i, D_a, E, F and H (G_I^YZ is shared by all blocks).
+    for (int X0 = 0; X0 < P; X0 += x6) {
+        const int nX = std::min(x6, P - X0);
+        const long long xP = (long long)nX * P;
         seg_begin(THC_STEP_ALG6_GEMM);
-        // E^XY = sum_i C_i^XY x_i^I (line 8), F^XZ = sum_a D_a^XZ x_a^I (line 9)
-        THC_TRY(mm(nI, (int)PP, o, View<T>{x.p + I0, 1, G}, rm(C6.p, PP), Ech.p, PP, 1, 0));
-        THC_TRY(mm(nI, (int)PP, v, View<T>{x.p + (long long)o * G + I0, 1, G}, rm(D6.p, PP),
-                   Fch.p, PP, 1, 0));
-        const T* Gp;
-        if (gall_resident) {
-            Gp = Gall.p + (long long)I0 * PP;
-        } else {
-            THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p + (long long)I0 * P, (long long)G * P, 1},
-                       Gch.p, P, 1, 0, nI, 0, P, PP));
-            Gp = Gch.p;
+        // C_i^XY (line 4) and D_a^XY (line 5) for the block's X
+        THC_TRY(mm(nX, P, v, tr(yv + X0, P), rm(A6.p, P), C6.p, P, 1, 0, o, 0, (long long)v * P,
+                   xP));
+        THC_TRY(mm(nX, P, o, tr(yo + X0, P), View<T>{A6.p, (long long)v * P, 1}, D6.p, P, 1, 0,
+                   v, 0, P, xP));
+        THC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(T) * nX * PP, st));
+        for (int I0 = 0; I0 < G; I0 += ic) {
+            const int nI = std::min(ic, G - I0);
+            seg_begin(THC_STEP_ALG6_GEMM);
+            // E^XY = sum_i C_i^XY x_i^I (line 8), F^XZ = sum_a D_a^XZ x_a^I (line 9)
+            THC_TRY(mm(nI, (int)xP, o, View<T>{x.p + I0, 1, G}, rm(C6.p, xP), Ech.p, xP, 1, 0));
+            THC_TRY(mm(nI, (int)xP, v, View<T>{x.p + (long long)o * G + I0, 1, G}, rm(D6.p, xP),
+                       Fch.p, xP, 1, 0));
+            const T* Gp;
+            if (gall_resident) {
+                Gp = Gall.p + (long long)I0 * PP;
+            } else {
+                THC_TRY(mm(P, P, o, tr(yo, P),
+                           View<T>{U6.p + (long long)I0 * P, (long long)G * P, 1}, Gch.p, P, 1,
+                           0, nI, 0, P, PP));
+                Gp = Gch.p;
+            }
+            // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
+            seg_begin(THC_STEP_TRIANGLE);
+            // 5 flops per (I, X, Y, Z); the float64 kernel shares t between the
+            // mirror outputs (Y, Z) and (Z, Y): 7 flops per pair
+            if (prof.on)
+                prof.flops[THC_STEP_TRIANGLE] +=
+                    (std::is_same<T, double>::value ? 3.5 : 5.0) * nI * (double)nX * P * P;
+            THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+            seg_end();
         }
-        // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
-        seg_begin(THC_STEP_TRIANGLE);
-        // 5 flops per (I, X, Y, Z); the float64 kernel shares t between the
-        // mirror outputs (Y, Z) and (Z, Y): 7 flops per pair
-        if (prof.on)
-            prof.flops[THC_STEP_TRIANGLE] +=
-                (std::is_same<T, double>::value ? 3.5 : 5.0) * nI * (double)P * P * P;
-        THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nI, st, tcerr.p));
-        seg_end();
+        seg_begin(THC_STEP_ALG6_POST);
+        // I_ia = sum_YZ y_i^Z y_a^Y H^XYZ (line 14); sigma^XX' += sum_ia y_i^X' y_a^X' I_ia
+        THC_TRY(mm(o, P, P, rm(yo, P), View<T>{H.p, 1, P}, M6.p, P, 1, 0, nX, 0, PP,
+                   (long long)o * P));
+        THC_TRY(mm(o, v, P, rm(M6.p, P), tr(yv, P), I6.p, v, 1, 0, nX, (long long)o * P, 0, ov));
+        THC_TRY(mm(nX, P, (int)ov, rm(I6.p, ov), rm(KRy.p, P), sgm + (long long)X0 * P, P, 1, 1));
     }
-    seg_begin(THC_STEP_ALG6_POST);
-    // I_ia = sum_YZ y_i^Z y_a^Y H^XYZ (line 14); sigma^XX' += sum_ia y_i^X' y_a^X' I_ia
-    THC_TRY(mm(o, P, P, rm(yo, P), View<T>{H.p, 1, P}, M6.p, P, 1, 0, P, 0, PP,
-               (long long)o * P));
-    THC_TRY(mm(o, v, P, rm(M6.p, P), tr(yv, P), I6.p, v, 1, 0, P, (long long)o * P, 0, ov));
-    THC_TRY(mm(P, P, (int)ov, rm(I6.p, ov), rm(KRy.p, P), sgm, P, 1, 1));
     return Err{};
 }
 
@@ -751,11 +847,11 @@ Err Engine<T>::alg7(T* sgm) {
                    0, nx, (long long)o * P, (long long)v * P, ov));
     }
     THC_CUDA(lincomb(R7.p, (long long)P * ov, 1, R7.p, 1, S7.p, 0, (const T*)nullptr, st));
-    // Coulomb part: C^XI = sum_ia x_i^I x_a^I R_ia^X, D = C z (lines 9-10)
-    THC_TRY(mm(P, G, (int)ov, rm(R7.p, ov), rm(KRx.p, G), C7.p, G, 1, 0));
-    THC_TRY(mm(P, G, G, rm(C7.p, G), rm(z.p, G), D7.p, G, 1, 0));
-    THC_TRY(mm(P, P, G, rm(C7.p, G), tr(D7.p, G), sgm, P, 1, 1));
     if (alg7_dense) {
+        // Coulomb part: C^XI = sum_ia x_i^I x_a^I R_ia^X, D = C z (lines 9-10)
+        THC_TRY(mm(P, G, (int)ov, rm(R7.p, ov), rm(KRx.p, G), C7.p, G, 1, 0));
+        THC_TRY(mm(P, G, G, rm(C7.p, G), rm(z.p, G), D7.p, G, 1, 0));
+        THC_TRY(mm(P, P, G, rm(C7.p, G), tr(D7.p, G), sgm, P, 1, 1));
         // Exchange parts through the dense (ib|ja): sigma -= 1/2 R Kx R^T,
         // sigma += 1/2 S Kx S^T (the same sums as lines 12-22).
         for (int pass = 0; pass < 2; ++pass) {
@@ -774,6 +870,9 @@ Err Engine<T>::alg7(T* sgm) {
             const int nx = std::min(xb, P - X0);
             THC_TRY(mm(o, G, v, rm(src + (long long)X0 * ov, v), rm(xv, G), N7.p, G, 1, 0, nx,
                        ov, 0, (long long)o * G));
+            // Coulomb part (line 9) from the same product: C^XI = sum_i x_i^I
+            // (R_X x_v)_i^I, stored transposed (C7[I][X])
+            if (pass == 0) THC_CUDA(diag_reduce(xo, N7.p, o, G, nx, C7.p, P, X0, st));
             THC_TRY(mm(G, G, o, tr(xo, G), rm(N7.p, G), E7.p, G, 1, 0, nx, 0, (long long)o * G,
                        GG));
             THC_CUDA(hadamard_batched(E7.p, z.p, GG, nx, st));
@@ -785,6 +884,9 @@ Err Engine<T>::alg7(T* sgm) {
                        sign, 1));
         }
     }
+    // D^T = z C^T (line 10, z symmetric); sigma += C D^T
+    THC_TRY(mm(G, P, G, rm(z.p, G), rm(C7.p, P), D7.p, P, 1, 0));
+    THC_TRY(mm(P, P, G, tr(C7.p, P), rm(D7.p, P), sgm, P, 1, 1));
     return Err{};
 }
 
@@ -813,7 +915,8 @@ Err Engine<T>::residual_dev(bool want_energy) {
         const int nb = std::min(kb, K - A0);
         const T* Lov_s = Lov.p + A0 * ov;
         seg_begin(THC_STEP_DRESS);
-        THC_TRY(dress(Loo.p + A0 * oo2, Lov_s, Lvv.p + A0 * vv2, nb, Lh_oo.p, Lh_vv.p, Lh_vo.p));
+        THC_TRY(dress(Loo.p + A0 * oo2, Lov_s, Lvv.p + A0 * ((long long)v * (v + 1) / 2), nb,
+                      Lh_oo.p, Lh_vv.p, Lh_vo.p));
         seg_begin(THC_STEP_FOCK);
         THC_TRY(fock_slab(nb, Lh_oo.p, Lov_s, Lh_vo.p, Lh_vv.p));
         seg_begin(THC_STEP_ALG1);

@@ -22,6 +22,11 @@ struct DBuf {
         THC_CUDA(cudaMalloc(&p, count * sizeof(T)));
         return Err{};
     }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
     ~DBuf() { if (p) cudaFree(p); }
     DBuf() = default;
     DBuf(const DBuf&) = delete;
@@ -66,6 +71,7 @@ template <typename T>
 struct Engine {
     int o = 0, v = 0, n = 0, P = 0, G = 0, K = 0;
     int kb = 0, ic = 0, xb = 0;
+    int x6 = 0;                             // amplitude indices X per Alg. 6 block
     bool gall_resident = false;
     MMKind mm_kind = MMKind::SIMT;
     cudaStream_t st = nullptr;
@@ -78,15 +84,16 @@ struct Engine {
 
     // Fixed data (storage type T unless noted).
     DBuf<T> y, x, z;                        // n x P, n x G, G x G
-    DBuf<T> Loo, Lov, Lvv;                  // K x o x o, K x o x v, K x v x v (undressed)
+    DBuf<T> Loo, Lov, Lvv;                  // K x o x o, K x o x v, K x v(v+1)/2 (undressed;
+                                            // Lvv holds lower triangles, row a: b <= a)
     DBuf<T> foo, fvv;                       // diagonal Fock blocks diag(eps_o), diag(eps_v)
     DBuf<T> epsT;                           // n orbital energies
     DBuf<T> oo, vv, S;                      // P x P
-    DBuf<T> KRy, KRx;                       // (o v) x P, (o v) x G
+    DBuf<T> KRy, KRx;                       // (o v) x P, (o v) x G (KRx: dense Alg. 7 only)
     DBuf<T> Atil;                           // P x K   (Alg. 2 line 6 / Alg. 8 line 6)
     DBuf<double> Wen;                       // P x P   energy weight of the core
     DBuf<T> Gall;                           // G x P x P (Alg. 6 line 10), if resident
-    DBuf<T> B6;                             // (o v) x G (Alg. 6 line 2)
+    DBuf<T> B6;                             // (o v) x G (Alg. 6 line 2), init only
     DBuf<T> U6;                             // o x G x P  sum_a B_ia^I y_a^Z
 
     // Per-residual state and accumulators.
@@ -118,9 +125,10 @@ struct Engine {
     DBuf<T> Lh_oo, Lh_vv, Lh_vo, dtr, Wfo, Wfv;
     DBuf<T> M1, Bbar, N1, Btil, C1, D1, M2, M3, E, TA, W, M4, D8, M5, Mo;
 
-    // Alg. 6 scratch.
+    // Alg. 6 scratch (C6, D6, Ech, Fch, H, M6, I6 hold one block of x6 X's).
     DBuf<T> A6, C6, D6, Ech, Fch, Gch, H, M6, I6;
-    // Alg. 7 scratch.
+    // Alg. 7 scratch (C7, D7: P x G on the dense route, G x P transposed on
+    // the blocked route).
     DBuf<T> R7, S7, C7, D7, Yv, M7, Yo, N7, E7, P7, G7;
     bool alg7_dense = false;
     // Algs. 4 and 5 (O(N^5) route for Eqs. 32-33)
@@ -131,9 +139,22 @@ struct Engine {
     DBuf<T> Kx;                             // (ov) x (ov): Kx[(ia),(jb)] = (ib|ja)
     DBuf<T> W7;                             // P x (ov)
 
+    // init = init_begin, load_cholesky of all K vectors, init_finish; with
+    // L == nullptr it stops after init_begin and the caller supplies the
+    // vectors (pending until init_finish).
     Err init(const thc_config& cfg, const double* eps_o, const double* eps_v,
              const double* Y, const double* L, const double* xin, const double* zin,
              cudaStream_t s);
+    Err init_begin(const thc_config& cfg, const double* eps_o, const double* eps_v,
+                   const double* Y, const double* xin, const double* zin, cudaStream_t s);
+    // Cholesky vectors k0 .. k0 + nk - 1 (nk x n x n float64, host or device).
+    Err load_cholesky(int k0, int nk, const double* L);
+    Err init_finish();
+    bool pending = false;                   // Cholesky vectors still arriving
+    thc_config cfg0{};
+    std::vector<char> loaded;               // per Cholesky vector
+    DBuf<double> lstage;                    // float64 staging of kb vectors
+    DBuf<T> lstageT;
     Err residual(const double* Zc, const double* t1in, double* sigmaZ, double* sigma1,
                  double* energy);
     Err energy(const double* Zc, const double* t1in, double* e);

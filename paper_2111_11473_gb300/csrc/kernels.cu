@@ -30,7 +30,39 @@ __global__ void k_split(const T* full, int nb, int o, int v, Blocks<T> out) {
         if (r < o && c < o) out.oo[(a * o + r) * o + c] = val;
         else if (r < o) { if (out.ov) out.ov[(a * o + r) * v + (c - o)] = val; }
         else if (c < o) { if (out.vo) out.vo[(a * v + (r - o)) * o + c] = val; }
-        else out.vv[(a * v + (r - o)) * v + (c - o)] = val;
+        else if (out.vv) out.vv[(a * v + (r - o)) * v + (c - o)] = val;
+        else if (r >= c) {
+            const long long ra = r - o, cb = c - o, vt = (long long)v * (v + 1) / 2;
+            out.vvp[a * vt + ra * (ra + 1) / 2 + cb] = val;
+        }
+    }
+}
+
+// Full v x v matrices from their packed lower triangles (row a holds b <= a).
+// Tiles below the diagonal copy rows; tiles above it read the mirror tile and
+// write it transposed, so every global access runs along a row.
+template <typename T>
+__global__ void k_unpack_vv(const T* packed, int nb, int v, T* out) {
+    __shared__ T tile[32][33];
+    const long long vt = (long long)v * (v + 1) / 2;
+    const T* src = packed + (long long)blockIdx.z * vt;
+    T* dst = out + (long long)blockIdx.z * v * v;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    // Source tile rows sr0.., columns sc0.. with sr0 >= sc0.
+    const int sr0 = 32 * max(bx, by), sc0 = 32 * min(bx, by);
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = sr0 + j, c = sc0 + threadIdx.x;
+        T val = T(0);
+        if (r < v && c < v)
+            val = r >= c ? src[(long long)r * (r + 1) / 2 + c] : src[(long long)c * (c + 1) / 2 + r];
+        tile[j][threadIdx.x] = val;
+    }
+    __syncthreads();
+    const int r0 = 32 * by, c0 = 32 * bx;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        if (r < v && c < v) dst[(long long)r * v + c] = by >= bx ? tile[j][threadIdx.x]
+                                                                : tile[threadIdx.x][j];
     }
 }
 
@@ -176,90 +208,9 @@ __global__ void k_scale_rows(const T* y, int R, int P, const T* w, int x0, int n
     }
 }
 
-// Register-tiled triangle kernel: a block owns TXB amplitude indices X and a
-// 32 x 32 (Y, Z) tile of H; per grid point I it stages G_I^{YZ} and the E, F
-// rows of its X's in shared memory, 4 grid points per stage.
-constexpr int TXB = 4, TYZ = 32, IST = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_triangle(T* H, const T* E, const T* F,
-                                                  const T* G, int P, int nI) {
-    __shared__ T sG[IST][TYZ][TYZ + 1];
-    __shared__ T sEy[IST][TXB][TYZ], sEz[IST][TXB][TYZ];
-    __shared__ T sFy[IST][TXB][TYZ], sFz[IST][TXB][TYZ];
-    const int Z0 = blockIdx.x * TYZ, Y0 = blockIdx.y * TYZ, X0 = blockIdx.z * TXB;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const long long PP = (long long)P * P;
-    T acc[TXB][2][2];
-#pragma unroll
-    for (int x = 0; x < TXB; ++x)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) acc[x][i][j] = 0;
-    for (int I0 = 0; I0 < nI; I0 += IST) {
-        for (int e = tid; e < IST * TYZ * TYZ; e += 256) {
-            int s = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
-            int I = I0 + s, Y = Y0 + r, Z = Z0 + c;
-            sG[s][r][c] = (I < nI && Y < P && Z < P) ? G[I * PP + (long long)Y * P + Z] : T(0);
-        }
-        for (int e = tid; e < IST * TXB * TYZ; e += 256) {
-            int s = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
-            int I = I0 + s, X = X0 + x;
-            bool okx = (I < nI && X < P);
-            long long base = I * PP + (long long)X * P;
-            sEy[s][x][c] = (okx && Y0 + c < P) ? E[base + Y0 + c] : T(0);
-            sEz[s][x][c] = (okx && Z0 + c < P) ? E[base + Z0 + c] : T(0);
-            sFy[s][x][c] = (okx && Y0 + c < P) ? F[base + Y0 + c] : T(0);
-            sFz[s][x][c] = (okx && Z0 + c < P) ? F[base + Z0 + c] : T(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < IST; ++s) {
-            T g[2][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) g[i][j] = sG[s][ty + 16 * i][tx + 16 * j];
-#pragma unroll
-            for (int x = 0; x < TXB; ++x) {
-                T ey[2], fy[2], ez[2], fz[2];
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    ey[i] = sEy[s][x][ty + 16 * i];
-                    fy[i] = sFy[s][x][ty + 16 * i];
-                    ez[i] = sEz[s][x][tx + 16 * i];
-                    fz[i] = sFz[s][x][tx + 16 * i];
-                }
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        T t = ey[i] * fz[j];
-                        t = fma(ez[j], fy[i], t);
-                        acc[x][i][j] = fma(t, g[i][j], acc[x][i][j]);
-                    }
-            }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int x = 0; x < TXB; ++x) {
-        int X = X0 + x;
-        if (X >= P) continue;
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            int Y = Y0 + ty + 16 * i;
-            if (Y >= P) continue;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                int Z = Z0 + tx + 16 * j;
-                if (Z >= P) continue;
-                H[((long long)X * P + Y) * P + Z] += acc[x][i][j];
-            }
-        }
-    }
-}
+// Tile of the float64 triangle kernel: TXB amplitude indices X and a pair of
+// TYZ x TYZ (Y, Z) tiles per block.
+constexpr int TXB = 4, TYZ = 32;
 
 // Float32 triangle kernel.  A block owns a 32 x 32 x 32 (X, Y, Z) tile of H;
 // lane = X, and the 16 warps form a 4 x 4 grid of 8 x 8 (Y, Z) register tiles.
@@ -291,9 +242,9 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src, bool o
 
 // Stage grid points I0 .. I0 + SIST - 1 of the block's tiles (zeros outside).
 __device__ __forceinline__ void sym64_load(TriSym64Stage& st, const double* E, const double* F,
-                                           const double* G, int P, int nI, int I0, int X0,
-                                           int Y0, int Z0) {
-    const long long PP = (long long)P * P;
+                                           const double* G, int P, int nX, int nI, int I0,
+                                           int X0, int Y0, int Z0) {
+    const long long PP = (long long)P * P, XP = (long long)nX * P;
     const int tid = threadIdx.x;
     for (int e = tid; e < SIST * TYZ * TYZ; e += 256) {
         const int s = e / (TYZ * TYZ), r = (e / TYZ) % TYZ, c = e % TYZ;
@@ -306,8 +257,8 @@ __device__ __forceinline__ void sym64_load(TriSym64Stage& st, const double* E, c
     for (int e = tid; e < SIST * TXB * TYZ; e += 256) {
         const int s = e / (TXB * TYZ), x = (e / TYZ) % TXB, c = e % TYZ;
         const int I = I0 + s, X = X0 + x;
-        const bool okx = I < nI && X < P;
-        const long long base = I * PP + (long long)X * P;
+        const bool okx = I < nI && X < nX;
+        const long long base = I * XP + (long long)X * P;
         const bool oy = okx && Y0 + c < P, oz = okx && Z0 + c < P;
         cp_async8(&st.ey[s][x][c], oy ? E + base + Y0 + c : E, oy);
         cp_async8(&st.ez[s][x][c], oz ? E + base + Z0 + c : E, oz);
@@ -327,7 +278,7 @@ __device__ __forceinline__ void sym64_load(TriSym64Stage& st, const double* E, c
 // points are staged with cp.async while the current pair is computed.
 __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double* E,
                                                         const double* F, const double* G,
-                                                        int P, int nI) {
+                                                        int P, int nX, int nI) {
     extern __shared__ __align__(16) unsigned char sym64_raw[];
     TriSym64Stage* stg = reinterpret_cast<TriSym64Stage*>(sym64_raw);
     const int nb = (P + TYZ - 1) / TYZ;
@@ -348,11 +299,11 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
 #pragma unroll
             for (int j = 0; j < 2; ++j) a1[x][i][j] = a2[x][i][j] = 0;
     const int nsteps = (nI + SIST - 1) / SIST;
-    if (nsteps > 0) sym64_load(stg[0], E, F, G, P, nI, 0, X0, Y0, Z0);
+    if (nsteps > 0) sym64_load(stg[0], E, F, G, P, nX, nI, 0, X0, Y0, Z0);
     for (int k = 0; k < nsteps; ++k) {
         const TriSym64Stage& cur = stg[k & 1];
         if (k + 1 < nsteps) {
-            sym64_load(stg[(k + 1) & 1], E, F, G, P, nI, (k + 1) * SIST, X0, Y0, Z0);
+            sym64_load(stg[(k + 1) & 1], E, F, G, P, nX, nI, (k + 1) * SIST, X0, Y0, Z0);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -395,7 +346,7 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
 #pragma unroll
     for (int x = 0; x < TXB; ++x) {
         const int X = X0 + x;
-        if (X >= P) continue;
+        if (X >= nX) continue;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int Y = Y0 + ty + 16 * i;
@@ -411,7 +362,7 @@ __global__ void __launch_bounds__(256) k_triangle_sym64(double* H, const double*
 #pragma unroll
     for (int x = 0; x < TXB; ++x) {
         const int X = X0 + x;
-        if (X >= P) continue;
+        if (X >= nX) continue;
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const int Y = Y0 + ty + 16 * i;
@@ -440,10 +391,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok)
 }
 
 __device__ __forceinline__ void tri_load(TriStage& st, const float* E, const float* F,
-                                         const float* G, int I, int P, int X0, int Y0, int Z0) {
-    const long long PP = (long long)P * P;
-    const float* Ei = E + I * PP;
-    const float* Fi = F + I * PP;
+                                         const float* G, int I, int P, int nX, int X0, int Y0,
+                                         int Z0) {
+    const long long PP = (long long)P * P, XP = (long long)nX * P;
+    const float* Ei = E + I * XP;
+    const float* Fi = F + I * XP;
     const float* Gi = G + I * PP;
     const int t = threadIdx.x;
 #pragma unroll
@@ -452,7 +404,7 @@ __device__ __forceinline__ void tri_load(TriStage& st, const float* E, const flo
         const int r = e >> 6, c = e & 63;
         const int X = X0 + r;
         const int col = c < TT ? Y0 + c : Z0 + (c - TT);
-        const bool ok = X < P && col < P;
+        const bool ok = X < nX && col < P;
         const long long off = ok ? (long long)X * P + col : 0;
         cp_async4(&st.e[r][c], Ei + off, ok);
         cp_async4(&st.f[r][c], Fi + off, ok);
@@ -469,7 +421,7 @@ __device__ __forceinline__ void tri_load(TriStage& st, const float* E, const flo
 
 __global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* E,
                                                          const float* F, const float* G,
-                                                         int P, int nI) {
+                                                         int P, int nX, int nI) {
     extern __shared__ __align__(16) unsigned char tri_smem[];
     TriStage* st = reinterpret_cast<TriStage*>(tri_smem);
     const int Z0 = blockIdx.x * TT, Y0 = blockIdx.y * TT, X0 = blockIdx.z * TT;
@@ -482,14 +434,14 @@ __global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* 
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
     for (int s = 0; s < TSTAGES - 1; ++s) {
-        if (s < nI) tri_load(st[s], E, F, G, s, P, X0, Y0, Z0);
+        if (s < nI) tri_load(st[s], E, F, G, s, P, nX, X0, Y0, Z0);
         asm volatile("cp.async.commit_group;\n" ::);
     }
     for (int I = 0; I < nI; ++I) {
         asm volatile("cp.async.wait_group %0;\n" ::"n"(TSTAGES - 2));
         __syncthreads();
         const int nxt = I + TSTAGES - 1;
-        if (nxt < nI) tri_load(st[nxt % TSTAGES], E, F, G, nxt, P, X0, Y0, Z0);
+        if (nxt < nI) tri_load(st[nxt % TSTAGES], E, F, G, nxt, P, nX, X0, Y0, Z0);
         asm volatile("cp.async.commit_group;\n" ::);
         const TriStage& c = st[I % TSTAGES];
         float ey[8], fy[8], ez[8], fz[8];
@@ -519,7 +471,7 @@ __global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* 
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
     const int X = X0 + lane;
-    if (X >= P) return;
+    if (X >= nX) return;
 #pragma unroll
     for (int yy = 0; yy < 8; ++yy) {
         const int Y = Y0 + wy * 8 + yy;
@@ -633,7 +585,8 @@ __device__ __forceinline__ unsigned long long tri_fma2(unsigned long long a, uns
 __global__ void __launch_bounds__(256, 1)
     k_triangle_f32_tma(float* H, const __grid_constant__ CUtensorMap tmE,
                        const __grid_constant__ CUtensorMap tmF,
-                       const __grid_constant__ CUtensorMap tmG, int P, int nI, int* err) {
+                       const __grid_constant__ CUtensorMap tmG, int P, int nX, int nI,
+                       int* err) {
     extern __shared__ __align__(1024) unsigned char tri_raw[];
     TriTmaSmem& sm = *reinterpret_cast<TriTmaSmem*>(
         (reinterpret_cast<uintptr_t>(tri_raw) + 1023) & ~uintptr_t(1023));
@@ -757,7 +710,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int X = X0 + lx + 8 * j;
-        if (X >= P) continue;
+        if (X >= nX) continue;
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
             const int Y = Y0 + y_base + y;
@@ -783,7 +736,8 @@ __global__ void __launch_bounds__(256, 1)
 PFN_cuTensorMapEncodeTiled_v12000 g_tri_encode = nullptr;
 std::once_flag g_tri_once;
 
-cudaError_t tri_map(CUtensorMap* m, const float* base, int P, int nI) {
+// Map of nI matrices of rows x P floats (rows are P-float lines).
+cudaError_t tri_map(CUtensorMap* m, const float* base, int rows, int P, int nI) {
     std::call_once(g_tri_once, [] {
         cudaDriverEntryPointQueryResult q;
         void* fn = nullptr;
@@ -793,8 +747,8 @@ cudaError_t tri_map(CUtensorMap* m, const float* base, int P, int nI) {
             g_tri_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
     if (!g_tri_encode) return cudaErrorNotSupported;
-    cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)nI};
-    cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * P * 4};
+    cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)rows, (cuuint64_t)nI};
+    cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)rows * P * 4};
     cuuint32_t box[3] = {(cuuint32_t)TT, (cuuint32_t)TT, (cuuint32_t)TI};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_tri_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box,
@@ -873,6 +827,14 @@ cudaError_t split_blocks(const T* full, int nb, int o, int v, Blocks<T> out,
                          cudaStream_t s) {
     long long n = (long long)nb * (o + v) * (o + v);
     k_split<T><<<nblocks(n), NT, 0, s>>>(full, nb, o, v, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t unpack_vv(const T* packed, int nb, int v, T* out, cudaStream_t s) {
+    dim3 grid(cdiv(v, 32), cdiv(v, 32), nb);
+    k_unpack_vv<T><<<grid, dim3(32, 8), 0, s>>>(packed, nb, v, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -971,15 +933,16 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* 
 }
 
 template <typename T>
-cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
+cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, int nI,
                      cudaStream_t s, int* tri_err) {
+    if (nX <= 0 || nI <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         if (P % 4 == 0 && ((uintptr_t)E % 16 == 0) && ((uintptr_t)F % 16 == 0) &&
             ((uintptr_t)G % 16 == 0) && tri_err) {
             CUtensorMap mE, mF, mG;
-            cudaError_t e = tri_map(&mE, E, P, nI);
-            if (e == cudaSuccess) e = tri_map(&mF, F, P, nI);
-            if (e == cudaSuccess) e = tri_map(&mG, G, P, nI);
+            cudaError_t e = tri_map(&mE, E, nX, P, nI);
+            if (e == cudaSuccess) e = tri_map(&mF, F, nX, P, nI);
+            if (e == cudaSuccess) e = tri_map(&mG, G, P, P, nI);
             if (e != cudaSuccess) return e;
             static bool tma_attr = false;
             const int smem = (int)sizeof(TriTmaSmem) + 1024;
@@ -989,8 +952,8 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
                 if (e != cudaSuccess) return e;
                 tma_attr = true;
             }
-            dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(P, TT));
-            k_triangle_f32_tma<<<grid, 256, smem, s>>>(H, mE, mF, mG, P, nI, tri_err);
+            dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(nX, TT));
+            k_triangle_f32_tma<<<grid, 256, smem, s>>>(H, mE, mF, mG, P, nX, nI, tri_err);
             count_launches(1);
             return cudaGetLastError();
         }
@@ -1002,14 +965,14 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
-        dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(P, TT));
-        k_triangle_f32<<<grid, 512, smem, s>>>(H, E, F, G, P, nI);
+        dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(nX, TT));
+        k_triangle_f32<<<grid, 512, smem, s>>>(H, E, F, G, P, nX, nI);
         count_launches(1);
         return cudaGetLastError();
     }
     if constexpr (std::is_same<T, double>::value) {
         const unsigned nb = cdiv(P, TYZ);
-        dim3 grid(nb * (nb + 1) / 2, cdiv(P, TXB));
+        dim3 grid(nb * (nb + 1) / 2, cdiv(nX, TXB));
         const int smem = (int)(2 * sizeof(TriSym64Stage));
         static bool attr = false;
         if (!attr) {
@@ -1018,13 +981,11 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_triangle_sym64<<<grid, 256, smem, s>>>(H, E, F, G, P, nI);
-    } else {
-        dim3 grid(cdiv(P, TYZ), cdiv(P, TYZ), cdiv(P, TXB));
-        k_triangle<T><<<grid, 256, 0, s>>>(H, E, F, G, P, nI);
+        k_triangle_sym64<<<grid, 256, smem, s>>>(H, E, F, G, P, nX, nI);
+        count_launches(1);
+        return cudaGetLastError();
     }
-    count_launches(1);
-    return cudaGetLastError();
+    return cudaErrorNotSupported;
 }
 
 template <typename T>
@@ -1061,6 +1022,7 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
 
 #define THC_INSTANTIATE(T)                                                              \
     template cudaError_t split_blocks<T>(const T*, int, int, int, Blocks<T>, cudaStream_t); \
+    template cudaError_t unpack_vv<T>(const T*, int, int, T*, cudaStream_t);            \
     template cudaError_t transpose_batched<T>(const T*, T*, int, int, int, cudaStream_t); \
     template cudaError_t convert<T>(const double*, T*, long long, cudaStream_t);        \
     template cudaError_t to_double<T>(const T*, double*, long long, cudaStream_t);      \
@@ -1079,7 +1041,7 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
     template cudaError_t khatri_rao<T>(const T*, const T*, int, int, int, T*, cudaStream_t); \
     template cudaError_t scale_rows<T>(const T*, int, int, const T*, int, int, T*,     \
                                        cudaStream_t);                                   \
-    template cudaError_t triangle<T>(T*, const T*, const T*, const T*, int, int,       \
+    template cudaError_t triangle<T>(T*, const T*, const T*, const T*, int, int, int,  \
                                      cudaStream_t, int*);                               \
     template cudaError_t dot<T>(const T*, const T*, long long, double*, double*,       \
                                 cudaStream_t);                                          \

@@ -12,11 +12,16 @@ struct Blocks {
     T* ov = nullptr;  // nb x o x v
     T* vo = nullptr;  // nb x v x o
     T* vv = nullptr;  // nb x v x v
+    T* vvp = nullptr; // nb x v(v+1)/2: lower triangle of the vv block, row a
+                      // holding b = 0..a (written when vv is null)
 };
 
 template <typename T>
 cudaError_t split_blocks(const T* full, int nb, int o, int v, Blocks<T> out,
                          cudaStream_t s);
+// out[k] (v x v) = the symmetric matrix whose lower triangle is packed[k].
+template <typename T>
+cudaError_t unpack_vv(const T* packed, int nb, int v, T* out, cudaStream_t s);
 template <typename T>
 cudaError_t transpose_batched(const T* in, T* out, int nb, int rows, int cols,
                               cudaStream_t s);
@@ -71,10 +76,12 @@ template <typename T>
 cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx,
                        T* out, cudaStream_t s);
 
-// Alg. 6 line 11: H[X][Y][Z] += sum_I (E_I^XY F_I^XZ + E_I^XZ F_I^XY) G_I^YZ.
+// Alg. 6 line 11: H[X][Y][Z] += sum_I (E_I^XY F_I^XZ + E_I^XZ F_I^XY) G_I^YZ
+// for a block of nX rows X (X < nX <= P, Y, Z < P): H is nX x P x P, E and F
+// are nI x nX x P, G is nI x P x P.
 // tri_err (device int, may be null) receives 1 if a bounded wait expired.
 template <typename T>
-cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nI,
+cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, int nI,
                      cudaStream_t s, int* tri_err = nullptr);
 
 // Deterministic float64 sums.

@@ -526,7 +526,12 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             if (use_mlp && !mlp_off) {
                 THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, nullptr, rr, r, sc, lr, feat.p,
                                       jjb.p, st));
-                THC_TRY(mlp->forward(feat.p, rr, yb.p));
+                // Rows are independent: at most 2^20 per pass bounds the
+                // network's activation buffers (4 x rows x width floats).
+                const long long chunk = 1LL << 20;
+                for (long long r0 = 0; r0 < rr; r0 += chunk)
+                    THC_TRY(mlp->forward(feat.p + r0 * kMlpFeatures, std::min(chunk, rr - r0),
+                                         yb.p + r0));
                 THC_CUDA(mlp_apply(sq.p, e.p, yb.p, r, smlp.p, st));
                 k_add<<<nb(rr), 256, 0, st>>>(x.p + ov, smlp.p, rr, xnew.p + ov);
                 count_launches(1);

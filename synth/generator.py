@@ -100,6 +100,93 @@ def make_system(o: int, v: int, P: int, G: int, K: int, seed: int,
                   np.ascontiguousarray(z), np.ascontiguousarray(L))
 
 
+@dataclass
+class DeviceSystem:
+    """A system whose Cholesky vectors are formed on a torch device, a slab
+    at a time (the 2500-basis shape has 375 GB of them in float64).  Same
+    draws as ``make_system``; z and the pivoted Cholesky factor R are formed
+    on the device in float64, the vectors in float32 (the precision the
+    mixed-precision engine stores them in)."""
+    o: int
+    v: int
+    P: int
+    G: int
+    K: int
+    seed: int
+    eps_o: np.ndarray   # (o,)
+    eps_v: np.ndarray   # (v,)
+    Y: np.ndarray       # (n, P)
+    x: np.ndarray       # (n, G)
+    z: np.ndarray       # (G, G)
+    Rt: object          # torch (K, G) float64 on the device: column k of R is row k
+    L = None
+
+    @property
+    def n(self) -> int:
+        return self.o + self.v
+
+    def cholesky_slabs(self, nk: int = 32):
+        """Yield (k0, L[k0:k0+nk]) as float64 (nk, n, n) device tensors with
+        L[k, p, q] = sum_I x[p, I] x[q, I] R[I, k] formed in float32 and
+        symmetrised."""
+        import torch
+        dev = self.Rt.device
+        xf = torch.from_numpy(self.x).to(dev, torch.float32)
+        n = self.n
+        for k0 in range(0, self.K, nk):
+            kk = min(nk, self.K - k0)
+            # M[k, q, I] = R[I, k] x[q, I];  L[k] = M[k] x^T
+            M = self.Rt[k0:k0 + kk].to(torch.float32)[:, None, :] * xf[None, :, :]
+            Lk = (M.reshape(kk * n, self.G) @ xf.T).reshape(kk, n, n)
+            del M
+            Lk = 0.5 * (Lk + Lk.transpose(1, 2))
+            yield k0, Lk.to(torch.float64)
+            del Lk
+
+
+def _pivoted_cholesky_torch(V, rank: int):
+    """``_pivoted_cholesky`` on a torch tensor, without host synchronisation:
+    returns R^T (rank x G)."""
+    import torch
+    G = V.shape[0]
+    Rt = torch.zeros((rank, G), dtype=V.dtype, device=V.device)
+    d = V.diagonal().clone()
+    for k in range(rank):
+        p = torch.argmax(d).view(1)
+        piv = d.index_select(0, p)
+        col = V.index_select(0, p)[0] - Rt[:k].T @ Rt[:k].index_select(1, p)[:, 0]
+        col = col / torch.sqrt(piv)
+        Rt[k] = col
+        d -= col * col
+        d.index_fill_(0, p, 0.0)
+    return Rt
+
+
+def make_device_system(o: int, v: int, P: int, G: int, K: int, seed: int, device,
+                       gamma: float = 0.3) -> DeviceSystem:
+    """``make_system`` with z, R and the Cholesky vectors formed on ``device``
+    (the vectors lazily, through ``DeviceSystem.cholesky_slabs``)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    eps_o = np.sort(rng.uniform(-1.5, -0.3, o))
+    eps_v = np.sort(rng.uniform(0.1, 3.0, v))
+    n = o + v
+    x = rng.standard_normal((n, G)) / np.sqrt(G)
+    A = np.abs(rng.standard_normal((G, K))) * np.sqrt(gamma / (K * 2.0 / np.pi))
+    Y = rng.standard_normal((n, P)) / np.sqrt(P)
+    At = torch.from_numpy(A).to(device)
+    del A
+    z = At @ At.T
+    del At
+    z.diagonal().add_(1e-3)
+    z = 0.5 * (z + z.T)
+    Rt = _pivoted_cholesky_torch(z, K)
+    zh = z.cpu().numpy()
+    del z
+    return DeviceSystem(o, v, P, G, K, seed, eps_o, eps_v, np.ascontiguousarray(Y),
+                        np.ascontiguousarray(x), np.ascontiguousarray(zh), Rt)
+
+
 def random_amplitudes(P: int, o: int, v: int, seed: int,
                       t2_scale: float = 1e-2, t1_scale: float = 1e-2):
     """A symmetric THC core Zc (P x P) and singles t1 (o x v).
@@ -128,7 +215,8 @@ CONFIGS = {
 def config_system(name: str, max_bytes: float = 64e9) -> System:
     """The named workload.  Refuses systems whose float64 Cholesky array
     (K n^2 doubles) exceeds max_bytes: the 2500-basis shape needs 375 GB
-    and n^2 G K = 1.2e18 flops to form."""
+    (and 2 n^2 G K = 1.2e15 flops to form); ``make_device_system`` forms it
+    on a GPU in slabs instead."""
     o, v, P, G, K, seed = CONFIGS[name]
     need = 8.0 * K * (o + v) ** 2
     if need > max_bytes:

@@ -25,8 +25,9 @@ def lib():
 
 def test_header_declares_the_abi():
     assert _declared() == ["thc_config_default", "thc_cp_als", "thc_destroy", "thc_energy",
-                           "thc_energy_noalloc", "thc_init",
-                           "thc_last_error", "thc_mlp_create", "thc_mlp_destroy",
+                           "thc_energy_noalloc", "thc_init", "thc_init_finish",
+                           "thc_last_error", "thc_load_cholesky", "thc_mlp_create",
+                           "thc_mlp_destroy",
                            "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",
                            "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
                            "thc_mp2_density",
@@ -61,6 +62,8 @@ def test_config_defaults_and_argument_errors(lib):
     assert lib.thc_init(None, None, None, None, None, None, None, None, C.byref(h)) == 1
     assert lib.thc_last_error(None).decode() != ""
     assert lib.thc_residual(None, None, None, None, None, None) == 1
+    assert lib.thc_load_cholesky(None, 0, 1, None) == 1
+    assert lib.thc_init_finish(None) == 1
     lib.thc_destroy(None)
 
 
