@@ -71,7 +71,8 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # G=1200, from one ncu capture of the current kernels (summaries in
 # profiles/residual_fp64_o40_v200_P400_G1200_K600_launches.md and
 # profiles/triangle_f32_o40_v200_P400_G1200_K600.md).  Other sizes: null.
-TRIANGLE_TRAFFIC_BYTES = {"fp64": 115.88e9 + 0.52e9, "mixed": 13.55e9 + 0.26e9}
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 115.88e9 + 0.52e9, "fp64tc": 115.88e9 + 0.52e9,
+                          "mixed": 13.55e9 + 0.26e9}
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
@@ -288,8 +289,10 @@ def solve_variants(pkg, s, dev, stream, ctx, args, prec, rate=None):
     out = {}
     f = None
     if not args.skip_fp64_solve:
-        fp64_ctx = ctx if prec == pkg.THC_PREC_FP64 else _context(
-            pkg, s, precision=pkg.THC_PREC_FP64, stream=stream)
+        # the float64 solve runs on the float64 policy benchmarked (CUDA-core
+        # or tensor-core products), the CUDA-core one when mixed is benchmarked
+        fprec = prec if prec != pkg.THC_PREC_MIXED else pkg.THC_PREC_FP64
+        fp64_ctx = ctx if prec == fprec else _context(pkg, s, precision=fprec, stream=stream)
         f = precond.run_solve(fp64_ctx, None, None, r_tol=args.fp64_rtol,
                               max_iter=args.max_iter)
         f["evals_per_s"] = None
@@ -358,7 +361,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64tc", "mixed"],
+                    help="fp64: float64 on the CUDA cores; fp64tc: float64 with the products "
+                         "as exact integer slices on the tensor cores; mixed: float32 + bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
@@ -399,7 +404,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     s = _system(seed_offset=rank, device=dev)
-    prec = pkg.THC_PREC_FP64 if args.precision == "fp64" else pkg.THC_PREC_MIXED
+    prec = {"fp64": pkg.THC_PREC_FP64, "fp64tc": pkg.THC_PREC_FP64_TC,
+            "mixed": pkg.THC_PREC_MIXED}[args.precision]
     t_init = time.perf_counter()
     ctx = _context(pkg, s, dev, precision=prec, stream=stream, t2sq_route=args.t2sq_route)
     init_s = time.perf_counter() - t_init
@@ -473,7 +479,7 @@ def main():
              for k, v in prof.items() if k not in ("residuals", "kernel_launches")}
     dom = max((k for k in steps), key=lambda k: steps[k]["ms_per_residual"])
     tri_ms, tri_fl, tri_n = prof["triangle"]
-    fp64 = args.precision == "fp64"
+    fp64 = args.precision != "mixed"
     total_ms = max(1e-9, sum(v["ms_per_residual"] for v in steps.values()) *
                    max(1, prof["residuals"]))
     if tri_n > 0:

@@ -50,11 +50,16 @@ typedef enum {
     THC_ERR_UNSUPPORTED = 7     /* feature not available on this device */
 } thc_status;
 
-/* Arithmetic policy for the bulk contractions.  FP64: every step in float64.
- * MIXED: operands stored in float32, tensor-core GEMMs with split (hi/lo)
- * bf16 products and float32 accumulation, float32 CUDA-core triangle kernel;
- * the sigma accumulation, energy, least squares and DIIS stay float64. */
-typedef enum { THC_PREC_FP64 = 0, THC_PREC_MIXED = 1 } thc_precision;
+/* Arithmetic policy for the bulk contractions.  FP64: every step in float64
+ * on the CUDA cores.  MIXED: operands stored in float32, tensor-core GEMMs
+ * with split (hi/lo) bf16 products and float32 accumulation, float32
+ * CUDA-core triangle kernel; the sigma accumulation, energy, least squares
+ * and DIIS stay float64.  FP64_TC: float64 storage and arithmetic as FP64,
+ * but every product of at least 3e7 flops runs on the tensor cores as exact
+ * integer products of 8 slices of 7 bits per operand row (scaled by a power
+ * of two per row), combined in float64: each product term is within about
+ * 1.2e-16 of its row and column scale, float64 rounding level. */
+typedef enum { THC_PREC_FP64 = 0, THC_PREC_MIXED = 1, THC_PREC_FP64_TC = 2 } thc_precision;
 
 typedef struct {
     int n_occ;               /* o > 0 */
@@ -381,6 +386,17 @@ thc_status thc_cp_als(int n_occ, int n_vir, int n_rr, int rank, const double* U,
  */
 thc_status thc_selftest_gemm(int cases, unsigned long long seed, double* max_rel_err,
                              int* failures, void* stream);
+
+/*
+ * thc_selftest_gemm_f64 - randomised check of the float64 tensor-core
+ * products (THC_PREC_FP64_TC) against the float64 CUDA-core products:
+ * `cases` random shapes (up to three exact K chunks), orientations, batch
+ * modes and beta, entries uniform or spread over 2^-40 .. 1.  *max_rel: the
+ * largest max|difference| / max(1, max|C|); *failures: cases above
+ * 1e-15 (K + 1).  Errors: THC_ERR_CUDA.
+ */
+thc_status thc_selftest_gemm_f64(int cases, unsigned long long seed, double* max_rel,
+                                 int* failures, void* stream);
 
 /*
  * thc_selftest_bounded_wait - exercise the bounded-wait path that every

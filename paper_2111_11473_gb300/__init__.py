@@ -6,7 +6,7 @@ no CPU fallback: if the library is not built, or no GPU is visible, the calls
 raise.
 """
 from .binding import (Context, Mlp, Report, ThcError, load_library, exported_symbols,
-                      THC_PREC_FP64, THC_PREC_MIXED)
+                      THC_PREC_FP64, THC_PREC_MIXED, THC_PREC_FP64_TC)
 
 __all__ = ["Context", "Mlp", "Report", "ThcError", "load_library", "exported_symbols",
-           "THC_PREC_FP64", "THC_PREC_MIXED"]
+           "THC_PREC_FP64", "THC_PREC_MIXED", "THC_PREC_FP64_TC"]

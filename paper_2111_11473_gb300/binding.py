@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libthc.so")
 
 THC_PREC_FP64 = 0
 THC_PREC_MIXED = 1
+THC_PREC_FP64_TC = 2
 
 STATUS = {0: "THC_OK", 1: "THC_ERR_ARG", 2: "THC_ERR_CUDA", 3: "THC_ERR_OOM",
           4: "THC_ERR_NUMERIC", 5: "THC_ERR_NOT_CONVERGED", 6: "THC_ERR_TIMEOUT",
@@ -100,6 +101,8 @@ _SIGNATURES = {
                                 C.c_ulonglong, C.POINTER(C.c_double)]),
     "thc_mlp_destroy": (None, [_VP]),
     "thc_selftest_bounded_wait": (C.c_int, [C.c_int, _VP]),
+    "thc_selftest_gemm_f64": (C.c_int, [C.c_int, C.c_ulonglong, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int), _VP]),
     "thc_selftest_gemm": (C.c_int, [C.c_int, C.c_ulonglong, C.POINTER(C.c_double),
                                     C.POINTER(C.c_int), _VP]),
     "thc_cp_als": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP,
@@ -161,6 +164,17 @@ def selftest_gemm(cases=64, seed=0, stream=None):
     mr = C.c_double(0)
     nf = C.c_int(0)
     status = lib.thc_selftest_gemm(int(cases), int(seed), C.byref(mr), C.byref(nf), _VP(st))
+    return STATUS.get(status, "?"), mr.value, nf.value
+
+
+def selftest_gemm_f64(cases=64, seed=0, stream=None):
+    """Randomised float64 tensor-core (integer-slice) vs CUDA-core product
+    check; returns (status name, max relative difference, failures)."""
+    lib = load_library()
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    mr = C.c_double(0)
+    nf = C.c_int(0)
+    status = lib.thc_selftest_gemm_f64(int(cases), int(seed), C.byref(mr), C.byref(nf), _VP(st))
     return STATUS.get(status, "?"), mr.value, nf.value
 
 

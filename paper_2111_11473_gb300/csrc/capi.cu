@@ -37,7 +37,8 @@ thc::Err check_config(const thc_config* cfg) {
     if (!cfg) return {THC_ERR_ARG, "cfg is NULL"};
     if (cfg->n_occ <= 0 || cfg->n_vir <= 0 || cfg->n_p <= 0 || cfg->n_g <= 0 || cfg->n_k <= 0)
         return {THC_ERR_ARG, "every dimension must be positive"};
-    if (cfg->precision != THC_PREC_FP64 && cfg->precision != THC_PREC_MIXED)
+    if (cfg->precision != THC_PREC_FP64 && cfg->precision != THC_PREC_MIXED &&
+        cfg->precision != THC_PREC_FP64_TC)
         return {THC_ERR_ARG, "unknown precision policy"};
     if (cfg->k_slab < 0 || cfg->i_chunk < 0 || cfg->x_block < 0 || cfg->x_block6 < 0)
         return {THC_ERR_ARG, "blocking sizes must be >= 0"};
@@ -113,7 +114,7 @@ thc_status thc_init(const thc_config* cfg, const double* eps_occ, const double* 
     if (c->cfg.lsq_rel_cutoff <= 0) c->cfg.lsq_rel_cutoff = 1e-10;
     c->st = (cudaStream_t)stream;
     {
-        if (cfg->precision == THC_PREC_FP64) {
+        if (cfg->precision != THC_PREC_MIXED) {
             c->e64.reset(new thc::Engine<double>());
             e = c->e64->init(c->cfg, eps_occ, eps_vir, Y, L, x, z, c->st);
         } else {
@@ -370,6 +371,25 @@ thc_status thc_selftest_gemm(int cases, unsigned long long seed, double* max_rel
     }
     if (nf) {
         g_init_error = "thc_selftest_gemm: " + std::to_string(nf) + " case(s) outside the bound";
+        return THC_ERR_NUMERIC;
+    }
+    return THC_OK;
+}
+
+thc_status thc_selftest_gemm_f64(int cases, unsigned long long seed, double* max_rel,
+                                 int* failures, void* stream) {
+    if (cases < 0) return THC_ERR_ARG;
+    double mr = 0;
+    int nf = 0;
+    cudaError_t e = thc::gemm_f64_tc_selftest(cases, seed, &mr, &nf, (cudaStream_t)stream);
+    if (max_rel) *max_rel = mr;
+    if (failures) *failures = nf;
+    if (e != cudaSuccess) {
+        g_init_error = std::string("thc_selftest_gemm_f64: ") + cudaGetErrorString(e);
+        return THC_ERR_CUDA;
+    }
+    if (nf) {
+        g_init_error = "thc_selftest_gemm_f64: " + std::to_string(nf) + " case(s) outside the bound";
         return THC_ERR_NUMERIC;
     }
     return THC_OK;

@@ -163,6 +163,19 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
         }
+    } else {
+        // float64 products by exact integer slices on the tensor cores, when
+        // the estimated time beats the CUDA cores (1 TFLOP/s): 36 slice-pair
+        // products (about 1.2 PFLOP/s, each writing its float32 output) and
+        // float64 passes over the output, two pairs per pass at the largest.
+        const double out = (double)M * N * (reduce ? 1 : batch);
+        const double t_tc = 36.0 * (fl / 1.2e15 + out * 4.0 / 5e12 + 5e-6) +
+                            18.0 * out * 20.0 / 5e12;
+        if (f64tc && fl >= 3.0e7 && Kd >= 16 && t_tc < fl / 1.0e12) {
+            cudaError_t e = gemm_f64_tc(g, f64ws, st);
+            if (e == cudaSuccess) return Err{};
+            if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
+        }
     }
     THC_CUDA(gemm_simt(g, st));
     return Err{};
@@ -594,45 +607,74 @@ Err Engine<T>::init_finish() {
     THC_TRY(N7.alloc((size_t)xb * o * G));
     THC_TRY(E7.alloc((size_t)xb * G * G));
     THC_TRY(P7.alloc((size_t)xb * o * G));
-    THC_TRY(G7.alloc((size_t)xb * ov));
+    if (!alg7_dense) THC_TRY(G7.alloc((size_t)P * ov));   // G_ia^X for every X
     THC_TRY(tcerr.alloc(1));
     THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
-    if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
-        // Packed-operand workspace: the largest product of the residual.
-        struct Shape { long long M, N, K, b; };
+    // Products of the residual on the routes in use (the tensor-core
+    // workspaces are sized from the largest).
+    struct Shape { long long M, N, K, b; };
+    std::vector<Shape> shapes;
+    {
         const long long xP = (long long)x6 * P;
-        std::vector<Shape> shapes = {
+        shapes = {
             {P, P, (long long)kb * P, 1}, {(long long)P * kb, P, P, 1}, {P, P, o, kb},
             {P, P, v, kb}, {v, P, v, kb}, {o, G, v, xb}, {G, G, o, xb}, {o, G, G, xb},
-            {o, v, G, xb}, {xb, P, ov, 1}, {G, P, G, 1}, {P, P, G, 1},
+            {o, v, G, xb}, {P, P, ov, 1}, {G, P, G, 1}, {P, P, G, 1},
             {P, ov, P, 1}, {o, P, P, xb}, {o, v, P, xb}, {ov, P, P, 1}, {P, P, K, 1}};
         if (alg7_dense) {
             shapes.push_back({P, G, ov, 1});
             shapes.push_back({P, ov, ov, 1});
-            shapes.push_back({P, P, ov, 1});
         }
         if (!t2sq_n5) {
             for (const Shape& sh : std::initializer_list<Shape>{
                      {x6, P, v, o}, {x6, P, o, v}, {ic, xP, o, 1}, {ic, xP, v, 1},
                      {o, P, P, x6}, {o, v, P, x6}, {x6, P, ov, 1}})
                 shapes.push_back(sh);
+        } else {
+            const long long nb = nb45;
+            for (const Shape& sh : std::initializer_list<Shape>{
+                     {v, v, P, nb}, {v, G, v, nb}, {G, G, v, nb}, {o, G, G, nb},
+                     {o, o, G, nb}, {P, P, o, nb}, {v, P, P, nb}, {P, v, v, nb},
+                     {P, P, v, nb}, {o, v, P, nb}, {o, G, v, nb}, {G, G, o, nb},
+                     {o, v, G, nb}, {v, P, o, nb}, {o, P, P, nb}, {P, v, o, nb},
+                     {v, P, P, o}, {o, P, P, v}})
+                shapes.push_back(sh);
         }
+    }
+    if (std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC) {
+        // Slices of the largest product's operands; float32 slice-pair
+        // products of the largest output, several pairs per float64 pass
+        // (up to 2 GiB) when they are small.
+        size_t sl = 0, pt = 0, ex = 0;
+        for (const Shape& sh : shapes) {
+            size_t a = 0, b = 0, c = 0;
+            gemm_f64_tc_sizes((int)std::min<long long>(sh.M, INT32_MAX),
+                              (int)std::min<long long>(sh.N, INT32_MAX), (int)sh.K, (int)sh.b,
+                              false, &a, &b, &c);
+            sl = std::max(sl, a);
+            pt = std::max(pt, b);
+            ex = std::max(ex, c);
+        }
+        pt = std::max(pt, std::min<size_t>(36 * pt, (size_t)1 << 29));
+        THC_TRY(f64sl.alloc(sl));
+        THC_TRY(f64part.alloc(pt));
+        THC_TRY(f64exp.alloc(ex));
+        f64ws.slices = f64sl.p;
+        f64ws.slice_elems = f64sl.n;
+        f64ws.part = f64part.p;
+        f64ws.part_elems = f64part.n;
+        f64ws.expo = f64exp.p;
+        f64ws.expo_elems = f64exp.n;
+        f64ws.err = tcerr.p;
+        f64tc = true;
+    }
+    if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
+        // Packed-operand workspace: the largest product of the residual.
         size_t need = 0;
         for (const Shape& sh : shapes)
             need = std::max(need, gemm_tc_pack_elems((int)std::min<long long>(sh.M, INT32_MAX),
                                                      (int)std::min<long long>(sh.N, INT32_MAX),
                                                      (int)sh.K, (int)sh.b, false));
-        if (t2sq_n5) {
-            const long long nb = nb45;
-            const Shape s45[] = {{v, v, P, nb}, {v, G, v, nb}, {G, G, v, nb}, {o, G, G, nb},
-                                 {o, o, G, nb}, {P, P, o, nb}, {v, P, P, nb}, {P, v, v, nb},
-                                 {P, P, v, nb}, {o, v, P, nb}, {o, G, v, nb}, {G, G, o, nb},
-                                 {o, v, G, nb}, {v, P, o, nb}, {o, P, P, nb}, {P, v, o, nb},
-                                 {v, P, P, o}, {o, P, P, v}};
-            for (const Shape& sh : s45)
-                need = std::max(need, gemm_tc_pack_elems((int)sh.M, (int)sh.N, (int)sh.K,
-                                                         (int)sh.b, false));
-        }
         tc_products = cfg.tc_products;
         THC_TRY(tcpack.alloc(need));
         THC_TRY(tcpart.alloc((size_t)std::max<long long>(8 * PP, 1 << 22)));
@@ -878,11 +920,12 @@ Err Engine<T>::alg7(T* sgm) {
             THC_CUDA(hadamard_batched(E7.p, z.p, GG, nx, st));
             THC_TRY(mm(o, G, G, rm(xo, G), tr(E7.p, G), P7.p, G, 1, 0, nx, 0, GG,
                        (long long)o * G));
-            THC_TRY(mm(o, v, G, rm(P7.p, G), tr(xv, G), G7.p, v, 1, 0, nx, (long long)o * G, 0,
-                       ov));
-            THC_TRY(mm(nx, P, (int)ov, rm(G7.p, ov), tr(src, ov), sgm + (long long)X0 * P, P,
-                       sign, 1));
+            THC_TRY(mm(o, v, G, rm(P7.p, G), tr(xv, G), G7.p + (long long)X0 * ov, v, 1, 0, nx,
+                       (long long)o * G, 0, ov));
         }
+        // sigma^XX' += sign sum_ia G_ia^X src_ia^X' for all X at once, so
+        // that src is packed for the tensor cores once per pass.
+        THC_TRY(mm(P, P, (int)ov, rm(G7.p, ov), tr(src, ov), sgm, P, sign, 1));
     }
     // D^T = z C^T (line 10, z symmetric); sigma += C D^T
     THC_TRY(mm(G, P, G, rm(z.p, G), rm(C7.p, P), D7.p, P, 1, 0));

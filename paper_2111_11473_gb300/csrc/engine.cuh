@@ -108,6 +108,11 @@ struct Engine {
     DBuf<int> tcerr;                        // bounded-wait expiry flag
     TcWorkspace tcws;
     PackCache pcache;                       // packed constant operands (float engine)
+    bool f64tc = false;                     // float64 products on the tensor cores
+    F64TcWorkspace f64ws;
+    DBuf<__nv_bfloat16> f64sl;              // operand slices
+    DBuf<float> f64part;                    // slice-pair products
+    DBuf<int> f64exp;                       // per-row exponents
     ~Engine() { pcache.release(); }
     Err check_timeout();
     std::vector<double> eps_h;              // orbital energies (host copy)

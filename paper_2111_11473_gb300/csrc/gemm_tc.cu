@@ -769,6 +769,286 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// Float64 products on the tensor cores by exact integer slices (the splitting
+// scheme of Ozaki et al.).  Every row r of an operand (UMMA orientation, K
+// along the row; in a batch-reduced product the row runs over all batches) is
+// scaled by 2^-e_r, e_r the binary exponent of its largest entry, so that its
+// entries lie in (-1, 1), and is cut into kSlices = 8 signed 7-bit integers:
+//   x = 2^e_r (sum_t a_t 2^(-7t) + r_x),   a_t in [-127, 127], |r_x| < 2^-56.
+// A slice is exact in bf16, a product of two is an integer below 2^14, and a
+// float32 sum of at most 1024 of them is an integer below 2^24, so the tensor
+// cores' float32 accumulation over K chunks of 1024 is exact.  The 36 slice
+// pairs (t, u) with t + u <= 9 are added in float64 with their scales
+// 2^(e_r + e_c - 7 (t + u)).  The pairs left out (t + u = 10 and beyond) and
+// the remainders change each product term a_rk b_kc by less than about
+// 9 2^-56 = 1.2e-16 of 2^(e_r + e_c), the size of float64 rounding.
+namespace {
+
+constexpr int kSlices = 8;
+constexpr int kChunkSteps = 16;            // 16 x 64 = 1024 K per exact partial sum
+constexpr int kExpZero = -1100;            // exponents below this mark all-zero rows
+
+// Pairs (t, u), 1-based, t + u <= kSlices + 1: 36 of them.
+constexpr int kPairs = kSlices * (kSlices + 1) / 2;
+
+__device__ __forceinline__ int f64_exponent(double m) {
+    // m >= 0; the e with m < 2^e (e = floor(log2 m) + 1), from the IEEE-754 fields
+    const long long bits = __double_as_longlong(m);
+    const int f = (int)((bits >> 52) & 0x7ff);
+    return f == 0 ? -1022 : f - 1022;
+}
+
+// Load a PK_R x PK_K tile of a strided float64 operand (zeros outside) the way
+// k_pack does: reads run along whichever index is contiguous.
+__device__ __forceinline__ void f64_tile(double (*tile)[PK_K + 1], const double* s, long long rs,
+                                         long long ks, int R, int Kd, int r0, int k0) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (ks <= rs) {
+        for (int rr = warp; rr < PK_R; rr += 8) {
+            const int r = r0 + rr;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = k0 + h * 32 + lane;
+                tile[rr][h * 32 + lane] =
+                    (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.0;
+            }
+        }
+    } else {
+        for (int kk = warp; kk < PK_K; kk += 8) {
+            const int r = r0 + lane, k = k0 + kk;
+            tile[lane][kk] = (r < R && k < Kd) ? s[(long long)r * rs + (long long)k * ks] : 0.0;
+        }
+    }
+}
+
+// expo[bo * Rp + r] = max over the row of the exponent of |x| (atomic over
+// the K tiles; the array starts at INT_MIN-like values).
+__global__ void __launch_bounds__(256) k_row_exp(const double* src, long long rs, long long ks,
+                                                 long long bs, int R, int Kd, int Rp,
+                                                 int reduce, int* expo) {
+    __shared__ double tile[PK_R][PK_K + 1];
+    const int b = blockIdx.z;
+    const int k0 = blockIdx.x * PK_K;
+    const double* s = src + (long long)b * bs;
+    const int bo = reduce ? 0 : b;
+    const int t = threadIdx.x;
+    for (int r0 = blockIdx.y * PK_R; r0 < Rp; r0 += gridDim.y * PK_R) {
+        f64_tile(tile, s, rs, ks, R, Kd, r0, k0);
+        __syncthreads();
+        const int rr = t >> 3, oct = t & 7;
+        double m = 0.0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m = fmax(m, fabs(tile[rr][oct * 8 + e]));
+        // the 8 threads of a row are consecutive lanes of one warp
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o, 8));
+        const int r = r0 + rr;
+        if (oct == 0 && r < R && m > 0.0) atomicMax(&expo[(long long)bo * Rp + r], f64_exponent(m));
+        __syncthreads();
+    }
+}
+
+// Slices of one operand: out[t][bo][r][kb * Kp + k] = a_{t+1}(x(b, r, k)) as
+// bf16 (zero in the padding), in the packed K-major layout of k_pack.
+__global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs, long long ks,
+                                                 long long bs, int R, int Kd, int nb, int Rp,
+                                                 int Kp, int reduce, const int* expo,
+                                                 long long slice_elems, __nv_bfloat16* out) {
+    __shared__ double tile[PK_R][PK_K + 1];
+    const int b = blockIdx.z;
+    const int k0 = blockIdx.x * PK_K;
+    const double* s = src + (long long)b * bs;
+    const long long Ktot = reduce ? (long long)nb * Kp : Kp;
+    const int bo = reduce ? 0 : b, kb = reduce ? b : 0;
+    const int t = threadIdx.x;
+    for (int r0 = blockIdx.y * PK_R; r0 < Rp; r0 += gridDim.y * PK_R) {
+        f64_tile(tile, s, rs, ks, R, Kd, r0, k0);
+        __syncthreads();
+        const int rr = t >> 3, oct = t & 7;
+        const int r = r0 + rr, k = k0 + oct * 8;
+        if (r < Rp && k < Kp) {
+            const int e = r < R ? expo[(long long)bo * Rp + r] : kExpZero - 1;
+            union { __nv_bfloat16 h[8]; uint4 u; } v[kSlices];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double x = e < kExpZero ? 0.0 : scalbn(tile[rr][oct * 8 + j], -e);
+#pragma unroll
+                for (int q = 0; q < kSlices; ++q) {
+                    x *= 128.0;
+                    const double a = trunc(x);
+                    x -= a;
+                    v[q].h[j] = __double2bfloat16(a);
+                }
+            }
+            const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
+#pragma unroll
+            for (int q = 0; q < kSlices; ++q)
+                *reinterpret_cast<uint4*>(out + q * slice_elems + o) = v[q].u;
+        }
+        __syncthreads();
+    }
+}
+
+// C(b, i, j) = [beta C] + alpha 2^(eA + eB) sum_pairs 2^(-7 (t + u)) sum_s part,
+// for the pairs p0 .. p0 + np - 1 of this pass (first: the beta term).
+__global__ void k_f64_accumulate(const float* part, int np, int p0, int splits, int nbo, int M,
+                                 int N, const int* eA, int RpA, int a_bc, const int* eB, int RpB,
+                                 int b_bc, double* C, long long crs, long long ccs,
+                                 long long cbs, double alpha, double beta, int first) {
+    const long long MN = (long long)M * N, total = MN * nbo;
+    const long long per_pair = MN * nbo * splits;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / MN);
+        const long long e = idx % MN;
+        const int i = (int)(e / N), j = (int)(e % N);
+        const int ea = eA[(long long)(a_bc ? 0 : b) * RpA + i];
+        const int eb = eB[(long long)(b_bc ? 0 : b) * RpB + j];
+        double acc = 0.0;
+        if (ea >= kExpZero && eb >= kExpZero) {
+            int p = 0;
+            for (int t = 1; t <= kSlices; ++t)
+                for (int u = 1; t + u <= kSlices + 1; ++u, ++p) {
+                    if (p < p0 || p >= p0 + np) continue;
+                    const float* q = part + (long long)(p - p0) * per_pair + (long long)b * MN + e;
+                    double s = 0.0;
+                    for (int sp = 0; sp < splits; ++sp) s += (double)q[(long long)sp * nbo * MN];
+                    acc += scalbn(s, -7 * (t + u));
+                }
+            acc = scalbn(acc, ea + eb);
+        }
+        double* c = C + (long long)b * cbs + (long long)i * crs + (long long)j * ccs;
+        const double prev = first ? (beta != 0.0 ? beta * *c : 0.0) : *c;
+        *c = prev + alpha * acc;
+    }
+}
+
+}  // namespace
+
+void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slice_elems,
+                       size_t* part_elems, size_t* expo_elems) {
+    const long long Kp = rup(std::max(K, 1), BK);
+    const long long Ktot = reduce ? Kp * batch : Kp;
+    const long long nbo = reduce ? 1 : batch;
+    const long long Rm = rup(M, 128), Rn = rup(N, 128);
+    *slice_elems = (size_t)(kSlices * (Rm + Rn) * Ktot * nbo);
+    const long long splits = std::max<long long>(1, (Ktot / BK + kChunkSteps - 1) / kChunkSteps);
+    *part_elems = (size_t)(splits * nbo * (long long)M * N);
+    *expo_elems = (size_t)((Rm + Rn) * nbo);
+}
+
+cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    const bool swap = g.N > g.M;
+    const int Mr = swap ? g.N : g.M, Nr = swap ? g.M : g.N;
+    int BN = 128;
+    if (Nr <= 32) BN = 32;
+    else if (Nr <= 64) BN = 64;
+    const long long Kp = rup(std::max(g.K, 1), BK);
+    const int nb = g.batch;
+    const int nbo = g.reduce ? 1 : nb;
+    const long long Ktot = g.reduce ? Kp * nb : Kp;
+    const long long RpA = rup(Mr, BM), RpB = rup(Nr, BN);
+    View<double> va = g.A, vb{g.B.p, g.B.cs, g.B.rs};
+    long long sa = g.sAb, sb = g.sBb;
+    if (swap) {
+        std::swap(va, vb);
+        std::swap(sa, sb);
+    }
+    const bool a_bc = !g.reduce && nb > 1 && sa == 0;
+    const bool b_bc = !g.reduce && nb > 1 && sb == 0;
+    const int nba = a_bc ? 1 : nbo, nbb = b_bc ? 1 : nbo;
+    const long long sliceA = RpA * Ktot * nba, sliceB = RpB * Ktot * nbb;
+    if ((size_t)(kSlices * (sliceA + sliceB)) > ws.slice_elems) return cudaErrorMemoryAllocation;
+    if ((size_t)(RpA * nba + RpB * nbb) > ws.expo_elems) return cudaErrorMemoryAllocation;
+    const int ksteps = (int)(Ktot / BK);
+    const int mblocks = (int)(RpA / BM), nblocks = (int)(RpB / BN);
+    const long long tiles = (long long)mblocks * nblocks * nbo;
+    // Splits: K chunks of at most 1024 (exact partial sums), more when the
+    // tiles alone do not fill the GPU.
+    const int exact = (ksteps + kChunkSteps - 1) / kChunkSteps;
+    int splits = exact;
+    if (tiles * splits < 152 && ksteps >= 8)
+        splits = std::max<int>(splits, (int)std::min<long long>({(152 + tiles - 1) / tiles,
+                                                                  ksteps / 4, 32}));
+    while (splits > exact && (size_t)splits * nbo * Mr * Nr > ws.part_elems) --splits;
+    const long long one = (long long)splits * nbo * Mr * Nr;   // float32 partials of one pair
+    if ((size_t)one > ws.part_elems) return cudaErrorMemoryAllocation;
+    const int group = (int)std::min<long long>(kPairs, (long long)ws.part_elems / one);
+
+    __nv_bfloat16* slA = ws.slices;
+    __nv_bfloat16* slB = ws.slices + kSlices * sliceA;
+    int* eA = ws.expo;
+    int* eB = ws.expo + RpA * nba;
+    // Row exponents and slices of both operands.
+    const int red = g.reduce ? 1 : 0;
+    if ((e = cudaMemsetAsync(ws.expo, 0x80, sizeof(int) * (RpA * nba + RpB * nbb), s)) !=
+        cudaSuccess)
+        return e;
+    struct Side { View<double> v; long long sbat; int R; long long Rp; int nbg; __nv_bfloat16* sl;
+                  long long selems; int* ex; };
+    const Side sides[2] = {{va, sa, Mr, RpA, a_bc ? 1 : nb, slA, sliceA, eA},
+                           {vb, sb, Nr, RpB, b_bc ? 1 : nb, slB, sliceB, eB}};
+    for (const Side& sd : sides) {
+        const dim3 grid(cdiv(Kp, PK_K), std::min<unsigned>(cdiv(sd.Rp, PK_R), 65535), sd.nbg);
+        k_row_exp<<<grid, 256, 0, s>>>(sd.v.p, sd.v.rs, sd.v.cs, sd.sbat, sd.R, g.K, (int)sd.Rp,
+                                       red, sd.ex);
+        k_slice64<<<grid, 256, 0, s>>>(sd.v.p, sd.v.rs, sd.v.cs, sd.sbat, sd.R, g.K, nb,
+                                       (int)sd.Rp, (int)Kp, red, sd.ex, sd.selems, sd.sl);
+        count_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // Slice maps (one per slice and operand).
+    CUtensorMap mA[kSlices], mB[kSlices];
+    for (int q = 0; q < kSlices; ++q) {
+        if ((e = make_map(&mA[q], slA + q * sliceA, Ktot, RpA, nba, BM)) != cudaSuccess) return e;
+        if ((e = make_map(&mB[q], slB + q * sliceB, Ktot, RpB, nbb, BN)) != cudaSuccess) return e;
+    }
+    TcArgs a{};
+    a.M = Mr;
+    a.N = Nr;
+    a.nbo = nbo;
+    a.ksteps = ksteps;
+    a.nprod = 1;
+    a.a_bcast = a_bc ? 1 : 0;
+    a.b_bcast = b_bc ? 1 : 0;
+    a.err = ws.err;
+    a.alpha = 1.f;
+    a.beta = 0.f;
+    a.splits = splits;
+    a.mblocks = mblocks;
+    a.nblocks = nblocks;
+    a.ntiles = tiles * splits;
+    a.crs = Nr;
+    a.ccs = 1;
+    a.cbs = (long long)Mr * Nr;
+    const long long crs = swap ? 1 : g.ldc, ccs = swap ? g.ldc : 1;
+    const long long total = (long long)Mr * Nr * nbo;
+    const unsigned rblocks = (unsigned)std::min<long long>((total + 255) / 256, 152 * 16);
+    int p = 0, p0 = 0;
+    for (int t = 1; t <= kSlices; ++t)
+        for (int u = 1; t + u <= kSlices + 1; ++u, ++p) {
+            const CUtensorMap maps[4] = {mA[t - 1], mA[t - 1], mB[u - 1], mB[u - 1]};
+            a.C = ws.part + (long long)(p - p0) * one;
+            if (BN == 32) e = launch_tc<32>(maps, a, s);
+            else if (BN == 64) e = launch_tc<64>(maps, a, s);
+            else e = launch_tc<128>(maps, a, s);
+            if (e != cudaSuccess) return e;
+            if (p - p0 + 1 == group || p + 1 == kPairs) {
+                k_f64_accumulate<<<rblocks, 256, 0, s>>>(
+                    ws.part, p - p0 + 1, p0, splits, nbo, Mr, Nr, eA, (int)RpA, a_bc ? 1 : 0, eB,
+                    (int)RpB, b_bc ? 1 : 0, g.C, crs, ccs, g.reduce ? 0 : g.sCb, g.alpha, g.beta,
+                    p0 == 0 ? 1 : 0);
+                count_launches(1);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                p0 = p + 1;
+            }
+        }
+    return cudaSuccess;
+}
 
 // ---------------------------------------------------------------------------
 // Randomised self-test: tensor-core products against the CUDA-core products
@@ -892,6 +1172,126 @@ cudaError_t gemm_tc_selftest(int cases, unsigned long long seed, double* max_rel
     }
     for (void* p : {(void*)A, (void*)B, (void*)C1, (void*)C2, (void*)red, (void*)simt,
                     (void*)ws.buf, (void*)ws.partial, (void*)ws.err})
+        if (p) cudaFree(p);
+    return e;
+}
+
+namespace {
+
+__global__ void k_fill_uniform64(double* p, long long n, unsigned long long seed, int spread) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        double v = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        // spread > 0: magnitudes over 2^-spread .. 1 (rows with a wide range)
+        if (spread > 0) v = scalbn(v, -(int)((z >> 3) % (unsigned long long)(spread + 1)));
+        p[i] = v;
+    }
+}
+
+__global__ void k_max_abs_diff64(const double* a, const double* b, long long n, double* out) {
+    double m = 0.0, s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        m = fmax(m, fabs(a[i] - b[i]));
+        s = fmax(s, fabs(b[i]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+        atomicMax(reinterpret_cast<unsigned long long*>(out + 1), (unsigned long long)__double_as_longlong(s));
+    }
+}
+
+}  // namespace
+
+cudaError_t gemm_f64_tc_selftest(int cases, unsigned long long seed, double* max_rel,
+                                 int* failures, cudaStream_t st) {
+    *max_rel = 0;
+    *failures = 0;
+    const long long cap = 1LL << 21;   // elements per operand buffer
+    double *A = nullptr, *B = nullptr, *C1 = nullptr, *C2 = nullptr, *red = nullptr, *simt = nullptr;
+    F64TcWorkspace ws{};
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    al((void**)&A, cap * 8);
+    al((void**)&B, cap * 8);
+    al((void**)&C1, cap * 8);
+    al((void**)&C2, cap * 8);
+    al((void**)&red, 16);
+    al((void**)&simt, cap * 8);
+    ws.slice_elems = (size_t)1 << 26;
+    al((void**)&ws.slices, ws.slice_elems * 2);
+    ws.part_elems = (size_t)1 << 24;
+    al((void**)&ws.part, ws.part_elems * 4);
+    ws.expo_elems = (size_t)1 << 16;
+    al((void**)&ws.expo, ws.expo_elems * 4);
+    al((void**)&ws.err, 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.err, 0, 4, st);
+    unsigned long long s = seed * 2654435761ULL + 7;
+    for (int c = 0; c < cases && e == cudaSuccess; ++c) {
+        Gemm<double> g;
+        g.M = 1 + (int)(st_next(s) % 600);
+        g.N = 1 + (int)(st_next(s) % 600);
+        g.K = 1 + (int)(st_next(s) % 2600);    // up to three exact K chunks
+        g.batch = 1 + (int)(st_next(s) % 4);
+        const int mode = (int)(st_next(s) % 4);   // 0 separate, 1 shared A, 2 shared B, 3 reduce
+        g.reduce = mode == 3 && g.batch > 1;
+        const bool ta = st_next(s) & 1, tb = st_next(s) & 1;
+        const int spread = (st_next(s) % 3 == 0) ? 40 : 0;
+        g.beta = (st_next(s) & 1) ? 0.5 : 0.0;
+        g.alpha = 1.25;
+        while ((long long)g.batch * g.M * g.K > cap || (long long)g.batch * g.K * g.N > cap ||
+               (long long)g.batch * g.M * g.N > cap)
+            g.K = std::max(1, g.K / 2), g.M = std::max(1, g.M * 3 / 4);
+        const long long sa = (long long)g.M * g.K, sb = (long long)g.K * g.N,
+                        sc = (long long)g.M * g.N;
+        g.A = ta ? View<double>{A, 1, g.M} : View<double>{A, g.K, 1};
+        g.B = tb ? View<double>{B, 1, g.K} : View<double>{B, g.N, 1};
+        g.sAb = mode == 1 ? 0 : sa;
+        g.sBb = mode == 2 ? 0 : sb;
+        g.ldc = g.N;
+        g.sCb = sc;
+        const long long nC = (g.reduce ? 1 : g.batch) * sc;
+        k_fill_uniform64<<<256, 256, 0, st>>>(A, g.batch * sa, st_next(s), spread);
+        k_fill_uniform64<<<256, 256, 0, st>>>(B, g.batch * sb, st_next(s), spread);
+        k_fill_uniform64<<<256, 256, 0, st>>>(C1, nC, st_next(s), 0);
+        count_launches(3);
+        if ((e = cudaMemcpyAsync(C2, C1, nC * 8, cudaMemcpyDeviceToDevice, st))) break;
+        Gemm<double> h = g;
+        g.C = C1;
+        h.C = C2;
+        h.ws = simt;
+        h.ws_elems = cap;
+        if ((e = gemm_f64_tc(g, ws, st))) break;
+        if ((e = gemm_simt(h, st))) break;
+        if ((e = cudaMemsetAsync(red, 0, 16, st))) break;
+        k_max_abs_diff64<<<256, 256, 0, st>>>(C1, C2, nC, red);
+        count_launches(1);
+        double hr[2] = {0, 0};
+        int herr = 0;
+        if ((e = cudaMemcpyAsync(hr, red, 16, cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaMemcpyAsync(&herr, ws.err, 4, cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaStreamSynchronize(st))) break;
+        // Both sides are float64-accurate: a few units of 2^-53 times the
+        // size of the sums (K terms of up to 1/4, and beta C).
+        const double scale = std::max(1.0, hr[1]);
+        const double rel = hr[0] / scale;
+        const double bound = 1e-15 * ((double)g.K * (g.reduce ? g.batch : 1) + 1);
+        *max_rel = std::max(*max_rel, rel);
+        if (herr || !(rel <= bound)) ++*failures;
+    }
+    for (void* p : {(void*)A, (void*)B, (void*)C1, (void*)C2, (void*)red, (void*)simt,
+                    (void*)ws.slices, (void*)ws.part, (void*)ws.expo, (void*)ws.err})
         if (p) cudaFree(p);
     return e;
 }

@@ -77,4 +77,27 @@ size_t gemm_tc_pack_elems(int M, int N, int K, int batch, bool reduce);
 cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cudaStream_t s,
                     PackCache* cache = nullptr);
 
+// Float64 products on the tensor cores: each operand row is cut into 8
+// slices of 7-bit integers below a per-row power of two, the 36 slice pairs
+// that matter are multiplied exactly (bf16 integer products, float32 sums of
+// at most 1024 terms) and combined in float64.  Returns
+// cudaErrorMemoryAllocation (without launching) if the workspace is too small.
+struct F64TcWorkspace {
+    __nv_bfloat16* slices = nullptr;   // operand slices
+    size_t slice_elems = 0;
+    float* part = nullptr;             // float32 slice-pair products (exact integers)
+    size_t part_elems = 0;
+    int* expo = nullptr;               // per-row binary exponents
+    size_t expo_elems = 0;
+    int* err = nullptr;                // bounded-wait expiry flag
+};
+// Workspace needed by one product (part: one slice pair; more pairs per
+// float64 pass when there is room).
+void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slice_elems,
+                       size_t* part_elems, size_t* expo_elems);
+cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s);
+// Randomised check of gemm_f64_tc against the float64 CUDA-core product.
+cudaError_t gemm_f64_tc_selftest(int cases, unsigned long long seed, double* max_rel,
+                                 int* failures, cudaStream_t st);
+
 }  // namespace thc

@@ -32,7 +32,8 @@ def test_header_declares_the_abi():
                            "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
                            "thc_mp2_density",
                            "thc_profile_enable", "thc_profile_read",
-                           "thc_residual", "thc_selftest_bounded_wait", "thc_selftest_gemm", "thc_solve",
+                           "thc_residual", "thc_selftest_bounded_wait", "thc_selftest_gemm", "thc_selftest_gemm_f64",
+                           "thc_solve",
                            "thc_solve_opts_default", "thc_solve_pairs", "thc_step_name"]
 
 
