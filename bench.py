@@ -4,7 +4,11 @@ One step = one evaluation of the projected residual (Algs. 1-10: T1 dressing,
 fused Cholesky-slab pass, Algs. 6 and 7, Algs. 9-10) plus the energy, through
 thc_residual, on the synthetic system o=40, v=200, P=400, G=1200, K=600
 (seed 1).  The state (Zc, t1) is the solver's iterate after two Jacobi steps
-from zero.
+from zero.  Default arithmetic: float64 throughout, with the products run on
+the tensor cores as exact integer slices combined in float64 (agreeing with
+the float64 CUDA-core products to float64 rounding); --precision fp64 keeps
+every product on the CUDA cores, --precision mixed is the float32 + bf16x3
+policy.
 
   value      residual evaluations / s with inputs resident in HBM (device
              pointers), CUDA events on the library's stream, max over ranks
@@ -361,9 +365,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64tc", "mixed"],
-                    help="fp64: float64 on the CUDA cores; fp64tc: float64 with the products "
-                         "as exact integer slices on the tensor cores; mixed: float32 + bf16x3")
+    ap.add_argument("--precision", default="fp64tc", choices=["fp64", "fp64tc", "mixed"],
+                    help="fp64tc (default): float64, the products as exact integer slices on "
+                         "the tensor cores combined in float64; fp64: float64 on the CUDA "
+                         "cores; mixed: float32 + bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
@@ -515,6 +520,11 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32+bf16x3",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
+                   "products": {"fp64tc": "float64 by 8 exact 7-bit integer slices per operand "
+                                          "row on the tensor cores, combined in float64",
+                                "fp64": "float64 on the CUDA cores",
+                                "mixed": "float32 operands, bf16 hi/lo on the tensor cores"}[
+                                    args.precision],
                    "t2sq_route": args.t2sq_route,
                    "state": "solver iterate after two Jacobi steps from zero",
                    "l2": "inputs larger than L2 (Cholesky blocks %.3g GB)" % (

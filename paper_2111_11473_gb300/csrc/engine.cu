@@ -166,11 +166,11 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     } else {
         // float64 products by exact integer slices on the tensor cores, when
         // the estimated time beats the CUDA cores (1 TFLOP/s): 36 slice-pair
-        // products (about 1.2 PFLOP/s, each writing its float32 output) and
-        // float64 passes over the output, two pairs per pass at the largest.
+        // products at about 1.2 PFLOP/s, 8 level outputs written and read
+        // back in float32, one float64 pass over C and about 14 launches.
         const double out = (double)M * N * (reduce ? 1 : batch);
-        const double t_tc = 36.0 * (fl / 1.2e15 + out * 4.0 / 5e12 + 5e-6) +
-                            18.0 * out * 20.0 / 5e12;
+        const double t_tc = 36.0 * fl / 1.2e15 + 8.0 * out * 8.0 / 5e12 + out * 16.0 / 5e12 +
+                            14.0 * 5e-6;
         if (f64tc && fl >= 3.0e7 && Kd >= 16 && t_tc < fl / 1.0e12) {
             cudaError_t e = gemm_f64_tc(g, f64ws, st);
             if (e == cudaSuccess) return Err{};
@@ -642,9 +642,9 @@ Err Engine<T>::init_finish() {
         }
     }
     if (std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC) {
-        // Slices of the largest product's operands; float32 slice-pair
-        // products of the largest output, several pairs per float64 pass
-        // (up to 2 GiB) when they are small.
+        // Slices of the largest product's operands and the float32 level
+        // outputs of the largest product, at most a quarter of the free
+        // memory (a product that does not fit runs on the CUDA cores).
         size_t sl = 0, pt = 0, ex = 0;
         for (const Shape& sh : shapes) {
             size_t a = 0, b = 0, c = 0;
@@ -655,7 +655,11 @@ Err Engine<T>::init_finish() {
             pt = std::max(pt, b);
             ex = std::max(ex, c);
         }
-        pt = std::max(pt, std::min<size_t>(36 * pt, (size_t)1 << 29));
+        {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                pt = std::min(pt, free_b / 4 / sizeof(float));
+        }
         THC_TRY(f64sl.alloc(sl));
         THC_TRY(f64part.alloc(pt));
         THC_TRY(f64exp.alloc(ex));

@@ -775,28 +775,29 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
 // along the row; in a batch-reduced product the row runs over all batches) is
 // scaled by 2^-e_r, e_r the binary exponent of its largest entry, so that its
 // entries lie in (-1, 1), and is cut into kSlices = 8 signed 7-bit integers:
-//   x = 2^e_r (sum_t a_t 2^(-7t) + r_x),   a_t in [-127, 127], |r_x| < 2^-56.
+//   x = 2^e_r (sum_t a_t 2^(-7t) + r_x),   a_t in [-127, 127], |r_x| < 2^-56,
+// read straight from the IEEE-754 fields (integer operations only).
 // A slice is exact in bf16, a product of two is an integer below 2^14, and a
 // float32 sum of at most 1024 of them is an integer below 2^24, so the tensor
-// cores' float32 accumulation over K chunks of 1024 is exact.  The 36 slice
-// pairs (t, u) with t + u <= 9 are added in float64 with their scales
-// 2^(e_r + e_c - 7 (t + u)).  The pairs left out (t + u = 10 and beyond) and
-// the remainders change each product term a_rk b_kc by less than about
-// 9 2^-56 = 1.2e-16 of 2^(e_r + e_c), the size of float64 rounding.
+// cores' float32 accumulation over K chunks of 1024 is exact.  The pairs
+// (t, u) with t + u = l are one product over concatenated slices,
+//   S_l = [a_1 .. a_(l-1)] [b_(l-1) .. b_1]^T   (K of (l - 1) Ktot),
+// which is why A keeps its slices in order and B in reverse order along each
+// row.  The levels l = 2 .. 9 (36 pairs) are combined in float64 by Horner's
+// rule, sum_l 2^(-7l) S_l, and scaled by 2^(e_r + e_c).  The pairs left out
+// (l >= 10) and the remainders change each product term a_rk b_kc by less
+// than about 9 2^-56 = 1.2e-16 of 2^(e_r + e_c), the size of float64 rounding.
 namespace {
 
 constexpr int kSlices = 8;
 constexpr int kChunkSteps = 16;            // 16 x 64 = 1024 K per exact partial sum
-constexpr int kExpZero = -1100;            // exponents below this mark all-zero rows
+constexpr int kLevels = kSlices;           // l = 2 .. kSlices + 1
 
-// Pairs (t, u), 1-based, t + u <= kSlices + 1: 36 of them.
-constexpr int kPairs = kSlices * (kSlices + 1) / 2;
-
-__device__ __forceinline__ int f64_exponent(double m) {
-    // m >= 0; the e with m < 2^e (e = floor(log2 m) + 1), from the IEEE-754 fields
-    const long long bits = __double_as_longlong(m);
-    const int f = (int)((bits >> 52) & 0x7ff);
-    return f == 0 ? -1022 : f - 1022;
+// Biased exponent field of |x| (0 for zero; subnormals count as field 1).
+__device__ __forceinline__ int f64_field(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    const int f = (int)(b >> 52);
+    return f == 0 ? (b != 0 ? 1 : 0) : f;
 }
 
 // Load a PK_R x PK_K tile of a strided float64 operand (zeros outside) the way
@@ -822,8 +823,8 @@ __device__ __forceinline__ void f64_tile(double (*tile)[PK_K + 1], const double*
     }
 }
 
-// expo[bo * Rp + r] = max over the row of the exponent of |x| (atomic over
-// the K tiles; the array starts at INT_MIN-like values).
+// expo[bo * Rp + r] = max over the row of the biased exponent field (atomic
+// over the K tiles; the array starts at zero = all-zero row).
 __global__ void __launch_bounds__(256) k_row_exp(const double* src, long long rs, long long ks,
                                                  long long bs, int R, int Kd, int Rp,
                                                  int reduce, int* expo) {
@@ -837,24 +838,37 @@ __global__ void __launch_bounds__(256) k_row_exp(const double* src, long long rs
         f64_tile(tile, s, rs, ks, R, Kd, r0, k0);
         __syncthreads();
         const int rr = t >> 3, oct = t & 7;
-        double m = 0.0;
+        int m = 0;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) m = fmax(m, fabs(tile[rr][oct * 8 + e]));
+        for (int e = 0; e < 8; ++e) m = max(m, f64_field(tile[rr][oct * 8 + e]));
         // the 8 threads of a row are consecutive lanes of one warp
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o, 8));
+        for (int o = 4; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o, 8));
         const int r = r0 + rr;
-        if (oct == 0 && r < R && m > 0.0) atomicMax(&expo[(long long)bo * Rp + r], f64_exponent(m));
+        if (oct == 0 && r < R && m > 0) atomicMax(&expo[(long long)bo * Rp + r], m);
         __syncthreads();
     }
 }
 
-// Slices of one operand: out[t][bo][r][kb * Kp + k] = a_{t+1}(x(b, r, k)) as
-// bf16 (zero in the padding), in the packed K-major layout of k_pack.
+// bf16 bits of a small integer (|a| <= 127), exact.
+__device__ __forceinline__ unsigned short small_int_bf16(int a) {
+    const unsigned sign = a < 0 ? 0x8000u : 0u;
+    const unsigned m = (unsigned)(a < 0 ? -a : a);
+    if (m == 0) return (unsigned short)sign;
+    const int p = 31 - __clz(m);                       // leading bit, 0 .. 6
+    const unsigned frac = (m << (7 - p)) & 0x7fu;      // 7 bits after it
+    return (unsigned short)(sign | ((unsigned)(p + 127) << 7) | frac);
+}
+
+// Slices of one operand: row (bo, r) holds kSlices segments of Ktot
+// elements, segment q = slice q + 1 (or slice kSlices - q with reverse), in
+// the packed K-major layout of k_pack (zero in the padding).  x = m 2^E with
+// the 53-bit significand m; |x| 2^(56 - e) = m 2^(E - e + 56) truncated to an
+// integer V < 2^56 gives the slices as its 7-bit digits.
 __global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs, long long ks,
                                                  long long bs, int R, int Kd, int nb, int Rp,
-                                                 int Kp, int reduce, const int* expo,
-                                                 long long slice_elems, __nv_bfloat16* out) {
+                                                 int Kp, int reduce, int reverse, const int* expo,
+                                                 __nv_bfloat16* out) {
     __shared__ double tile[PK_R][PK_K + 1];
     const int b = blockIdx.z;
     const int k0 = blockIdx.x * PK_K;
@@ -868,60 +882,119 @@ __global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs
         const int rr = t >> 3, oct = t & 7;
         const int r = r0 + rr, k = k0 + oct * 8;
         if (r < Rp && k < Kp) {
-            const int e = r < R ? expo[(long long)bo * Rp + r] : kExpZero - 1;
-            union { __nv_bfloat16 h[8]; uint4 u; } v[kSlices];
+            // row exponent e = field - 1022 (|x| < 2^e); 0 = all-zero row
+            const int fe = r < R ? expo[(long long)bo * Rp + r] : 0;
+            union { unsigned short h[8]; uint4 u; } v[kSlices];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                double x = e < kExpZero ? 0.0 : scalbn(tile[rr][oct * 8 + j], -e);
+                const unsigned long long bits =
+                    (unsigned long long)__double_as_longlong(tile[rr][oct * 8 + j]);
+                const int f = (int)((bits >> 52) & 0x7ff);
+                const unsigned long long mant =
+                    (bits & 0xfffffffffffffULL) | (f ? (1ULL << 52) : 0ULL);
+                // shift = E - e + 56 with E = max(f, 1) - 1075, e = fe - 1022
+                const int sh = (f ? f : 1) - fe + 3;
+                unsigned long long V = 0;
+                if (fe > 0 && mant != 0) {
+                    if (sh >= 0) V = mant << sh;          // sh <= 3: V < 2^56
+                    else if (sh > -64) V = mant >> (-sh);
+                }
+                const bool neg = (bits >> 63) != 0;
 #pragma unroll
                 for (int q = 0; q < kSlices; ++q) {
-                    x *= 128.0;
-                    const double a = trunc(x);
-                    x -= a;
-                    v[q].h[j] = __double2bfloat16(a);
+                    const int slice = reverse ? kSlices - 1 - q : q;      // 0-based digit
+                    const int dig = (int)((V >> (7 * (kSlices - 1 - slice))) & 0x7f);
+                    v[q].h[j] = small_int_bf16(neg ? -dig : dig);
                 }
             }
-            const long long o = ((long long)bo * Rp + r) * Ktot + (long long)kb * Kp + k;
+            const long long row = ((long long)bo * Rp + r) * kSlices;
 #pragma unroll
             for (int q = 0; q < kSlices; ++q)
-                *reinterpret_cast<uint4*>(out + q * slice_elems + o) = v[q].u;
+                *reinterpret_cast<uint4*>(out + (row + q) * Ktot + (long long)kb * Kp + k) =
+                    v[q].u;
         }
         __syncthreads();
     }
 }
 
-// C(b, i, j) = [beta C] + alpha 2^(eA + eB) sum_pairs 2^(-7 (t + u)) sum_s part,
-// for the pairs p0 .. p0 + np - 1 of this pass (first: the beta term).
-__global__ void k_f64_accumulate(const float* part, int np, int p0, int splits, int nbo, int M,
-                                 int N, const int* eA, int RpA, int a_bc, const int* eB, int RpB,
-                                 int b_bc, double* C, long long crs, long long ccs,
-                                 long long cbs, double alpha, double beta, int first) {
-    const long long MN = (long long)M * N, total = MN * nbo;
-    const long long per_pair = MN * nbo * splits;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(idx / MN);
-        const long long e = idx % MN;
-        const int i = (int)(e / N), j = (int)(e % N);
-        const int ea = eA[(long long)(a_bc ? 0 : b) * RpA + i];
-        const int eb = eB[(long long)(b_bc ? 0 : b) * RpB + j];
+// Split counts and partial offsets of the levels l = 2 .. 9.
+struct F64Levels {
+    int splits[kLevels];
+    long long off[kLevels];
+};
+
+__device__ __forceinline__ double pow2(int k) {
+    return (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(k + 1023) << 52)
+                                     : scalbn(1.0, k);
+}
+
+// C(b, u, w) = beta C + alpha 2^(e_r + e_c) sum_l 2^(-7l) S_l(b, u, w), S_l
+// the sum of the level's splits, in C's own orientation (u < M rows, w < N
+// contiguous columns of the product as called; the level outputs are written
+// the same way, so every access runs along w).  Levels 2-6 are combined
+// exactly in int64 (S_2 2^28 + ... + S_6, below 2^63 for up to 2048 splits of
+// integers below 2^24); levels 7-9, which sit 2^-35 and further below level
+// 2, in float32, whose rounding there is below 2^-57 of the product scale.
+// Grid: x over M N, y over the batches.
+__global__ void k_f64_accumulate(const float* part, F64Levels lv, int nbo, int M, int N,
+                                 int swap, const int* eA, int RpA, int a_bc, const int* eB,
+                                 int RpB, int b_bc, double* C, long long ldc, long long cbs,
+                                 double alpha, double beta) {
+    const int b = blockIdx.y;
+    const unsigned MN = (unsigned)M * (unsigned)N;
+    const long long pbs = (long long)MN * nbo;     // split stride of the level outputs
+    const int* ea = eA + (long long)(a_bc ? 0 : b) * RpA;
+    const int* eb = eB + (long long)(b_bc ? 0 : b) * RpB;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += gridDim.x * blockDim.x) {
+        const unsigned u = e / (unsigned)N, w = e - u * (unsigned)N;
+        // accumulator row i (A side) and column j (B side)
+        const int fa = swap ? ea[w] : ea[u];
+        const int fb = swap ? eb[u] : eb[w];
         double acc = 0.0;
-        if (ea >= kExpZero && eb >= kExpZero) {
-            int p = 0;
-            for (int t = 1; t <= kSlices; ++t)
-                for (int u = 1; t + u <= kSlices + 1; ++u, ++p) {
-                    if (p < p0 || p >= p0 + np) continue;
-                    const float* q = part + (long long)(p - p0) * per_pair + (long long)b * MN + e;
-                    double s = 0.0;
-                    for (int sp = 0; sp < splits; ++sp) s += (double)q[(long long)sp * nbo * MN];
-                    acc += scalbn(s, -7 * (t + u));
-                }
-            acc = scalbn(acc, ea + eb);
+        if (fa > 0 && fb > 0) {
+            const float* pb = part + (long long)b * MN + e;
+            long long H = 0;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {   // levels 2 .. 6
+                const float* p = pb + lv.off[q];
+                long long sl = 0;
+                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += __float2int_rn(p[sp * pbs]);
+                H = H * 128 + sl;
+            }
+            float T = 0.f;
+#pragma unroll
+            for (int q = kLevels - 1; q >= 5; --q) {   // levels 9 .. 7
+                const float* p = pb + lv.off[q];
+                float sl = 0.f;
+                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += p[sp * pbs];
+                T = fmaf(T, 0.0078125f, sl);
+            }
+            // level-6 units: H + 2^-7 T;  2^(-42) 2^(e_r + e_c), e = field - 1022
+            const double h = fma((double)T, 0.0078125, (double)H);
+            acc = h * pow2((fa - 1022) + (fb - 1022) - 42);
         }
-        double* c = C + (long long)b * cbs + (long long)i * crs + (long long)j * ccs;
-        const double prev = first ? (beta != 0.0 ? beta * *c : 0.0) : *c;
-        *c = prev + alpha * acc;
+        double* c = C + (long long)b * cbs + (long long)u * ldc + w;
+        *c = (beta != 0.0 ? beta * *c : 0.0) + alpha * acc;
     }
+}
+
+// 3-D map over bf16 rows of `pitch` elements of which the first kext are read.
+cudaError_t make_map_pitch(CUtensorMap* map, const __nv_bfloat16* base, long long kext,
+                           long long pitch, long long rows, int nbo, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)kext, (cuuint64_t)rows, (cuuint64_t)nbo};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * 2), (cuuint64_t)(pitch * 2 * rows)};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Exact-chunk splits of level l (K of (l - 1) Ktot).
+inline int level_splits(int l, long long Ktot) {
+    const long long steps = (l - 1) * Ktot / BK;
+    return (int)std::max<long long>(1, (steps + kChunkSteps - 1) / kChunkSteps);
 }
 
 }  // namespace
@@ -933,8 +1006,10 @@ void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slic
     const long long nbo = reduce ? 1 : batch;
     const long long Rm = rup(M, 128), Rn = rup(N, 128);
     *slice_elems = (size_t)(kSlices * (Rm + Rn) * Ktot * nbo);
-    const long long splits = std::max<long long>(1, (Ktot / BK + kChunkSteps - 1) / kChunkSteps);
-    *part_elems = (size_t)(splits * nbo * (long long)M * N);
+    // every level's float32 outputs (exact splits only)
+    long long sp = 0;
+    for (int l = 2; l <= kSlices + 1; ++l) sp += level_splits(l, Ktot);
+    *part_elems = (size_t)(sp * nbo * (long long)M * N);
     *expo_elems = (size_t)((Rm + Rn) * nbo);
 }
 
@@ -961,93 +1036,109 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     const bool a_bc = !g.reduce && nb > 1 && sa == 0;
     const bool b_bc = !g.reduce && nb > 1 && sb == 0;
     const int nba = a_bc ? 1 : nbo, nbb = b_bc ? 1 : nbo;
-    const long long sliceA = RpA * Ktot * nba, sliceB = RpB * Ktot * nbb;
-    if ((size_t)(kSlices * (sliceA + sliceB)) > ws.slice_elems) return cudaErrorMemoryAllocation;
+    const long long pitch = kSlices * Ktot;
+    const long long sliceA = RpA * pitch * nba, sliceB = RpB * pitch * nbb;
+    if ((size_t)(sliceA + sliceB) > ws.slice_elems) return cudaErrorMemoryAllocation;
     if ((size_t)(RpA * nba + RpB * nbb) > ws.expo_elems) return cudaErrorMemoryAllocation;
-    const int ksteps = (int)(Ktot / BK);
     const int mblocks = (int)(RpA / BM), nblocks = (int)(RpB / BN);
     const long long tiles = (long long)mblocks * nblocks * nbo;
-    // Splits: K chunks of at most 1024 (exact partial sums), more when the
-    // tiles alone do not fill the GPU.
-    const int exact = (ksteps + kChunkSteps - 1) / kChunkSteps;
-    int splits = exact;
-    if (tiles * splits < 152 && ksteps >= 8)
-        splits = std::max<int>(splits, (int)std::min<long long>({(152 + tiles - 1) / tiles,
-                                                                  ksteps / 4, 32}));
-    while (splits > exact && (size_t)splits * nbo * Mr * Nr > ws.part_elems) --splits;
-    const long long one = (long long)splits * nbo * Mr * Nr;   // float32 partials of one pair
-    if ((size_t)one > ws.part_elems) return cudaErrorMemoryAllocation;
-    const int group = (int)std::min<long long>(kPairs, (long long)ws.part_elems / one);
+    const long long MNb = (long long)Mr * Nr * nbo;
+    // Splits per level: exact K chunks, more when the tiles alone do not
+    // fill the GPU; every level's float32 outputs must fit the partial
+    // buffer together (one float64 pass).
+    F64Levels lv{};
+    long long used = 0;
+    for (int q = 0; q < kLevels; ++q) {
+        const int l = q + 2;
+        const int exact = level_splits(l, Ktot);
+        const int ksteps = (int)((l - 1) * Ktot / BK);
+        int sp = exact;
+        if (tiles * sp < 152 && ksteps >= 8)
+            sp = std::max<int>(sp, (int)std::min<long long>({(152 + tiles - 1) / tiles,
+                                                             ksteps / 4, 32}));
+        lv.splits[q] = sp;
+        lv.off[q] = used;
+        used += (long long)sp * MNb;
+    }
+    for (int q = kLevels - 1; q >= 0 && (size_t)used > ws.part_elems; --q) {
+        // drop the balancing splits, deepest levels first
+        const int exact = level_splits(q + 2, Ktot);
+        used -= (long long)(lv.splits[q] - exact) * MNb;
+        lv.splits[q] = exact;
+    }
+    if ((size_t)used > ws.part_elems || lv.splits[0] > 2048) return cudaErrorMemoryAllocation;
+    used = 0;
+    for (int q = 0; q < kLevels; ++q) {
+        lv.off[q] = used;
+        used += (long long)lv.splits[q] * MNb;
+    }
 
     __nv_bfloat16* slA = ws.slices;
-    __nv_bfloat16* slB = ws.slices + kSlices * sliceA;
+    __nv_bfloat16* slB = ws.slices + sliceA;
     int* eA = ws.expo;
     int* eB = ws.expo + RpA * nba;
     // Row exponents and slices of both operands.
     const int red = g.reduce ? 1 : 0;
-    if ((e = cudaMemsetAsync(ws.expo, 0x80, sizeof(int) * (RpA * nba + RpB * nbb), s)) !=
+    if ((e = cudaMemsetAsync(ws.expo, 0, sizeof(int) * (RpA * nba + RpB * nbb), s)) !=
         cudaSuccess)
         return e;
     struct Side { View<double> v; long long sbat; int R; long long Rp; int nbg; __nv_bfloat16* sl;
-                  long long selems; int* ex; };
-    const Side sides[2] = {{va, sa, Mr, RpA, a_bc ? 1 : nb, slA, sliceA, eA},
-                           {vb, sb, Nr, RpB, b_bc ? 1 : nb, slB, sliceB, eB}};
+                  int* ex; int rev; };
+    const Side sides[2] = {{va, sa, Mr, RpA, a_bc ? 1 : nb, slA, eA, 0},
+                           {vb, sb, Nr, RpB, b_bc ? 1 : nb, slB, eB, 1}};
     for (const Side& sd : sides) {
         const dim3 grid(cdiv(Kp, PK_K), std::min<unsigned>(cdiv(sd.Rp, PK_R), 65535), sd.nbg);
         k_row_exp<<<grid, 256, 0, s>>>(sd.v.p, sd.v.rs, sd.v.cs, sd.sbat, sd.R, g.K, (int)sd.Rp,
                                        red, sd.ex);
         k_slice64<<<grid, 256, 0, s>>>(sd.v.p, sd.v.rs, sd.v.cs, sd.sbat, sd.R, g.K, nb,
-                                       (int)sd.Rp, (int)Kp, red, sd.ex, sd.selems, sd.sl);
+                                       (int)sd.Rp, (int)Kp, red, sd.rev, sd.ex, sd.sl);
         count_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    // Slice maps (one per slice and operand).
-    CUtensorMap mA[kSlices], mB[kSlices];
-    for (int q = 0; q < kSlices; ++q) {
-        if ((e = make_map(&mA[q], slA + q * sliceA, Ktot, RpA, nba, BM)) != cudaSuccess) return e;
-        if ((e = make_map(&mB[q], slB + q * sliceB, Ktot, RpB, nbb, BN)) != cudaSuccess) return e;
     }
     TcArgs a{};
     a.M = Mr;
     a.N = Nr;
     a.nbo = nbo;
-    a.ksteps = ksteps;
     a.nprod = 1;
     a.a_bcast = a_bc ? 1 : 0;
     a.b_bcast = b_bc ? 1 : 0;
     a.err = ws.err;
     a.alpha = 1.f;
     a.beta = 0.f;
-    a.splits = splits;
     a.mblocks = mblocks;
     a.nblocks = nblocks;
-    a.ntiles = tiles * splits;
-    a.crs = Nr;
-    a.ccs = 1;
+    // Level outputs in the orientation of C (element (m, n) at m N + n).
+    a.crs = swap ? 1 : Nr;
+    a.ccs = swap ? Mr : 1;
     a.cbs = (long long)Mr * Nr;
-    const long long crs = swap ? 1 : g.ldc, ccs = swap ? g.ldc : 1;
-    const long long total = (long long)Mr * Nr * nbo;
-    const unsigned rblocks = (unsigned)std::min<long long>((total + 255) / 256, 152 * 16);
-    int p = 0, p0 = 0;
-    for (int t = 1; t <= kSlices; ++t)
-        for (int u = 1; t + u <= kSlices + 1; ++u, ++p) {
-            const CUtensorMap maps[4] = {mA[t - 1], mA[t - 1], mB[u - 1], mB[u - 1]};
-            a.C = ws.part + (long long)(p - p0) * one;
-            if (BN == 32) e = launch_tc<32>(maps, a, s);
-            else if (BN == 64) e = launch_tc<64>(maps, a, s);
-            else e = launch_tc<128>(maps, a, s);
-            if (e != cudaSuccess) return e;
-            if (p - p0 + 1 == group || p + 1 == kPairs) {
-                k_f64_accumulate<<<rblocks, 256, 0, s>>>(
-                    ws.part, p - p0 + 1, p0, splits, nbo, Mr, Nr, eA, (int)RpA, a_bc ? 1 : 0, eB,
-                    (int)RpB, b_bc ? 1 : 0, g.C, crs, ccs, g.reduce ? 0 : g.sCb, g.alpha, g.beta,
-                    p0 == 0 ? 1 : 0);
-                count_launches(1);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
-                p0 = p + 1;
-            }
-        }
-    return cudaSuccess;
+    for (int q = 0; q < kLevels; ++q) {
+        const int l = q + 2;
+        CUtensorMap maps[4];
+        const long long kext = (l - 1) * Ktot;
+        if ((e = make_map_pitch(&maps[0], slA, kext, pitch, RpA, nba, BM)) != cudaSuccess) return e;
+        if ((e = make_map_pitch(&maps[2], slB + (kSlices + 1 - l) * Ktot, kext, pitch, RpB, nbb,
+                                BN)) != cudaSuccess)
+            return e;
+        maps[1] = maps[0];
+        maps[3] = maps[2];
+        a.ksteps = (int)(kext / BK);
+        a.splits = lv.splits[q];
+        a.ntiles = tiles * lv.splits[q];
+        a.C = ws.part + lv.off[q];
+        if (BN == 32) e = launch_tc<32>(maps, a, s);
+        else if (BN == 64) e = launch_tc<64>(maps, a, s);
+        else e = launch_tc<128>(maps, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    const long long MN = (long long)Mr * Nr;
+    if (MN >= (1LL << 32) || nbo > 65535) return cudaErrorMemoryAllocation;
+    const dim3 rgrid((unsigned)std::min<long long>((MN + 255) / 256, 152 * 16 / nbo + 1),
+                     (unsigned)nbo);
+    k_f64_accumulate<<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
+                                           (int)RpA, a_bc ? 1 : 0, eB, (int)RpB, b_bc ? 1 : 0,
+                                           g.C, g.ldc, g.reduce ? 0 : g.sCb, g.alpha, g.beta);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -1231,7 +1322,7 @@ cudaError_t gemm_f64_tc_selftest(int cases, unsigned long long seed, double* max
     al((void**)&simt, cap * 8);
     ws.slice_elems = (size_t)1 << 26;
     al((void**)&ws.slices, ws.slice_elems * 2);
-    ws.part_elems = (size_t)1 << 24;
+    ws.part_elems = (size_t)1 << 28;   // the 8 levels of the largest case (about 1.4e8)
     al((void**)&ws.part, ws.part_elems * 4);
     ws.expo_elems = (size_t)1 << 16;
     al((void**)&ws.expo, ws.expo_elems * 4);

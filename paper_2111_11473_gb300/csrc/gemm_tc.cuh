@@ -91,8 +91,8 @@ struct F64TcWorkspace {
     size_t expo_elems = 0;
     int* err = nullptr;                // bounded-wait expiry flag
 };
-// Workspace needed by one product (part: one slice pair; more pairs per
-// float64 pass when there is room).
+// Workspace needed by one product (part: the float32 outputs of its 8
+// slice levels, combined in one float64 pass).
 void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slice_elems,
                        size_t* part_elems, size_t* expo_elems);
 cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s);
