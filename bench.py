@@ -503,7 +503,11 @@ def main():
         # Algs. 4-5 route: the dominant step is a group of batched products.
         ms_d, fl_d, n_d = prof[dom]
         achieved = fl_d / (ms_d * 1e-3) / 1e12
-        if fp64:
+        if args.precision == "fp64tc":
+            # 36 bf16 products per float64 multiply-add (8 slices a side)
+            peak = _peaks().get("bf16_tflops", 1931.0) / 36.0
+            bound, src = "tensor", "measured bf16 burst peak / 36 (slice products)"
+        elif fp64:
             peak, bound, src = FP64_ALU_TFLOPS, "alu", "derived: 152 SMs x 2 fp64 FMA lanes x 2 x 2.07 GHz"
         else:
             # bf16x3: three bf16 products per algorithmic multiply-add
