@@ -75,8 +75,8 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # G=1200, from one ncu capture of the current kernels (summaries in
 # profiles/residual_fp64_o40_v200_P400_G1200_K600_launches.md and
 # profiles/triangle_f32_o40_v200_P400_G1200_K600.md).  Other sizes: null.
-TRIANGLE_TRAFFIC_BYTES = {"fp64": 115.88e9 + 0.52e9, "fp64tc": 115.88e9 + 0.52e9,
-                          "mixed": 13.55e9 + 0.26e9}
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": 97.58e9 + 0.52e9,
+                          "mixed": 13.49e9 + 0.26e9}
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
