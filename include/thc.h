@@ -190,6 +190,19 @@ thc_status thc_energy(thc_ctx* ctx, const double* Zc, const double* t1,
  */
 thc_status thc_mp2_density(thc_ctx* ctx, const double* Zc, double* D_oo, double* D_vv);
 
+/*
+ * Checkpoint of a stopped solve (a plain Jacobi + DIIS thc_solve that ended
+ * at max_iter): thc_solve_state_size gives the bytes of the host blob,
+ * thc_solve_state_save writes it (next point, DIIS vectors and overlap
+ * matrix, iteration count), thc_solve_state_load puts it into a context of
+ * the same system (same sizes and working basis), after which thc_solve
+ * with resume = 1 continues it.  Errors: THC_ERR_ARG if there is no stopped
+ * solve, the buffer is too small, or the blob belongs to another system.
+ */
+thc_status thc_solve_state_size(thc_ctx* ctx, size_t* bytes);
+thc_status thc_solve_state_save(thc_ctx* ctx, void* buf, size_t bytes);
+thc_status thc_solve_state_load(thc_ctx* ctx, const void* buf, size_t bytes);
+
 /* Learned preconditioner network (see thc_mlp_create). */
 typedef struct thc_mlp thc_mlp;
 
@@ -207,6 +220,14 @@ typedef struct {
     int record_pairs;    /* > 0: record this many training pairs per
                             iteration (elements drawn with replacement) */
     unsigned long long record_seed;   /* seed of that draw */
+    int resume;          /* 1 = continue the last plain Jacobi + DIIS solve of
+                            this context where it stopped at max_iter (or the
+                            state given to thc_solve_state_load): its next
+                            point, DIIS history and iteration count; Zc_inout
+                            and t1_inout are then outputs only.  The result is
+                            bit-identical to one uninterrupted solve.
+                            THC_ERR_ARG with use_mlp or record_pairs, another
+                            diis_n, or no stopped solve. */
 } thc_solve_opts;
 
 typedef struct {

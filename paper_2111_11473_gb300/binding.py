@@ -32,7 +32,7 @@ class ThcSolveOpts(C.Structure):
     _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
                 ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int),
                 ("history", C.c_void_p), ("mlp", C.c_void_p), ("record_pairs", C.c_int),
-                ("record_seed", C.c_ulonglong)]
+                ("record_seed", C.c_ulonglong), ("resume", C.c_int)]
 
 
 class ThcReport(C.Structure):
@@ -83,6 +83,9 @@ _SIGNATURES = {
     "thc_energy": (C.c_int, [_VP, _DP, _DP, _DP]),
     "thc_mp2_density": (C.c_int, [_VP, _DP, _DP, _DP]),
     "thc_solve": (C.c_int, [_VP, C.POINTER(ThcSolveOpts), _DP, _DP, C.POINTER(ThcReport)]),
+    "thc_solve_state_size": (C.c_int, [_VP, C.POINTER(C.c_size_t)]),
+    "thc_solve_state_save": (C.c_int, [_VP, _VP, C.c_size_t]),
+    "thc_solve_state_load": (C.c_int, [_VP, _VP, C.c_size_t]),
     "thc_profile_enable": (C.c_int, [_VP, C.c_int]),
     "thc_profile_read": (C.c_int, [_VP, C.POINTER(ThcProfile)]),
     "thc_step_name": (C.c_char_p, [C.c_int]),
@@ -313,11 +316,13 @@ class Context:
 
     def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
               use_mlp=False, verbose=False, raise_on_failure=True, history=None, mlp=None,
-              record_pairs=0, record_seed=0):
+              record_pairs=0, record_seed=0, resume=False):
         """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero.
 
         If ``history`` is a list, (energy, |r|, seconds) per iteration is
-        appended to it."""
+        appended to it.  ``resume`` continues the stopped solve of this
+        context (or the state given to load_solve_state); Zc and t1 are then
+        outputs only."""
         if Zc is None:
             Zc = np.zeros((self.P, self.P))
         if t1 is None:
@@ -332,6 +337,7 @@ class Context:
         opts.history = hbuf.ctypes.data
         opts.mlp = mlp._h.value if mlp is not None else None
         opts.record_pairs, opts.record_seed = int(record_pairs), int(record_seed)
+        opts.resume = int(bool(resume))
         rep = ThcReport()
         st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
         if history is not None:
@@ -341,6 +347,19 @@ class Context:
         if st != 0 and raise_on_failure:
             self._check(st)
         return Zc, t1, report
+
+    def solve_state(self) -> bytes:
+        """Checkpoint of the stopped solve (thc_solve_state_save)."""
+        n = C.c_size_t(0)
+        self._check(self._lib.thc_solve_state_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self._lib.thc_solve_state_save(self._h, C.cast(buf, _VP), n))
+        return buf.raw
+
+    def load_solve_state(self, state: bytes):
+        """Make a checkpoint of the same system resumable here."""
+        buf = C.create_string_buffer(state, len(state))
+        self._check(self._lib.thc_solve_state_load(self._h, C.cast(buf, _VP), len(state)))
 
     def solve_pairs(self):
         """Training pairs (X, j, t) recorded by the last solve, as numpy float32."""

@@ -1,6 +1,8 @@
 // C ABI of the THC-RR-CCSD library (declared in include/thc.h).
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <memory>
 #include <new>
 #include <string>
@@ -51,6 +53,16 @@ thc::Err check_config(const thc_config* cfg) {
     return {};
 }
 
+// The solver of a context, set up on first use.
+thc::Err solver_of(thc_ctx* c) {
+    if (c->solver) return {};
+    c->solver.reset(new thc::Solver());
+    thc::Err e = c->e64 ? c->solver->setup(*c->e64, c->cfg.lsq_rel_cutoff)
+                        : c->solver->setup(*c->e32, c->cfg.lsq_rel_cutoff);
+    if (!e.ok()) c->solver.reset();
+    return e;
+}
+
 // Calls that evaluate anything need the Cholesky vectors in place.
 thc::Err ready(const thc_ctx* c) {
     const bool pend = c->e64 ? c->e64->pending : c->e32->pending;
@@ -64,6 +76,28 @@ thc::Err ready(const thc_ctx* c) {
 
 namespace thc {
 void set_thread_error(const std::string& msg) { g_init_error = msg; }
+
+namespace {
+std::atomic<long long> g_fail_alloc_left{0};
+std::atomic<bool> g_poison{false};
+}  // namespace
+
+void debug_arm_from_env() {
+    const char* f = std::getenv("THC_FAIL_ALLOC_AT");
+    g_fail_alloc_left = f ? std::max(0LL, std::atoll(f)) : 0LL;
+    const char* q = std::getenv("THC_POISON_WORKSPACE");
+    g_poison = q && q[0] && q[0] != '0';
+}
+
+bool debug_alloc_fails() {
+    long long left = g_fail_alloc_left.load();
+    while (left > 0) {
+        if (g_fail_alloc_left.compare_exchange_weak(left, left - 1)) return left == 1;
+    }
+    return false;
+}
+
+bool debug_poison() { return g_poison.load(); }
 }  // namespace thc
 
 extern "C" {
@@ -95,6 +129,7 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts) {
     opts->mlp = nullptr;
     opts->record_pairs = 0;
     opts->record_seed = 0;
+    opts->resume = 0;
     return THC_OK;
 }
 
@@ -104,6 +139,7 @@ thc_status thc_init(const thc_config* cfg, const double* eps_occ, const double* 
     g_init_error.clear();
     if (!out) { g_init_error = "out is NULL"; return THC_ERR_ARG; }
     *out = nullptr;
+    thc::debug_arm_from_env();
     thc::Err e = check_config(cfg);
     if (e.ok() && (!eps_occ || !eps_vir || !Y || !x || !z))
         e = {THC_ERR_ARG, "an input pointer is NULL"};
@@ -186,18 +222,41 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
     c->err.clear();
     if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!opts || !Zc_inout || !t1_inout) return fail(c, {THC_ERR_ARG, "NULL argument"});
-    if (!c->solver) {
-        c->solver.reset(new thc::Solver());
-        thc::Err e = c->e64 ? c->solver->setup(*c->e64, c->cfg.lsq_rel_cutoff)
-                            : c->solver->setup(*c->e32, c->cfg.lsq_rel_cutoff);
-        if (!e.ok()) { c->solver.reset(); return fail(c, e); }
-    }
+    if (thc::Err e = solver_of(c); !e.ok()) return fail(c, e);
     thc_report rep{};
     thc::Mlp* mlp = opts->mlp ? &opts->mlp->m : nullptr;
     if (mlp) mlp->st = c->st;
     thc::Err e = c->e64 ? c->solver->run(*c->e64, *opts, Zc_inout, t1_inout, &rep, mlp)
                         : c->solver->run(*c->e32, *opts, Zc_inout, t1_inout, &rep, mlp);
     if (report) *report = rep;
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+thc_status thc_solve_state_size(thc_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return THC_ERR_ARG;
+    c->err.clear();
+    if (!c->solver || !c->solver->resumable)
+        return fail(c, {THC_ERR_ARG, "no stopped plain solve in this context"});
+    *bytes = c->solver->state_bytes();
+    return THC_OK;
+}
+
+thc_status thc_solve_state_save(thc_ctx* c, void* buf, size_t bytes) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (!c->solver) return fail(c, {THC_ERR_ARG, "no stopped plain solve in this context"});
+    thc::Err e = c->solver->state_save(buf, bytes, c->st);
+    if (!e.ok()) return fail(c, e);
+    return THC_OK;
+}
+
+thc_status thc_solve_state_load(thc_ctx* c, const void* buf, size_t bytes) {
+    if (!c) return THC_ERR_ARG;
+    c->err.clear();
+    if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
+    if (thc::Err e = solver_of(c); !e.ok()) return fail(c, e);
+    thc::Err e = c->solver->state_load(buf, bytes, c->st);
     if (!e.ok()) return fail(c, e);
     return THC_OK;
 }

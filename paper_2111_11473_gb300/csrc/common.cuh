@@ -34,6 +34,16 @@ struct Err {
         if (!e_.ok()) return e_;                                               \
     } while (0)
 
+// Debugging hooks, armed at each thc_init from the environment:
+// THC_FAIL_ALLOC_AT=n makes the n-th device allocation of the library after
+// that point fail with THC_ERR_OOM (failure injection; counted across
+// threads); THC_POISON_WORKSPACE=1 fills every scratch buffer with NaN bytes
+// at the end of initialisation, so that a read of scratch the path has not
+// written shows up as a non-finite result.
+void debug_arm_from_env();
+bool debug_alloc_fails();
+bool debug_poison();
+
 // A strided view of a matrix: element (r, c) lives at p[r*rs + c*cs].
 template <typename T>
 struct View {

@@ -102,8 +102,12 @@ Err Engine<T>::check_finite(const double* a, long long count, const char* what) 
 
 template <typename T>
 void Engine<T>::seg_begin(int step) {
+    // NVTX range per step (visible to ncu's NVTX filters and other tools)
+    if (nvtx_open) nvtxRangePop();
+    nvtxRangePushA(thc_step_name(step));
+    nvtx_open = true;
     if (!prof.on) return;
-    if (prof.cur >= 0) seg_end();
+    if (prof.cur >= 0) prof_close();
     cudaEvent_t e = prof.next_event();
     cudaEventRecord(e, st);
     prof.marks.push_back({step, {prof.used - 1, -1}});
@@ -112,6 +116,15 @@ void Engine<T>::seg_begin(int step) {
 
 template <typename T>
 void Engine<T>::seg_end() {
+    if (nvtx_open) {
+        nvtxRangePop();
+        nvtx_open = false;
+    }
+    prof_close();
+}
+
+template <typename T>
+void Engine<T>::prof_close() {
     if (!prof.on || prof.cur < 0) return;
     cudaEvent_t e = prof.next_event();
     cudaEventRecord(e, st);
@@ -698,6 +711,28 @@ Err Engine<T>::init_finish() {
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
                 pcache.budget = std::min<size_t>(free_b / 2, 96ull << 30);
         }
+    }
+    if (debug_poison()) {
+        // NaN bytes in every scratch buffer (not the inputs, the fixed
+        // intermediates of init, or the flags that start at zero).
+        auto poison = [&](auto& b) -> Err {
+            if (b.p) THC_CUDA(cudaMemsetAsync(b.p, 0xff, b.n * sizeof(*b.p), st));
+            return Err{};
+        };
+        for (DBuf<T>* b : {&splitk, &Tc, &t1, &xoo, &xvv, &Ccross, &Abar, &Q, &Wq, &Joo, &Xoo,
+                           &Foo, &Jov, &Xov, &Fov, &Jvo, &Xvo, &Fvo, &E1, &Jvv, &Xvv, &Fvv, &ST,
+                           &E9, &V9, &O9, &M9, &FvoT, &Lh_oo, &Lh_vv, &Lh_vo, &dtr, &Wfo, &Wfv,
+                           &M1, &N1, &M2, &M3, &M4, &M5, &Bbar, &Btil, &C1, &D1, &E, &W, &TA,
+                           &Ta0, &D8, &Mo, &A6, &C6, &D6, &Ech, &Fch, &Gch, &H, &M6, &I6, &Q4,
+                           &S5, &C45, &M245, &D45, &M345, &F45, &M445, &G45, &M545, &I45, &R45,
+                           &W7, &R7, &S7, &C7, &D7, &Yv, &M7, &Yo, &N7, &E7, &P7, &G7, &sigT,
+                           &sig1T})
+            THC_TRY(poison(*b));
+        for (DBuf<double>* b : {&Tcd, &t1d, &sig, &sig1, &en, &red}) THC_TRY(poison(*b));
+        THC_TRY(poison(tcpack));
+        THC_TRY(poison(tcpart));
+        THC_TRY(poison(f64sl));
+        THC_TRY(poison(f64part));
     }
     THC_CUDA(cudaStreamSynchronize(st));
     pending = false;

@@ -3,7 +3,10 @@
 #pragma once
 
 #include <algorithm>
+#include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "gemm_tc.cuh"
@@ -19,7 +22,18 @@ struct DBuf {
     Err alloc(size_t count) {
         n = count;
         if (count == 0) return Err{};
-        THC_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        if (debug_alloc_fails()) {
+            n = 0;
+            return Err{THC_ERR_OOM, "device allocation failed (injected by THC_FAIL_ALLOC_AT)"};
+        }
+        const cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();   // a failed allocation must not surface at a later check
+            p = nullptr;
+            n = 0;
+            return Err{e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA,
+                       std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        }
         return Err{};
     }
     void release() {
@@ -77,9 +91,11 @@ struct Engine {
     cudaStream_t st = nullptr;
     size_t bytes = 0;
     Profiler prof;
+    bool nvtx_open = false;                 // an NVTX step range is open
     // Open / close a timed segment of step `step` (no-ops when profiling is off).
     void seg_begin(int step);
     void seg_end();
+    void prof_close();                      // close the open timed segment
     Err prof_collect();
 
     // Fixed data (storage type T unless noted).

@@ -332,28 +332,43 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     const auto t0 = std::chrono::steady_clock::now();
     const long long PP = (long long)P * P, ov = (long long)o * v, rr = (long long)r * r;
     const int m = std::max(0, std::min(opts.diis_n, 32));
-    if (m > 0 && hx.n < (size_t)m * len) {
-        THC_TRY(hx.alloc((size_t)m * len));
-        THC_TRY(he.alloc((size_t)m * len));
-    }
-    nhist = 0;
-    head = 0;
-    B.assign((size_t)std::max(m, 1) * std::max(m, 1), 0.0);
-    // Start point: t1 and T = (S C)^T Zc (S C).
-    THC_CUDA(cudaMemcpyAsync(x.p, t1_io, sizeof(double) * ov, cudaMemcpyDefault, st));
-    THC_CUDA(cudaMemcpyAsync(Zc.p, Zc_io, sizeof(double) * PP, cudaMemcpyDefault, st));
-    THC_TRY(eng.check_sym(Zc.p, P, 1e-12, "Zc"));
-    THC_TRY(mm(st, P, r, P, rm64(Zc.p, P), rm64(SC.p, r), tmp.p, r, 1, 0));
-    THC_TRY(mm(st, r, r, P, tr64(SC.p, r), rm64(tmp.p, r), x.p + ov, r, 1, 0));
-    k_symmetrize<<<nb(rr), 256, 0, st>>>(x.p + ov, r);
-    count_launches(1);
     double energy = 0, norm = 0, e_prev = 0;
     bool converged = false;
-    int it = 0;
+    int it = 0, it0 = 0;
     const int max_iter = opts.max_iter > 0 ? opts.max_iter : 100;
     // learned preconditioner and training-pair recording
     const bool use_mlp = opts.use_mlp && mlp;
     const long long nrec = std::max(0, opts.record_pairs);
+    double resume_last_norm = 0, resume_rho = 1;
+    if (opts.resume) {
+        // Continue where the last plain run stopped: x, the DIIS history and
+        // the iteration count are kept; Zc_io and t1_io are outputs only.
+        if (!resumable) return Err{THC_ERR_ARG, "thc_solve: no stopped solve to resume"};
+        if (use_mlp || nrec > 0)
+            return Err{THC_ERR_ARG, "thc_solve: resume is for plain Jacobi + DIIS solves"};
+        if (m != m_done) return Err{THC_ERR_ARG, "thc_solve: resume with a different diis_n"};
+        it0 = it_done;
+        e_prev = e_prev_done;
+        resume_last_norm = last_norm_done;
+        resume_rho = rho_done;
+    } else {
+        if (m > 0 && hx.n < (size_t)m * len) {
+            THC_TRY(hx.alloc((size_t)m * len));
+            THC_TRY(he.alloc((size_t)m * len));
+        }
+        nhist = 0;
+        head = 0;
+        B.assign((size_t)std::max(m, 1) * std::max(m, 1), 0.0);
+        // Start point: t1 and T = (S C)^T Zc (S C).
+        THC_CUDA(cudaMemcpyAsync(x.p, t1_io, sizeof(double) * ov, cudaMemcpyDefault, st));
+        THC_CUDA(cudaMemcpyAsync(Zc.p, Zc_io, sizeof(double) * PP, cudaMemcpyDefault, st));
+        THC_TRY(eng.check_sym(Zc.p, P, 1e-12, "Zc"));
+        THC_TRY(mm(st, P, r, P, rm64(Zc.p, P), rm64(SC.p, r), tmp.p, r, 1, 0));
+        THC_TRY(mm(st, r, r, P, tr64(SC.p, r), rm64(tmp.p, r), x.p + ov, r, 1, 0));
+        k_symmetrize<<<nb(rr), 256, 0, st>>>(x.p + ov, r);
+        count_launches(1);
+    }
+    resumable = false;
     if (use_mlp || nrec > 0) {
         if (xprev.n < (size_t)len) {
             THC_TRY(xprev.alloc(len));
@@ -381,7 +396,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     std::vector<long long> hidx(nrec);
     unsigned long long rng = 0x2545F4914F6CDD1DULL ^ (unsigned long long)opts.record_seed;
     bool have_prev = false, last_was_mlp = false, mlp_off = false;
-    double last_norm = 0, rho_plain = 1.0;
+    double last_norm = resume_last_norm, rho_plain = resume_rho;
     int saved_slot = -1, n_acc = 0, n_rej = 0;
     // DIIS history: store (x, e) in slot and refresh that row of B.
     auto diis_store = [&](int slot, const double* xv, const double* ev) -> Err {
@@ -419,7 +434,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         }
         return Err{};
     };
-    for (it = 1; it <= max_iter; ++it) {
+    for (it = it0 + 1; it <= it0 + max_iter; ++it) {
         // Zc = C T C^T
         THC_TRY(mm(st, P, r, r, rm64(C.p, r), rm64(x.p + ov, r), tmp.p, r, 1, 0));
         THC_TRY(mm(st, P, P, r, rm64(tmp.p, r), tr64(C.p, r), Zc.p, P, 1, 0));
@@ -447,9 +462,9 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             return Err{THC_ERR_NUMERIC, "solver diverged (non-finite residual)"};
         if (opts.history) {
             const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            opts.history[3 * (it - 1) + 0] = energy;
-            opts.history[3 * (it - 1) + 1] = norm;
-            opts.history[3 * (it - 1) + 2] = el;
+            opts.history[3 * (it - it0 - 1) + 0] = energy;
+            opts.history[3 * (it - it0 - 1) + 1] = norm;
+            opts.history[3 * (it - it0 - 1) + 2] = el;
         }
         if (opts.verbose)
             fprintf(stderr, "thc_solve it %3d  E = %.12f  |r| = %.3e\n", it, energy, norm);
@@ -576,7 +591,15 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     } else {
         n_rec = 0;
     }
-    rep->iters = converged ? it : max_iter;
+    if (!converged && !use_mlp && nrec == 0) {
+        resumable = true;
+        it_done = it0 + max_iter;
+        m_done = m;
+        e_prev_done = e_prev;
+        last_norm_done = last_norm;
+        rho_done = rho_plain;
+    }
+    rep->iters = converged ? it : it0 + max_iter;
     rep->mlp_accepted = n_acc;
     rep->mlp_rejected = n_rej;
     rep->energy = energy;
@@ -592,6 +615,78 @@ template Err Solver::run<double>(Engine<double>&, const thc_solve_opts&, double*
                                  thc_report*, Mlp*);
 template Err Solver::run<float>(Engine<float>&, const thc_solve_opts&, double*, double*,
                                 thc_report*, Mlp*);
+
+namespace {
+struct StateHeader {
+    unsigned long long magic;
+    int P, r, o, v, m, nhist, head, it_done;
+    double e_prev, last_norm, rho;
+    long long len;
+};
+constexpr unsigned long long kStateMagic = 0x54484353544154ULL;   // "THCSTAT"
+}  // namespace
+
+size_t Solver::state_bytes() const {
+    const size_t m = (size_t)m_done;
+    return sizeof(StateHeader) + sizeof(double) * ((size_t)len + 2 * m * len + m * m);
+}
+
+Err Solver::state_save(void* buf, size_t bytes, cudaStream_t st) const {
+    if (!resumable) return Err{THC_ERR_ARG, "no stopped plain solve to save"};
+    if (!buf || bytes < state_bytes()) return Err{THC_ERR_ARG, "state buffer too small"};
+    StateHeader h{kStateMagic, P, r, o, v, m_done, nhist, head, it_done, e_prev_done,
+                  last_norm_done, rho_done, len};
+    unsigned char* q = static_cast<unsigned char*>(buf);
+    std::memcpy(q, &h, sizeof(h));
+    double* d = reinterpret_cast<double*>(q + sizeof(h));
+    const size_t m = (size_t)m_done;
+    THC_CUDA(cudaMemcpyAsync(d, x.p, sizeof(double) * len, cudaMemcpyDeviceToHost, st));
+    if (m > 0) {
+        THC_CUDA(cudaMemcpyAsync(d + len, hx.p, sizeof(double) * m * len, cudaMemcpyDeviceToHost, st));
+        THC_CUDA(cudaMemcpyAsync(d + len + m * len, he.p, sizeof(double) * m * len,
+                                 cudaMemcpyDeviceToHost, st));
+    }
+    THC_CUDA(cudaStreamSynchronize(st));
+    if (m > 0) std::memcpy(d + len + 2 * m * len, B.data(), sizeof(double) * m * m);
+    return Err{};
+}
+
+Err Solver::state_load(const void* buf, size_t bytes, cudaStream_t st) {
+    if (!buf || bytes < sizeof(StateHeader)) return Err{THC_ERR_ARG, "state buffer too small"};
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic) return Err{THC_ERR_ARG, "not a solver state"};
+    if (h.P != P || h.r != r || h.o != o || h.v != v || h.len != len || h.m < 0 || h.m > 32 ||
+        h.nhist < 0 || h.nhist > h.m || h.head < 0 || (h.m > 0 && h.head >= h.m))
+        return Err{THC_ERR_ARG, "solver state of another system or basis"};
+    const size_t m = (size_t)h.m;
+    if (bytes < sizeof(StateHeader) + sizeof(double) * ((size_t)len + 2 * m * len + m * m))
+        return Err{THC_ERR_ARG, "state buffer too small"};
+    const double* d =
+        reinterpret_cast<const double*>(static_cast<const unsigned char*>(buf) + sizeof(h));
+    if (m > 0 && hx.n < m * len) {
+        THC_TRY(hx.alloc(m * len));
+        THC_TRY(he.alloc(m * len));
+    }
+    THC_CUDA(cudaMemcpyAsync(x.p, d, sizeof(double) * len, cudaMemcpyHostToDevice, st));
+    if (m > 0) {
+        THC_CUDA(cudaMemcpyAsync(hx.p, d + len, sizeof(double) * m * len, cudaMemcpyHostToDevice, st));
+        THC_CUDA(cudaMemcpyAsync(he.p, d + len + m * len, sizeof(double) * m * len,
+                                 cudaMemcpyHostToDevice, st));
+    }
+    THC_CUDA(cudaStreamSynchronize(st));
+    B.assign(std::max<size_t>(m, 1) * std::max<size_t>(m, 1), 0.0);
+    if (m > 0) std::memcpy(B.data(), d + len + 2 * m * len, sizeof(double) * m * m);
+    nhist = h.nhist;
+    head = h.head;
+    m_done = h.m;
+    it_done = h.it_done;
+    e_prev_done = h.e_prev;
+    last_norm_done = h.last_norm;
+    rho_done = h.rho;
+    resumable = true;
+    return Err{};
+}
 
 Err Solver::pairs(float* X, float* j, float* t, long long max_n, long long* n_out,
                   cudaStream_t st) {

@@ -28,6 +28,11 @@ struct Solver {
     DBuf<double> ws;                   // split-K workspace
     std::vector<double> B;             // DIIS overlap matrix (host)
     int nhist = 0, head = 0;
+    // Where the last plain Jacobi + DIIS run stopped (at max_iter): x holds
+    // the next point, hx/he/B/nhist/head the DIIS history.
+    bool resumable = false;
+    int it_done = 0, m_done = 0;
+    double e_prev_done = 0, last_norm_done = 0, rho_done = 1;
 
     // Learned-preconditioner state: previous iterate, saved point of the last
     // proposal, features and network outputs for all r^2 elements.
@@ -44,6 +49,10 @@ struct Solver {
     template <typename T>
     Err run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, double* t1_io,
             thc_report* rep, Mlp* mlp);
+    // Checkpoint of a resumable run as one host blob (see thc_solve_state_save).
+    size_t state_bytes() const;
+    Err state_save(void* buf, size_t bytes, cudaStream_t st) const;
+    Err state_load(const void* buf, size_t bytes, cudaStream_t st);
     // Copy out the pairs recorded by the last run (host or device pointers).
     Err pairs(float* X, float* j, float* t, long long max_n, long long* n_out,
               cudaStream_t st);

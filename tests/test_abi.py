@@ -34,7 +34,8 @@ def test_header_declares_the_abi():
                            "thc_profile_enable", "thc_profile_read",
                            "thc_residual", "thc_selftest_bounded_wait", "thc_selftest_gemm", "thc_selftest_gemm_f64",
                            "thc_solve",
-                           "thc_solve_opts_default", "thc_solve_pairs", "thc_step_name"]
+                           "thc_solve_opts_default", "thc_solve_pairs", "thc_solve_state_load",
+                           "thc_solve_state_save", "thc_solve_state_size", "thc_step_name"]
 
 
 def test_library_exports_every_declared_symbol(lib):
