@@ -928,6 +928,57 @@ __device__ __forceinline__ double pow2(int k) {
                                      : scalbn(1.0, k);
 }
 
+// One output of k_f64_accumulate; MAXS > 0: every level has at most MAXS
+// splits (the split loops unroll, so all loads can issue up front).
+template <int MAXS>
+__device__ __forceinline__ void f64_accumulate_one(const float* part, const F64Levels& lv,
+                                                   unsigned e, int b, unsigned MN, long long pbs,
+                                                   int N, int swap, const int* ea,
+                                                   const int* eb, double* C, long long ldc,
+                                                   long long cbs, double alpha, double beta) {
+    const unsigned u = e / (unsigned)N, w = e - u * (unsigned)N;
+    // accumulator row i (A side) and column j (B side)
+    const int fa = swap ? ea[w] : ea[u];
+    const int fb = swap ? eb[u] : eb[w];
+    double acc = 0.0;
+    if (fa > 0 && fb > 0) {
+        const float* pb = part + (long long)b * MN + e;
+        long long H = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {   // levels 2 .. 6
+            const float* p = pb + lv.off[q];
+            long long sl = 0;
+            if constexpr (MAXS > 0) {
+#pragma unroll
+                for (int sp = 0; sp < MAXS; ++sp)
+                    if (sp < lv.splits[q]) sl += __float2int_rn(p[sp * pbs]);
+            } else {
+                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += __float2int_rn(p[sp * pbs]);
+            }
+            H = H * 128 + sl;
+        }
+        float T = 0.f;
+#pragma unroll
+        for (int q = kLevels - 1; q >= 5; --q) {   // levels 9 .. 7
+            const float* p = pb + lv.off[q];
+            float sl = 0.f;
+            if constexpr (MAXS > 0) {
+#pragma unroll
+                for (int sp = 0; sp < MAXS; ++sp)
+                    if (sp < lv.splits[q]) sl += p[sp * pbs];
+            } else {
+                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += p[sp * pbs];
+            }
+            T = fmaf(T, 0.0078125f, sl);
+        }
+        // level-6 units: H + 2^-7 T;  2^(-42) 2^(e_r + e_c), e = field - 1022
+        const double h = fma((double)T, 0.0078125, (double)H);
+        acc = h * pow2((fa - 1022) + (fb - 1022) - 42);
+    }
+    double* c = C + (long long)b * cbs + (long long)u * ldc + w;
+    *c = (beta != 0.0 ? beta * *c : 0.0) + alpha * acc;
+}
+
 // C(b, u, w) = beta C + alpha 2^(e_r + e_c) sum_l 2^(-7l) S_l(b, u, w), S_l
 // the sum of the level's splits, in C's own orientation (u < M rows, w < N
 // contiguous columns of the product as called; the level outputs are written
@@ -935,46 +986,27 @@ __device__ __forceinline__ double pow2(int k) {
 // exactly in int64 (S_2 2^28 + ... + S_6, below 2^63 for up to 2048 splits of
 // integers below 2^24); levels 7-9, which sit 2^-35 and further below level
 // 2, in float32, whose rounding there is below 2^-57 of the product scale.
-// Grid: x over M N, y over the batches.
-__global__ void k_f64_accumulate(const float* part, F64Levels lv, int nbo, int M, int N,
-                                 int swap, const int* eA, int RpA, int a_bc, const int* eB,
-                                 int RpB, int b_bc, double* C, long long ldc, long long cbs,
-                                 double alpha, double beta) {
+// Grid: x over M N, y over the batches; every thread takes two outputs a
+// grid-width apart per step, whose loads are independent (memory-latency
+// bound: the pipes are far from busy).
+template <int MAXS>
+__global__ void __launch_bounds__(256, 4) k_f64_accumulate(
+    const float* part, F64Levels lv, int nbo, int M, int N, int swap, const int* eA, int RpA,
+    int a_bc, const int* eB, int RpB, int b_bc, double* C, long long ldc, long long cbs,
+    double alpha, double beta) {
     const int b = blockIdx.y;
     const unsigned MN = (unsigned)M * (unsigned)N;
     const long long pbs = (long long)MN * nbo;     // split stride of the level outputs
     const int* ea = eA + (long long)(a_bc ? 0 : b) * RpA;
     const int* eb = eB + (long long)(b_bc ? 0 : b) * RpB;
-    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += gridDim.x * blockDim.x) {
-        const unsigned u = e / (unsigned)N, w = e - u * (unsigned)N;
-        // accumulator row i (A side) and column j (B side)
-        const int fa = swap ? ea[w] : ea[u];
-        const int fb = swap ? eb[u] : eb[w];
-        double acc = 0.0;
-        if (fa > 0 && fb > 0) {
-            const float* pb = part + (long long)b * MN + e;
-            long long H = 0;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {   // levels 2 .. 6
-                const float* p = pb + lv.off[q];
-                long long sl = 0;
-                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += __float2int_rn(p[sp * pbs]);
-                H = H * 128 + sl;
-            }
-            float T = 0.f;
-#pragma unroll
-            for (int q = kLevels - 1; q >= 5; --q) {   // levels 9 .. 7
-                const float* p = pb + lv.off[q];
-                float sl = 0.f;
-                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += p[sp * pbs];
-                T = fmaf(T, 0.0078125f, sl);
-            }
-            // level-6 units: H + 2^-7 T;  2^(-42) 2^(e_r + e_c), e = field - 1022
-            const double h = fma((double)T, 0.0078125, (double)H);
-            acc = h * pow2((fa - 1022) + (fb - 1022) - 42);
-        }
-        double* c = C + (long long)b * cbs + (long long)u * ldc + w;
-        *c = (beta != 0.0 ? beta * *c : 0.0) + alpha * acc;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += 2 * stride) {
+        const unsigned e2 = e + stride;
+        f64_accumulate_one<MAXS>(part, lv, e, b, MN, pbs, N, swap, ea, eb, C, ldc, cbs, alpha,
+                                 beta);
+        if (e2 < MN)
+            f64_accumulate_one<MAXS>(part, lv, e2, b, MN, pbs, N, swap, ea, eb, C, ldc, cbs,
+                                     alpha, beta);
     }
 }
 
@@ -1134,9 +1166,18 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     if (MN >= (1LL << 32) || nbo > 65535) return cudaErrorMemoryAllocation;
     const dim3 rgrid((unsigned)std::min<long long>((MN + 255) / 256, 152 * 16 / nbo + 1),
                      (unsigned)nbo);
-    k_f64_accumulate<<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
-                                           (int)RpA, a_bc ? 1 : 0, eB, (int)RpB, b_bc ? 1 : 0,
-                                           g.C, g.ldc, g.reduce ? 0 : g.sCb, g.alpha, g.beta);
+    int maxs = 0;
+    for (int q = 0; q < kLevels; ++q) maxs = std::max(maxs, lv.splits[q]);
+    if (maxs <= 2)
+        k_f64_accumulate<2><<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
+                                                  (int)RpA, a_bc ? 1 : 0, eB, (int)RpB,
+                                                  b_bc ? 1 : 0, g.C, g.ldc,
+                                                  g.reduce ? 0 : g.sCb, g.alpha, g.beta);
+    else
+        k_f64_accumulate<0><<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
+                                                  (int)RpA, a_bc ? 1 : 0, eB, (int)RpB,
+                                                  b_bc ? 1 : 0, g.C, g.ldc,
+                                                  g.reduce ? 0 : g.sCb, g.alpha, g.beta);
     count_launches(1);
     return cudaGetLastError();
 }
