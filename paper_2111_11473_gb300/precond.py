@@ -66,7 +66,7 @@ def run_solve(ctx: Context, e_ref=None, mlp=None, r_tol=1e-6, max_iter=80, e_tol
 def compare(ctx: Context, mlp: Mlp, e_ref=None, r_tol=1e-6, max_iter=80, e_tol=1e-6):
     """Plain Jacobi + DIIS against the same solve with the network's proposals.
 
-    The plain solve is the judge: its converged energy is the reference when
+    The plain solve decides: its converged energy is the reference when
     e_ref is None, and ``energy_diff`` reports how far the learned solve's
     converged energy lies from it."""
     plain = run_solve(ctx, e_ref, None, r_tol, max_iter, e_tol)

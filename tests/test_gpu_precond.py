@@ -3,7 +3,7 @@
 The network is trained on the GPU on pairs that the solver records on four
 systems (o = 6..12, v = 5o, P = 10o, G = 30o, K = 15o), then the held-out
 systems (o = 8) are solved with and without its proposals in mixed
-precision to |r| < 1e-6.  Plain Jacobi + DIIS judges the converged energy.
+precision to |r| < 1e-6.  Plain Jacobi + DIIS gives the reference converged energy.
 
 On this family of systems the orbital-energy denominators are already close
 to the best pointwise step, so the gain is small or negative; the test
