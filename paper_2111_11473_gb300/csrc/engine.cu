@@ -529,10 +529,17 @@ Err Engine<T>::init_finish() {
             const long long nblk = (perX * P + budget6 - 1) / std::max<long long>(budget6, 1);
             x6 = (int)std::min<long long>(P, ((P + nblk - 1) / nblk + 31) / 32 * 32);
         }
-        // Grid points per chunk: the E and F chunks take at most 4 GB, and so
-        // does G's chunk when it is rebuilt.
+        // Grid points per chunk: the E and F chunks take at most 4 GB; a
+        // rebuilt G chunk takes a twelfth of the free memory, 4-12 GiB (more
+        // grid points per triangle launch: fewer read-modify-writes of H).
         long long icl = (4LL << 30) / (2LL * x6 * P * TB);
-        if (!gall_fits) icl = std::min<long long>(icl, (4LL << 30) / (PP * TB));
+        if (!gall_fits) {
+            long long gbudget = 4LL << 30;
+            if (cfg.workspace_bytes == 0 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                gbudget = std::max<long long>(gbudget, std::min<long long>(
+                                                           12LL << 30, (long long)(free_b / 12)));
+            icl = std::min<long long>(icl, gbudget / (PP * TB));
+        }
         ic = cfg.i_chunk > 0 ? std::min(cfg.i_chunk, G)
                              : (int)std::max<long long>(1, std::min<long long>(G, icl));
     }
