@@ -80,6 +80,7 @@ void set_thread_error(const std::string& msg) { g_init_error = msg; }
 namespace {
 std::atomic<long long> g_fail_alloc_left{0};
 std::atomic<bool> g_poison{false};
+std::atomic<bool> g_products{false};
 }  // namespace
 
 void debug_arm_from_env() {
@@ -87,6 +88,8 @@ void debug_arm_from_env() {
     g_fail_alloc_left = f ? std::max(0LL, std::atoll(f)) : 0LL;
     const char* q = std::getenv("THC_POISON_WORKSPACE");
     g_poison = q && q[0] && q[0] != '0';
+    const char* d = std::getenv("THC_DEBUG_PRODUCTS");
+    g_products = d && d[0] && d[0] != '0';
 }
 
 bool debug_alloc_fails() {
@@ -98,6 +101,7 @@ bool debug_alloc_fails() {
 }
 
 bool debug_poison() { return g_poison.load(); }
+bool debug_products() { return g_products.load(); }
 }  // namespace thc
 
 extern "C" {

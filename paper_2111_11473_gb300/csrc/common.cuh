@@ -39,10 +39,13 @@ struct Err {
 // that point fail with THC_ERR_OOM (failure injection; counted across
 // threads); THC_POISON_WORKSPACE=1 fills every scratch buffer with NaN bytes
 // at the end of initialisation, so that a read of scratch the path has not
-// written shows up as a non-finite result.
+// written shows up as a non-finite result; THC_DEBUG_PRODUCTS=1 reports on
+// stderr every product of at least 3e7 flops that runs on the CUDA cores
+// although a tensor-core path is enabled, with the reason.
 void debug_arm_from_env();
 bool debug_alloc_fails();
 bool debug_poison();
+bool debug_products();
 
 // A strided view of a matrix: element (r, c) lives at p[r*rs + c*cs].
 template <typename T>

@@ -168,6 +168,7 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     g.ws = splitk.p; g.ws_elems = splitk.n;
     const double fl = 2.0 * M * N * (double)Kd * batch;
     if (prof.on && prof.cur >= 0) prof.flops[prof.cur] += fl;
+    const char* why = nullptr;   // why a large product stays on the CUDA cores
     if constexpr (std::is_same<T, float>::value) {
         // Large products go to the tensor cores; the rest stays on the CUDA
         // cores (also if the packed operands do not fit the workspace).
@@ -175,6 +176,9 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
             cudaError_t e = gemm_tc(g, tcws, tc_products, st, &pcache);
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
+            why = "workspace";
+        } else if (tc_products > 0 && fl >= 3.0e7) {
+            why = "K < 16";
         }
     } else {
         // float64 products by exact integer slices on the tensor cores, when
@@ -188,8 +192,14 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
             cudaError_t e = gemm_f64_tc(g, f64ws, st);
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
+            why = "workspace";
+        } else if (f64tc && fl >= 3.0e7) {
+            why = Kd < 16 ? "K < 16" : "cost model";
         }
     }
+    if (why && debug_products())
+        fprintf(stderr, "thc: product M=%d N=%d K=%d batch=%d%s (%.3g flop) on the CUDA cores: %s\n",
+                M, N, Kd, batch, reduce ? " reduced" : "", fl, why);
     THC_CUDA(gemm_simt(g, st));
     return Err{};
 }

@@ -1,11 +1,13 @@
 // Strided, batched and batch-reducing matrix product on the CUDA cores.
 //
-// This is the float64 contraction engine of the library (tcgen05 has no
-// float64 kind) and the float32 reference path.  Every operand is a strided
+// This runs the float64 products of the CUDA-core policy, the products too
+// small for the tensor-core paths, and the float32 reference path.  Every
+// operand is a strided
 // view, so transposes, shared (stride-0) batch operands and column slices of
 // row-major arrays need no copies.  Tiles of 64 or 80 per side (chosen per
 // product to pad least) x 16, 256 threads, double-buffered shared memory.
 #include <algorithm>
+#include <type_traits>
 
 #include <atomic>
 
@@ -181,6 +183,45 @@ __global__ void gemm_splitk_reduce(const Gemm<T> g) {
 
 constexpr int kTargetBlocks = 2 * 152;
 
+// C(0, n) = alpha sum_k A(0, k) B(k, n) + beta C(0, n): a row vector times a
+// matrix, one thread per output column (a 64 x 64 tile would compute 64 rows
+// for the one that exists).
+template <typename T>
+__global__ void k_gemv_row(Gemm<T> g) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.N;
+         n += (long long)gridDim.x * blockDim.x) {
+        T acc = 0;
+        for (int k = 0; k < g.K; ++k)
+            acc += g.A.p[(long long)k * g.A.cs] * g.B.p[(long long)k * g.B.rs + n * g.B.cs];
+        T* c = g.C + n;
+        *c = g.beta != 0.0 ? (T)(g.alpha * acc + g.beta * *c) : (T)(g.alpha * acc);
+    }
+}
+
+// C(m, 0) = alpha sum_k A(m, k) B(k, 0) + beta C(m, 0): a matrix times a
+// vector, one 256-thread block per output row (the rows are few and long
+// here), fixed-order reduction.
+template <typename T>
+__global__ void k_gemv_col(Gemm<T> g) {
+    __shared__ T part[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long m = blockIdx.x; m < g.M; m += gridDim.x) {
+        T acc = 0;
+        for (int k = threadIdx.x; k < g.K; k += blockDim.x)
+            acc += g.A.p[m * g.A.rs + (long long)k * g.A.cs] * g.B.p[(long long)k * g.B.rs];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) part[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T sum = 0;
+            for (int w = 0; w < 8; ++w) sum += part[w];
+            T* c = g.C + m * g.ldc;
+            *c = g.beta != 0.0 ? (T)(g.alpha * sum + g.beta * *c) : (T)(g.alpha * sum);
+        }
+        __syncthreads();
+    }
+}
+
 // Tile edges (64 or 80 per side): the pair that pads the product least
 // (e.g. 400 = 5 x 80 instead of 7 x 64 = 448), among those that still give
 // two waves of blocks, directly or through split-K (ksteps 16-deep steps
@@ -214,15 +255,28 @@ cudaError_t launch(Gemm<T> g, cudaStream_t s) {
     if (g.K <= 0) {
         g.K = 0;   // C = beta C
     }
+    if (std::is_same<T, double>::value && g.batch == 1 && !g.reduce && g.K > 0 &&
+        (g.M == 1 || g.N == 1)) {
+        // float64 vector products (float32 tiles are cheap enough)
+        if (g.M == 1) {
+            k_gemv_row<T><<<(unsigned)std::min<long long>((g.N + 255) / 256, 152 * 8), 256, 0, s>>>(g);
+        } else {
+            k_gemv_col<T><<<(unsigned)std::min<long long>(g.M, 152 * 8), 256, 0, s>>>(g);
+        }
+        count_launches(1);
+        return cudaGetLastError();
+    }
     int BM = 64, BN = 64;
     tile_edges(g.M, g.N, g.reduce ? 1 : g.batch,
                (long long)(g.reduce ? g.batch : 1) * ((g.K + BK - 1) / BK), &BM, &BN);
     const long long tiles = (long long)cdiv(g.N, BN) * cdiv(g.M, BM) * (g.reduce ? 1 : g.batch);
     const long long ksteps = (long long)(g.reduce ? g.batch : 1) * ((g.K + BK - 1) / BK);
     int splits = 1;
-    if (g.ws && tiles < kTargetBlocks && ksteps >= 32) {
+    if (g.ws && tiles < kTargetBlocks && ksteps >= 8) {
+        // split K (chunks of at least 4 steps) when the tiles alone leave
+        // most SMs idle: a float64 tile runs at 4 G multiply-adds/s per SM
         long long want = (kTargetBlocks + tiles - 1) / tiles;
-        long long cap_k = ksteps / 16;
+        long long cap_k = ksteps / 4;
         long long per = (long long)g.M * g.N * (g.reduce ? 1 : g.batch);
         long long cap_ws = (long long)(g.ws_elems / (size_t)per);
         splits = (int)std::max(1LL, std::min({want, cap_k, cap_ws, 64LL}));
