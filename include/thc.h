@@ -27,6 +27,17 @@
  *     failure thc_last_error() describes the first error on that context.
  *   - A context belongs to one GPU and one stream and is not thread-safe;
  *     separate contexts are independent.
+ *
+ * Debugging environment variables, read at every thc_init:
+ *   THC_FAIL_ALLOC_AT=n     the n-th device allocation from then on fails
+ *                           with THC_ERR_OOM (failure injection);
+ *   THC_POISON_WORKSPACE=1  every scratch buffer is filled with NaN bytes at
+ *                           the end of initialisation, so a read of scratch
+ *                           that has not been written shows up as a
+ *                           non-finite result;
+ *   THC_DEBUG_PRODUCTS=1    every product of at least 3e7 flops that runs on
+ *                           the CUDA cores although a tensor-core path is
+ *                           enabled is reported on stderr with the reason.
  */
 #ifndef THC_H
 #define THC_H
