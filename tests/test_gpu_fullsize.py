@@ -17,15 +17,19 @@ from tests.gpu_util import context
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def o40_system():
+@pytest.fixture(scope="module", params=["fp64", "fp64tc"])
+def o40_system(request):
+    """The bench system in a float64 context: CUDA-core products, and the
+    tensor-core integer-slice products the benchmark runs by default."""
     import __graft_entry__ as g
     g.build()
+    import paper_2111_11473_gb300 as pkg
     o, v, P, G, K, seed = CONFIGS["o40_v200_P400_G1200_K600"]
     s = make_system(o, v, P, G, K, seed)
     from oracle import closed_shell as cs
     H = cs.Hamiltonian.from_inputs(s.eps_o, s.eps_v, s.L, s.x, s.z)
-    ctx = context(s)
+    prec = {"fp64": pkg.THC_PREC_FP64, "fp64tc": pkg.THC_PREC_FP64_TC}[request.param]
+    ctx = context(s, precision=prec)
     yield s, H, ctx
     ctx.close()
 
