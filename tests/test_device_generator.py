@@ -22,3 +22,20 @@ def test_device_generator_matches_host_generator(case):
     # float32 vectors: a few units of float32 rounding relative to the largest entry
     assert np.abs(L - s.L).max() < 2e-6 * np.abs(s.L).max()
     assert np.array_equal(L, L.transpose(0, 2, 1))
+
+
+def test_bench_generates_large_systems_in_slabs(monkeypatch):
+    """bench.py takes the slab-wise generator for systems whose float64
+    Cholesky array exceeds its host limit, and the host generator otherwise."""
+    pytest.importorskip("torch")
+    import bench
+    from synth import DeviceSystem, System
+    bench.set_workload("o5_v20_P60_G120_K60")
+    try:
+        assert isinstance(bench._system(device="cpu"), System)
+        monkeypatch.setattr(bench, "HOST_L_LIMIT", 1.0)
+        d = bench._system(device="cpu")
+        assert isinstance(d, DeviceSystem) and d.L is None
+        assert (d.o, d.v, d.P, d.G, d.K) == (5, 20, 60, 120, 60)
+    finally:
+        bench.set_workload(bench.DEFAULT_WORKLOAD)
