@@ -370,14 +370,25 @@ const char* thc_step_name(int step);
  *   energy  host or device scalar, output
  *   stream  cudaStream_t or NULL
  *
- * Needs o*P + P*P + P + o*o + K + 1 <= THC_NOALLOC_SCRATCH; larger sizes, and
- * inputs that are not device memory, return THC_ERR_ARG with the reason in
- * thc_last_error(NULL).  The first call
- * on a device looks up the scratch array's device address (with that device
- * current), so make it before any stream capture.  Every call on a device
- * shares the one array and leaves its contents behind: calls whose work
- * overlaps on the GPU (other streams, other threads) race, so serialise them.
- * Synchronous on `stream`.  Agrees with thc_energy to rounding.
+ * Needs o*P + P*P + P + o*o + 32*K + 1 <= THC_NOALLOC_SCRATCH; larger sizes,
+ * inputs that are not device memory, and inputs on a device other than the
+ * current one return THC_ERR_ARG with the reason in thc_last_error(NULL).
+ * `stream` must belong to the current device.
+ *
+ * First call per device.  CUDA loads a library's device code lazily (the
+ * default since CUDA 12.2), so the scratch array is committed on a device
+ * when the first call there loads this code, not when the library is
+ * loaded.  A caller whose memory pool will hold nearly all of HBM should
+ * therefore make one call (any valid size) before the pool reserves its
+ * memory, or run with CUDA_MODULE_LOADING=EAGER.  The first call also looks
+ * up the array's device address (with that device current), so make it
+ * before any stream capture.  Later calls allocate nothing.
+ *
+ * Every call on a device shares the one array and leaves its contents
+ * behind: calls whose work overlaps on the GPU (other streams, other
+ * threads) race, so serialise them.  Synchronous on `stream`.  Agrees with
+ * thc_energy to rounding.  Cost: five small launches per Cholesky vector,
+ * run one vector after another; meant for modest sizes.
  */
 #define THC_NOALLOC_SCRATCH (1 << 21)
 thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,

@@ -80,6 +80,14 @@ struct Gemm {
 long long launches();
 void count_launches(int n);
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (device, kernel); thread-safe.  cudaFuncSetAttribute acts
+// on the current device only, so a process that launches on several devices
+// needs the opt-in on each of them.
+cudaError_t smem_optin(const void* kernel, int bytes);
+// Number of SMs of the current device (cached per device).
+int device_sms();
+
 cudaError_t gemm_simt(const Gemm<double>& g, cudaStream_t s);
 cudaError_t gemm_simt(const Gemm<float>& g, cudaStream_t s);
 

@@ -10,6 +10,9 @@
 #include <type_traits>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "common.cuh"
 
@@ -20,6 +23,37 @@ std::atomic<long long> g_launches{0};
 }
 long long launches() { return g_launches.load(); }
 void count_launches(int n) { g_launches += n; }
+
+namespace {
+std::mutex g_optin_mu;
+std::map<std::pair<int, const void*>, int> g_optin;   // (device, kernel) -> bytes
+std::map<int, int> g_sms;                              // device -> SM count
+}  // namespace
+
+cudaError_t smem_optin(const void* kernel, int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_optin_mu);
+    auto it = g_optin.find({dev, kernel});
+    if (it != g_optin.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) g_optin[{dev, kernel}] = bytes;
+    return e;
+}
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    std::lock_guard<std::mutex> lock(g_optin_mu);
+    auto it = g_sms.find(dev);
+    if (it != g_sms.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        n = 152;
+    g_sms[dev] = n;
+    return n;
+}
 
 namespace {
 

@@ -516,29 +516,13 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, long long Ktot
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int g_sms = 0;
-std::once_flag g_sms_once;
-
 template <int BN>
 cudaError_t launch_tc(const CUtensorMap* maps, const TcArgs& a, cudaStream_t s) {
     const int smem = (int)sizeof(TcSmem<BN>) + 1024;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm_tc<BN, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    std::call_once(g_sms_once, [] {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            g_sms = 0;
-    });
-    const long long sms = g_sms > 0 ? g_sms : 152;
+    cudaError_t e = smem_optin((const void*)k_gemm_tc<BN, false>, smem);
+    if (e == cudaSuccess) e = smem_optin((const void*)k_gemm_tc<BN, true>, smem);
+    if (e != cudaSuccess) return e;
+    const long long sms = device_sms();
     const unsigned grid = (unsigned)std::min<long long>(a.ntiles, sms);
     if (a.splits == 1 && a.beta != 0.f)
         k_gemm_tc<BN, true><<<grid, kTcThreads, smem, s>>>(maps[0], maps[1], maps[2], maps[3], a);

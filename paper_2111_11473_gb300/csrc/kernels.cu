@@ -944,27 +944,17 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, in
             if (e == cudaSuccess) e = tri_map(&mF, F, nX, P, nI);
             if (e == cudaSuccess) e = tri_map(&mG, G, P, P, nI);
             if (e != cudaSuccess) return e;
-            static bool tma_attr = false;
             const int smem = (int)sizeof(TriTmaSmem) + 1024;
-            if (!tma_attr) {
-                e = cudaFuncSetAttribute(k_triangle_f32_tma,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-                if (e != cudaSuccess) return e;
-                tma_attr = true;
-            }
+            e = smem_optin((const void*)k_triangle_f32_tma, smem);
+            if (e != cudaSuccess) return e;
             dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(nX, TT));
             k_triangle_f32_tma<<<grid, 256, smem, s>>>(H, mE, mF, mG, P, nX, nI, tri_err);
             count_launches(1);
             return cudaGetLastError();
         }
-        static bool attr_set = false;
         const int smem = (int)(TSTAGES * sizeof(TriStage));
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(k_triangle_f32,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        cudaError_t e = smem_optin((const void*)k_triangle_f32, smem);
+        if (e != cudaSuccess) return e;
         dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(nX, TT));
         k_triangle_f32<<<grid, 512, smem, s>>>(H, E, F, G, P, nX, nI);
         count_launches(1);
@@ -974,13 +964,8 @@ cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, in
         const unsigned nb = cdiv(P, TYZ);
         dim3 grid(nb * (nb + 1) / 2, cdiv(nX, TXB));
         const int smem = (int)(2 * sizeof(TriSym64Stage));
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_triangle_sym64,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        cudaError_t e = smem_optin((const void*)k_triangle_sym64, smem);
+        if (e != cudaSuccess) return e;
         k_triangle_sym64<<<grid, 256, smem, s>>>(H, E, F, G, P, nX, nI);
         count_launches(1);
         return cudaGetLastError();

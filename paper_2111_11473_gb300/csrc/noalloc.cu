@@ -54,38 +54,48 @@ __device__ double nb_block_sum(double v) {
     return v;
 }
 
-// One Cholesky vector A:  part = 2 a^T Zc a - sum_XY Zc^XY B^XY B^YX
-//                                + 2 (L_A . t1)^2 - sum_ij M_ij M_ji
-// with M3 = L_A y_v (o x P), a^X = sum_i y_i^X M3[i][X], B = M3^T y_o,
-// M = L_A t1^T (o x o).
-__global__ void k_energy_vector(const double* yo, const double* M3, const double* B,
-                                const double* Mo, const double* LA, const double* t1,
-                                const double* Zc, int o, int v, int P, double* a,
-                                double* part) {
-    for (int X = threadIdx.x; X < P; X += blockDim.x) {
+// a^X = sum_i y_i^X M3[i][X] for one Cholesky vector (M3 = L_A y_v, o x P).
+__global__ void k_energy_avec(const double* yo, const double* M3, int o, int P, double* a) {
+    for (int X = blockIdx.x * blockDim.x + threadIdx.x; X < P; X += gridDim.x * blockDim.x) {
         double s = 0;
         for (int i = 0; i < o; ++i) s += yo[(long long)i * P + X] * M3[(long long)i * P + X];
         a[X] = s;
     }
-    __syncthreads();
+}
+
+// Partial sums of one Cholesky vector A's part of the energy,
+//   part = 2 a^T Zc a - sum_XY Zc^XY B^XY B^YX + 2 (L_A . t1)^2 - sum_ij M_ij M_ji,
+// with B = M3^T y_o and M = L_A t1^T (o x o).  Each of the kNoallocBlocks
+// blocks takes a strided share of the P^2 (and o v, o^2) elements and writes
+// one partial; the two singles pieces are formed by block 0 alone, since the
+// square of L_A . t1 needs the whole dot product.
+constexpr int kNoallocBlocks = 32;
+
+__global__ void k_energy_vector(const double* B, const double* Mo, const double* LA,
+                                const double* t1, const double* Zc, const double* a, int o,
+                                int v, int P, double* part) {
     const long long PP = (long long)P * P;
     double acc = 0;
-    for (long long e = threadIdx.x; e < PP; e += blockDim.x) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < PP;
+         e += (long long)gridDim.x * blockDim.x) {
         const int X = (int)(e / P), Y = (int)(e % P);
         acc += Zc[e] * (2.0 * a[X] * a[Y] - B[e] * B[(long long)Y * P + X]);
     }
-    double s1 = 0, q = 0;
-    for (int e = threadIdx.x; e < o * v; e += blockDim.x) s1 += LA[e] * t1[e];
-    for (int e = threadIdx.x; e < o * o; e += blockDim.x) {
-        const int i = e / o, j = e % o;
-        q += Mo[e] * Mo[j * o + i];
-    }
     acc = nb_block_sum(acc);
-    __syncthreads();
-    s1 = nb_block_sum(s1);
-    __syncthreads();
-    q = nb_block_sum(q);
-    if (threadIdx.x == 0) *part = acc + 2.0 * s1 * s1 - q;
+    if (blockIdx.x == 0) {
+        double s1 = 0, q = 0;
+        for (int e = threadIdx.x; e < o * v; e += blockDim.x) s1 += LA[e] * t1[e];
+        for (int e = threadIdx.x; e < o * o; e += blockDim.x) {
+            const int i = e / o, j = e % o;
+            q += Mo[e] * Mo[j * o + i];
+        }
+        __syncthreads();
+        s1 = nb_block_sum(s1);
+        __syncthreads();
+        q = nb_block_sum(q);
+        acc += 2.0 * s1 * s1 - q;
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 __global__ void k_sum_vector(const double* part, int n, double* out) {
@@ -109,6 +119,14 @@ extern "C" thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
         return THC_ERR_ARG;
     }
     // The kernels read the inputs in place: they must be device memory.
+    // They must also live on the current device, whose copy of the scratch
+    // array the kernels are given.
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        set_thread_error("thc_energy_noalloc: no current CUDA device");
+        return THC_ERR_CUDA;
+    }
     for (const double* p : {Y, Lov, Zc, t1}) {
         cudaPointerAttributes a{};
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeDevice) {
@@ -116,11 +134,18 @@ extern "C" thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
             set_thread_error("thc_energy_noalloc: Y, Lov, Zc and t1 must be device memory");
             return THC_ERR_ARG;
         }
+        if (a.device != cur) {
+            set_thread_error("thc_energy_noalloc: Y, Lov, Zc and t1 must be memory of the "
+                             "current device (" + std::to_string(cur) + "), not of device " +
+                             std::to_string(a.device));
+            return THC_ERR_ARG;
+        }
     }
-    // Scratch layout: M3 (o P) | B (P P) | a (P) | Mo (o o) | part (K) | result (1)
-    const long long need = (long long)o * P + (long long)P * P + P + (long long)o * o + K + 1;
+    // Scratch layout: M3 (o P) | B (P P) | a (P) | Mo (o o) | part (32 K) | result (1)
+    const long long need = (long long)o * P + (long long)P * P + P + (long long)o * o +
+                           (long long)kNoallocBlocks * K + 1;
     if (need > (long long)THC_NOALLOC_SCRATCH) {
-        set_thread_error("thc_energy_noalloc: o*P + P*P + P + o*o + K + 1 = " +
+        set_thread_error("thc_energy_noalloc: o*P + P*P + P + o*o + 32*K + 1 = " +
                          std::to_string(need) + " doubles exceeds the fixed scratch of " +
                          std::to_string((long long)THC_NOALLOC_SCRATCH) + " doubles");
         return THC_ERR_ARG;
@@ -138,13 +163,13 @@ extern "C" thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
     double* a = B + (long long)P * P;
     double* Mo = a + P;
     double* part = Mo + (long long)o * o;
-    double* result = part + K;
+    double* result = part + (long long)kNoallocBlocks * K;
     const double* yo = Y;
     const double* yv = Y + (long long)o * P;
     const long long ov = (long long)o * v;
     // Every region is overwritten before it is read; the partial sums are
     // cleared anyway so that a failed launch cannot leave stale values.
-    e = cudaMemsetAsync(part, 0, sizeof(double) * (K + 1), st);
+    e = cudaMemsetAsync(part, 0, sizeof(double) * ((long long)kNoallocBlocks * K + 1), st);
     for (int A = 0; A < K && e == cudaSuccess; ++A) {
         const double* LA = Lov + A * ov;
         Gemm<double> g;   // M3 = L_A y_v
@@ -162,12 +187,14 @@ extern "C" thc_status thc_energy_noalloc(int n_occ, int n_vir, int n_p, int n_k,
         m.C = Mo; m.ldc = o;
         e = gemm_simt(m, st);
         if (e != cudaSuccess) break;
-        k_energy_vector<<<1, 256, 0, st>>>(yo, M3, B, Mo, LA, t1, Zc, o, v, P, a, part + A);
-        count_launches(1);
+        k_energy_avec<<<(P + 255) / 256, 256, 0, st>>>(yo, M3, o, P, a);
+        k_energy_vector<<<kNoallocBlocks, 256, 0, st>>>(B, Mo, LA, t1, Zc, a, o, v, P,
+                                                        part + (long long)kNoallocBlocks * A);
+        count_launches(2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_sum_vector<<<1, 256, 0, st>>>(part, K, result);
+        k_sum_vector<<<1, 256, 0, st>>>(part, kNoallocBlocks * K, result);
         count_launches(1);
         e = cudaGetLastError();
     }

@@ -1,0 +1,106 @@
+"""Element-wise parity of the whole residual with the oracle at the benchmarked
+size o=40, v=200, P=400, G=1200, K=600 (seed 1), every term included: the
+ladders (Eq. 28, Alg. 1), the ring and bare terms (Eqs. 29-31), the T2^2
+terms through the triangle kernel (Eqs. 32-34, Alg. 6) and Alg. 7 (Eq. 35),
+the Fock and xi terms (Eq. 41), the singles (Eqs. 38, 42) and the energy.
+
+The oracle forms the 4-index amplitudes and integrals (vvvv alone is 12.8 GB)
+and takes about a minute per residual on the host cores, so the expected
+values are computed once per module:
+  * the bench state, made by the oracle itself: two Jacobi steps from zero in
+    the orthonormal working basis (Eq. 22), T -= sigma_q / (e_P + e_Q) and
+    t1 -= Omega1 / (eps_a - eps_i).  After the first step t1 = 0 (the
+    reference is Brillouin: F_ai = 0), after the second t1 != 0.  sigma is
+    small there (max |sigma| ~ 5e-5, a sum of terms of order 1e-3..1 that
+    nearly cancel), so float64 is also held to a bound relative to max|sigma|;
+  * a generic state, Zc and t1 drawn at amplitude scale 0.01.
+
+Float64 (CUDA-core products and tensor-core integer-slice products): max-abs
+1e-10 and 1e-11 of max|sigma|, energy 1e-9 Eh.  Mixed precision (float32,
+bf16x3 products): 1e-4 of max|sigma|, energy 1e-6 relative, the bounds of
+the small-size mixed tests.
+"""
+import numpy as np
+import pytest
+
+from synth import CONFIGS, make_system, random_amplitudes
+from tests.gpu_util import context
+
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-10
+REL_TOL_F64 = 1e-11
+E_TOL = 1e-9
+MIXED_REL = 1e-4
+
+
+def _sym(a):
+    return np.ascontiguousarray(0.5 * (a + a.T))
+
+
+@pytest.fixture(scope="module")
+def expected():
+    """System, states and the oracle's residual and energy at each state."""
+    from oracle import closed_shell as cs, solver as osolver, thc
+    o, v, P, G, K, seed = CONFIGS["o40_v200_P400_G1200_K600"]
+    s = make_system(o, v, P, G, K, seed)
+    H = cs.Hamiltonian.from_inputs(s.eps_o, s.eps_v, s.L, s.x, s.z)
+    C, e = thc.metric_basis(s.Y, s.eps_o, s.eps_v)
+    dq = e[:, None] + e[None, :]
+    d1 = s.eps_v[None, :] - s.eps_o[:, None]
+
+    def energy(Zc, t1):
+        return cs.energy(H, t1, thc.amplitudes(s.Y, Zc, o))
+
+    states = {}
+    # At (0, 0) the doubles residual is the bare (ai|bj) and Omega_i^a = F_ai.
+    D0 = cs.Dressed(H, np.zeros((o, v)))
+    sig0 = thc.project(s.Y, D0.g('vovo').transpose(1, 3, 0, 2), o)
+    r10 = D0.Fvo().T
+    T = -(C.T @ sig0 @ C) / dq
+    t1 = -r10 / d1
+    Z1 = _sym(C @ T @ C.T)
+    r1_1, sig_1 = osolver.projected_residual(H, s.Y, Z1, t1)
+    states["jacobi1"] = (Z1, t1.copy(), sig_1, r1_1, energy(Z1, t1))
+    T = T - (C.T @ sig_1 @ C) / dq
+    t1 = t1 - r1_1 / d1
+    Z2 = _sym(C @ T @ C.T)
+    r1_2, sig_2 = osolver.projected_residual(H, s.Y, Z2, t1)
+    states["jacobi2"] = (Z2, t1.copy(), sig_2, r1_2, energy(Z2, t1))
+    Zg, tg = random_amplitudes(P, o, v, 79, t2_scale=0.01, t1_scale=0.01)
+    r1_g, sig_g = osolver.projected_residual(H, s.Y, Zg, tg)
+    states["generic"] = (Zg, tg, sig_g, r1_g, energy(Zg, tg))
+    return s, states
+
+
+@pytest.fixture(scope="module", params=["fp64", "fp64tc", "mixed"])
+def ctx(request, expected):
+    import __graft_entry__ as g
+    g.build()
+    import paper_2111_11473_gb300 as pkg
+    s, _ = expected
+    prec = {"fp64": pkg.THC_PREC_FP64, "fp64tc": pkg.THC_PREC_FP64_TC,
+            "mixed": pkg.THC_PREC_MIXED}[request.param]
+    c = context(s, precision=prec)
+    yield request.param, c
+    c.close()
+
+
+@pytest.mark.parametrize("state", ["jacobi1", "jacobi2", "generic"])
+def test_fullsize_residual_matches_oracle(expected, ctx, state):
+    _, states = expected
+    name, c = ctx
+    Zc, t1, sig_ref, r1_ref, E_ref = states[state]
+    sig, sig1, E = c.residual(Zc, t1)
+    scale = max(np.abs(sig_ref).max(), np.abs(r1_ref).max())
+    d_sig = np.abs(sig - sig_ref).max()
+    d_r1 = np.abs(sig1 - r1_ref).max()
+    print(f"{name} {state}: max|sigma| {scale:.3e}, max|d sigma| {d_sig:.3e} "
+          f"({d_sig / scale:.2e} rel), max|d Omega1| {d_r1:.3e}, dE {E - E_ref:.3e}")
+    if name == "mixed":
+        assert max(d_sig, d_r1) < MIXED_REL * scale
+        assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))
+    else:
+        assert d_sig < RES_TOL and d_r1 < RES_TOL
+        assert max(d_sig, d_r1) < REL_TOL_F64 * scale
+        assert abs(E - E_ref) < E_TOL
