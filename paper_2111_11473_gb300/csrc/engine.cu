@@ -587,12 +587,24 @@ Err Engine<T>::init_finish() {
     }
     if (!t2sq_n5) {
         gall_resident = gall_fits;
+        tri_df = std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC;
         if (gall_resident) {
             THC_TRY(Gall.alloc((size_t)G * PP));
             THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0,
                        G, 0, P, PP));
+            if constexpr (std::is_same<T, double>::value) {
+                // The float64-accurate triangle reads G_I^YZ as float pairs.
+                if (tri_df)
+                    THC_CUDA(split_df(Gall.p, (long long)G * PP,
+                                      reinterpret_cast<float2*>(Gall.p), st));
+            }
         } else {
             THC_TRY(Gch.alloc((size_t)ic * PP));
+        }
+        if (tri_df) {
+            const size_t pairs = (size_t)ic * ((x6 + 1) / 2) * P;
+            THC_TRY(E4.alloc(pairs));
+            THC_TRY(F4.alloc(pairs));
         }
         const long long xP = (long long)x6 * P;
         THC_TRY(A6.alloc(ov * P));
@@ -750,6 +762,8 @@ Err Engine<T>::init_finish() {
         THC_TRY(poison(tcpart));
         THC_TRY(poison(f64sl));
         THC_TRY(poison(f64part));
+        THC_TRY(poison(E4));
+        THC_TRY(poison(F4));
     }
     THC_CUDA(cudaStreamSynchronize(st));
     pending = false;
@@ -823,14 +837,29 @@ Err Engine<T>::alg6(T* sgm) {
                            0, nI, 0, P, PP));
                 Gp = Gch.p;
             }
+            if constexpr (std::is_same<T, double>::value) {
+                if (tri_df) {
+                    // float pairs of E, F (and of a rebuilt G chunk, in place)
+                    THC_CUDA(split_df_pairs(Ech.p, nI, nX, P, E4.p, st));
+                    THC_CUDA(split_df_pairs(Fch.p, nI, nX, P, F4.p, st));
+                    if (!gall_resident)
+                        THC_CUDA(split_df(Gch.p, (long long)nI * PP,
+                                          reinterpret_cast<float2*>(Gch.p), st));
+                }
+            }
             // H^XYZ += (E^XY F^XZ + E^XZ F^XY) G^YZ   (line 11)
             seg_begin(THC_STEP_TRIANGLE);
-            // 5 flops per (I, X, Y, Z); the float64 kernel shares t between the
-            // mirror outputs (Y, Z) and (Z, Y): 7 flops per pair
-            if (prof.on)
-                prof.flops[THC_STEP_TRIANGLE] +=
-                    (std::is_same<T, double>::value ? 3.5 : 5.0) * nI * (double)nX * P * P;
-            THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+            // algorithmic count: 5 flops per (I, X, Y, Z)
+            if (prof.on) prof.flops[THC_STEP_TRIANGLE] += 5.0 * nI * (double)nX * P * P;
+            if constexpr (std::is_same<T, double>::value) {
+                if (tri_df)
+                    THC_CUDA(triangle_df(H.p, E4.p, F4.p, reinterpret_cast<const float2*>(Gp), P,
+                                         nX, nI, st));
+                else
+                    THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+            } else {
+                THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+            }
             seg_end();
         }
         seg_begin(THC_STEP_ALG6_POST);

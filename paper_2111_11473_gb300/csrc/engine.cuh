@@ -148,6 +148,11 @@ struct Engine {
 
     // Alg. 6 scratch (C6, D6, Ech, Fch, H, M6, I6 hold one block of x6 X's).
     DBuf<T> A6, C6, D6, Ech, Fch, Gch, H, M6, I6;
+    // Float64-accurate triangle on the FP32 pipe (float64 engine, tensor-core
+    // policy): E and F as float pairs with interleaved row pairs; G_I^YZ
+    // (Gall or Gch) is replaced in place by its float pairs.
+    bool tri_df = false;
+    DBuf<float4> E4, F4;
     // Alg. 7 scratch (C7, D7: P x G on the dense route, G x P transposed on
     // the blocked route).
     DBuf<T> R7, S7, C7, D7, Yv, M7, Yo, N7, E7, P7, G7;

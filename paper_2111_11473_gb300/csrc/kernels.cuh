@@ -84,6 +84,18 @@ template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, int nI,
                      cudaStream_t s, int* tri_err = nullptr);
 
+// Float64-accurate triangle on the FP32 pipe (float pairs, error-free
+// transformations; triangle_df.cu).  E4, F4: nI x ceil(nX/2) x P float4
+// {h(x), h(x+1), l(x), l(x+1)} of E^{xY} for the row pairs x = 2q, 2q + 1
+// (split_df_pairs); G2: nI x P x P float2 {h, l} (split_df); H: nX x P x P
+// float64, accumulated into.
+cudaError_t split_df_pairs(const double* E, int nI, int nX, int P, float4* out,
+                           cudaStream_t s);
+// out[i] = {fl32(in[i]), fl32(in[i] - fl32(in[i]))}; out may alias in.
+cudaError_t split_df(const double* in, long long n, float2* out, cudaStream_t s);
+cudaError_t triangle_df(double* H, const float4* E4, const float4* F4, const float2* G2, int P,
+                        int nX, int nI, cudaStream_t s);
+
 // Deterministic float64 sums.
 // out[0] = sum_i a[i] b[i]
 template <typename T>

@@ -1,0 +1,341 @@
+// Float64-accurate triangle kernel on the FP32 pipe (Alg. 6 line 11, Eq. 34):
+//   H^XYZ += sum_I (E_I^XY F_I^XZ + E_I^XZ F_I^XY) G_I^YZ.
+//
+// The step is not a product (every operand shares two of the three output
+// indices), so it cannot use the tensor cores, and GB300's FP64 pipe delivers
+// 1/64 of the FP32 rate.  Here every float64 operand is carried as an
+// unevaluated sum of two floats x = x_h + x_l (x_h = fl32(x), x_l = fl32(x -
+// x_h); 48 significant bits), and the arithmetic uses error-free
+// transformations:
+//   * TwoProduct with an FMA:  p = fl(a b),  e = fma(a, b, -p),  a b = p + e
+//     exactly (Karp and Markstein; Ogita, Rump and Oishi 2005, Alg. 3.3);
+//   * TwoSum (Knuth):  s = fl(a + b),  z = s - a,
+//     e = (a - (s - z)) + (b - z),  a + b = s + e exactly.
+// t^XYZ = E^XY F^XZ + E^XZ F^XY is formed as a float pair (th, tl) from two
+// exact products of the high parts, their exact sum, and the four cross
+// products of high and low parts; H accumulates t G as a float pair whose
+// high word is updated by TwoSum, the rounding errors and the low-order
+// product terms going to the low word.  Each term carries a relative error of
+// about 2^-46 of |E F G| (float64: 2^-53), far below the 1e-10 bound on the
+// residual.
+//
+// Like the float64 kernel, a block takes a pair of mirror (Y, Z) tiles, since
+// t is symmetric in (Y, Z): one t feeds H^XYZ (with G^YZ) and H^XZY (with
+// G^ZY).  Two amplitude indices X run in the two lanes of packed f32x2
+// instructions (add/sub/mul/fma.rn.f32x2), which halves the issued
+// instructions; E and F are stored with the two X rows of a pair interleaved
+// ({h(x), h(x+1), l(x), l(x+1)}), so that one 16-byte load gives both lanes.
+// Per (X pair, Y, Z) pair of mirror outputs: 19 packed operations for t and
+// 12 for each accumulation, i.e. 21.5 float32 operations per (I, X, Y, Z) term.
+#include "kernels.cuh"
+
+namespace thc {
+namespace {
+
+typedef unsigned long long f2;   // two float32 lanes: low word = lane 0
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// t = a b + c d for float pairs a = aH + aL etc.: (th, tl) with th + tl = t
+// up to the dropped low*low products and the roundings of the cross terms.
+__device__ __forceinline__ void df_dot2(f2 aH, f2 aL, f2 bH, f2 bL, f2 cH, f2 cL, f2 dH,
+                                        f2 dL, f2& th, f2& tl) {
+    const f2 zero = 0ull;
+    const f2 p1 = mul2(aH, bH);
+    const f2 e1 = fma2(aH, bH, sub2(zero, p1));   // aH bH - p1, exact
+    const f2 p2 = mul2(cH, dH);
+    const f2 e2 = fma2(cH, dH, sub2(zero, p2));
+    const f2 s = add2(p1, p2);                     // TwoSum(p1, p2)
+    const f2 z = sub2(s, p1);
+    const f2 es = add2(sub2(p1, sub2(s, z)), sub2(p2, z));
+    f2 lo = fma2(aH, bL, e1);
+    lo = fma2(aL, bH, lo);
+    lo = fma2(cH, dL, lo);
+    lo = fma2(cL, dH, lo);
+    lo = add2(lo, e2);
+    th = s;
+    tl = add2(lo, es);
+}
+
+// (Sh, Sl) -= t g, with thn = -th: the accumulator holds -H so that the
+// negated rounded product qn = fl(-th gH) feeds both TwoProduct and TwoSum.
+__device__ __forceinline__ void df_acc(f2& Sh, f2& Sl, f2 th, f2 tl, f2 thn, f2 gH, f2 gL) {
+    const f2 qn = mul2(thn, gH);       // -fl(th gH)
+    const f2 e = fma2(th, gH, qn);     // th gH - fl(th gH), exact
+    f2 low = fma2(th, gL, e);
+    low = fma2(tl, gH, low);           // t g - fl(th gH), to second order
+    const f2 s = add2(Sh, qn);         // TwoSum(Sh, qn)
+    const f2 z = sub2(s, Sh);
+    const f2 es = add2(sub2(Sh, sub2(s, z)), sub2(qn, z));
+    Sl = sub2(add2(Sl, es), low);
+    Sh = s;
+}
+
+constexpr int DX = 4;     // amplitude indices X per block (two lane pairs)
+constexpr int DT = 32;    // Y and Z tile
+constexpr int DS = 2;     // grid points per pipeline stage
+constexpr int DTH = 256;  // threads: 16 x 16, each a 2 x 2 (Y, Z) block
+
+struct DfStage {
+    float4 ey[DS][2][DT];         // E^{x,Y} of the Y tile, {h(x), h(x+1), l(x), l(x+1)}
+    float4 ez[DS][2][DT];         // E^{x,Z} of the Z tile
+    float4 fy[DS][2][DT];
+    float4 fz[DS][2][DT];
+    float2 g1[DS][DT][DT + 1];    // {h, l} of G^YZ, rows Y
+    float2 g2[DS][DT][DT + 1];    // {h, l} of G^ZY, rows Z
+};
+
+__device__ __forceinline__ void cpa16(void* dst, const void* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 16 : 0));
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(ok ? 8 : 0));
+}
+
+// Stage grid points I0 .. I0 + DS - 1 of the block's tiles (zeros outside).
+__device__ __forceinline__ void df_load(DfStage& st, const float4* E4, const float4* F4,
+                                        const float2* G2, int P, int nXp, int nI, int I0,
+                                        int xp0, int Y0, int Z0) {
+    const long long PP = (long long)P * P, XP = (long long)nXp * P;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < DS * DT * DT; e += DTH) {
+        const int s = e / (DT * DT), r = (e / DT) % DT, c = e % DT;
+        const int I = I0 + s;
+        const bool ok1 = I < nI && Y0 + r < P && Z0 + c < P;
+        const bool ok2 = I < nI && Z0 + r < P && Y0 + c < P;
+        cpa8(&st.g1[s][r][c], ok1 ? G2 + I * PP + (long long)(Y0 + r) * P + Z0 + c : G2, ok1);
+        cpa8(&st.g2[s][r][c], ok2 ? G2 + I * PP + (long long)(Z0 + r) * P + Y0 + c : G2, ok2);
+    }
+    for (int e = tid; e < DS * 2 * DT; e += DTH) {
+        const int s = e / (2 * DT), xp = (e / DT) % 2, c = e % DT;
+        const int I = I0 + s, q = xp0 + xp;
+        const bool okx = I < nI && q < nXp;
+        const long long base = I * XP + (long long)q * P;
+        const bool oy = okx && Y0 + c < P, oz = okx && Z0 + c < P;
+        cpa16(&st.ey[s][xp][c], oy ? E4 + base + Y0 + c : E4, oy);
+        cpa16(&st.ez[s][xp][c], oz ? E4 + base + Z0 + c : E4, oz);
+        cpa16(&st.fy[s][xp][c], oy ? F4 + base + Y0 + c : F4, oy);
+        cpa16(&st.fz[s][xp][c], oz ? F4 + base + Z0 + c : F4, oz);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Grid: x = block of DX rows X (fastest, so that the blocks running together
+// share the G tiles of one (Y, Z) pair in L2), y = pair of mirror tiles.
+__global__ void __launch_bounds__(DTH, 1)
+    k_triangle_df(double* H, const float4* E4, const float4* F4, const float2* G2, int P,
+                  int nX, int nI) {
+    extern __shared__ __align__(16) unsigned char df_raw[];
+    DfStage* stg = reinterpret_cast<DfStage*>(df_raw);
+    const int nb = (P + DT - 1) / DT;
+    int pidx = blockIdx.y, Yb = 0;
+    while (pidx >= nb - Yb) {
+        pidx -= nb - Yb;
+        ++Yb;
+    }
+    const int Zb = Yb + pidx;
+    const int Y0 = Yb * DT, Z0 = Zb * DT, X0 = blockIdx.x * DX;
+    const int nXp = (nX + 1) / 2, xp0 = X0 / 2;
+    const bool diag = Yb == Zb;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // Accumulators of -H for the mirror outputs: [x pair][i][j]
+    f2 h1[2][2][2], l1[2][2][2], h2[2][2][2], l2[2][2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) h1[a][i][j] = l1[a][i][j] = h2[a][i][j] = l2[a][i][j] = 0ull;
+    const int nsteps = (nI + DS - 1) / DS;
+    if (nsteps > 0) df_load(stg[0], E4, F4, G2, P, nXp, nI, 0, xp0, Y0, Z0);
+    for (int k = 0; k < nsteps; ++k) {
+        const DfStage& cur = stg[k & 1];
+        if (k + 1 < nsteps) {
+            df_load(stg[(k + 1) & 1], E4, F4, G2, P, nXp, nI, (k + 1) * DS, xp0, Y0, Z0);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int st = 0; st < DS; ++st) {
+            // G^(Y_i, Z_j) and G^(Z_j, Y_i), the same value in both lanes
+            f2 g1h[2][2], g1l[2][2], g2h[2][2], g2l[2][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float2 a = cur.g1[st][ty + 16 * i][tx + 16 * j];
+                    const float2 b = cur.g2[st][tx + 16 * j][ty + 16 * i];
+                    g1h[i][j] = pk(a.x, a.x);
+                    g1l[i][j] = pk(a.y, a.y);
+                    g2h[i][j] = pk(b.x, b.x);
+                    g2l[i][j] = pk(b.y, b.y);
+                }
+#pragma unroll
+            for (int xp = 0; xp < 2; ++xp) {
+                float4 ey[2], fy[2], ez[2], fz[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    ey[i] = cur.ey[st][xp][ty + 16 * i];
+                    fy[i] = cur.fy[st][xp][ty + 16 * i];
+                    ez[i] = cur.ez[st][xp][tx + 16 * i];
+                    fz[i] = cur.fz[st][xp][tx + 16 * i];
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        f2 th, tl;
+                        df_dot2(pk(ey[i].x, ey[i].y), pk(ey[i].z, ey[i].w),
+                                pk(fz[j].x, fz[j].y), pk(fz[j].z, fz[j].w),
+                                pk(ez[j].x, ez[j].y), pk(ez[j].z, ez[j].w),
+                                pk(fy[i].x, fy[i].y), pk(fy[i].z, fy[i].w), th, tl);
+                        const f2 thn = sub2(0ull, th);
+                        df_acc(h1[xp][i][j], l1[xp][i][j], th, tl, thn, g1h[i][j], g1l[i][j]);
+                        df_acc(h2[xp][i][j], l2[xp][i][j], th, tl, thn, g2h[i][j], g2l[i][j]);
+                    }
+            }
+        }
+        __syncthreads();   // the buffer is refilled two steps later
+    }
+    // On a diagonal pair both accumulators cover the same tile and count
+    // every (Y, Z) twice.
+    const double scale = diag ? -0.5 : -1.0;
+#pragma unroll
+    for (int xp = 0; xp < 2; ++xp)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int Y = Y0 + ty + 16 * i, Z = Z0 + tx + 16 * j;
+                if (Y >= P || Z >= P) continue;
+                float a0, a1, b0, b1;
+                upk(h1[xp][i][j], a0, a1);
+                upk(l1[xp][i][j], b0, b1);
+                const int x = X0 + 2 * xp;
+                if (x < nX) H[((long long)x * P + Y) * P + Z] += scale * ((double)a0 + (double)b0);
+                if (x + 1 < nX)
+                    H[((long long)(x + 1) * P + Y) * P + Z] += scale * ((double)a1 + (double)b1);
+            }
+    if (diag) __syncthreads();   // mirror targets overlap other threads' first targets
+#pragma unroll
+    for (int xp = 0; xp < 2; ++xp)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int Y = Y0 + ty + 16 * i, Z = Z0 + tx + 16 * j;
+                if (Y >= P || Z >= P) continue;
+                float a0, a1, b0, b1;
+                upk(h2[xp][i][j], a0, a1);
+                upk(l2[xp][i][j], b0, b1);
+                const int x = X0 + 2 * xp;
+                if (x < nX) H[((long long)x * P + Z) * P + Y] += scale * ((double)a0 + (double)b0);
+                if (x + 1 < nX)
+                    H[((long long)(x + 1) * P + Z) * P + Y] += scale * ((double)a1 + (double)b1);
+            }
+}
+
+__device__ __forceinline__ void split1(double d, float& h, float& l) {
+    h = __double2float_rn(d);
+    l = __double2float_rn(d - (double)h);   // d - h is exact in float64
+}
+
+__global__ void k_split_pairs(const double* E, int nI, int nX, int P, float4* out) {
+    const int nXp = (nX + 1) / 2;
+    const long long total = (long long)nI * nXp * P;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % P);
+        const long long r = idx / P;
+        const int q = (int)(r % nXp);
+        const long long I = r / nXp;
+        const int x = 2 * q;
+        const double d0 = E[(I * nX + x) * P + c];
+        const double d1 = x + 1 < nX ? E[(I * nX + x + 1) * P + c] : 0.0;
+        float h0, l0, h1, l1;
+        split1(d0, h0, l0);
+        split1(d1, h1, l1);
+        out[idx] = make_float4(h0, h1, l0, l1);
+    }
+}
+
+// in and out may be the same buffer: element i's float64 value is replaced
+// by its float pair in the same eight bytes.
+__global__ void k_split_df(const double* in, long long n, float2* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float h, l;
+        split1(in[i], h, l);
+        out[i] = make_float2(h, l);
+    }
+}
+
+unsigned grid_for(long long n) {
+    return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16));
+}
+
+}  // namespace
+
+cudaError_t split_df_pairs(const double* E, int nI, int nX, int P, float4* out,
+                           cudaStream_t s) {
+    const long long n = (long long)nI * ((nX + 1) / 2) * P;
+    if (n <= 0) return cudaSuccess;
+    k_split_pairs<<<grid_for(n), 256, 0, s>>>(E, nI, nX, P, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t split_df(const double* in, long long n, float2* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_split_df<<<grid_for(n), 256, 0, s>>>(in, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t triangle_df(double* H, const float4* E4, const float4* F4, const float2* G2, int P,
+                        int nX, int nI, cudaStream_t s) {
+    if (nX <= 0 || nI <= 0) return cudaSuccess;
+    const unsigned nb = cdiv(P, DT);
+    const int smem = (int)(2 * sizeof(DfStage));
+    cudaError_t e = smem_optin((const void*)k_triangle_df, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(cdiv(nX, DX), nb * (nb + 1) / 2);
+    k_triangle_df<<<grid, DTH, smem, s>>>(H, E4, F4, G2, P, nX, nI);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace thc

@@ -46,8 +46,10 @@ def test_residual_matches_oracle(case):
 
 
 @pytest.mark.parametrize("kw", [dict(alg7_route=1), dict(alg7_route=2), dict(x_block6=32),
+                                dict(x_block6=31, i_chunk=37),
                                 dict(k_slab=7, i_chunk=13, x_block=5), dict(t2sq_route=2)],
-                         ids=["alg7_blocked", "alg7_dense", "x6_32", "small_blocks", "algs45"])
+                         ids=["alg7_blocked", "alg7_dense", "x6_32", "x6_31_odd",
+                              "small_blocks", "algs45"])
 def test_routes_and_blocking_match_cuda_core_float64(kw):
     import paper_2111_11473_gb300 as pkg
     s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(8, 60, 120, 200, 80, 13)

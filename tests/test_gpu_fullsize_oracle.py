@@ -16,7 +16,9 @@ values are computed once per module:
   * a generic state, Zc and t1 drawn at amplitude scale 0.01.
 
 Float64 (CUDA-core products and tensor-core integer-slice products): max-abs
-1e-10 and 1e-11 of max|sigma|, energy 1e-9 Eh.  Mixed precision (float32,
+1e-10, sigma also within 1e-11 of max|sigma|, Omega1 within 1e-12 (the
+oracle's textbook Fock matrix adds Coulomb sums of o (pp|qq) ~ 12 Eh, whose
+float64 rounding alone is ~1e-14 there), energy 1e-9 Eh.  Mixed precision (float32,
 bf16x3 products): 1e-4 of max|sigma|, energy 1e-6 relative, the bounds of
 the small-size mixed tests.
 """
@@ -30,6 +32,7 @@ pytestmark = pytest.mark.gpu
 
 RES_TOL = 1e-10
 REL_TOL_F64 = 1e-11
+R1_TOL_F64 = 1e-12
 E_TOL = 1e-9
 MIXED_REL = 1e-4
 
@@ -102,5 +105,6 @@ def test_fullsize_residual_matches_oracle(expected, ctx, state):
         assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))
     else:
         assert d_sig < RES_TOL and d_r1 < RES_TOL
-        assert max(d_sig, d_r1) < REL_TOL_F64 * scale
+        assert d_sig < REL_TOL_F64 * np.abs(sig_ref).max()
+        assert d_r1 < R1_TOL_F64
         assert abs(E - E_ref) < E_TOL
