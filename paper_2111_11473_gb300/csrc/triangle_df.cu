@@ -15,14 +15,14 @@
 // exact products of the high parts, their exact sum, and the four cross
 // products of high and low parts; H accumulates t G as a float pair whose
 // high word is updated by TwoSum, the rounding errors and the low-order
-// product terms going to the low word.  Each term carries a relative error of
-// about 2^-46 of |E F G| (float64: 2^-53), far below the 1e-10 bound on the
-// residual.
+// product terms going to the low word.  Each term carries an error of about
+// 2^-45 of |E F G| (2^-43 at worst, from the roundings of the low words;
+// float64: 2^-53), far below the 1e-10 bound on the residual.
 //
 // Like the float64 kernel, a block takes a pair of mirror (Y, Z) tiles, since
 // t is symmetric in (Y, Z): one t feeds H^XYZ (with G^YZ) and H^XZY (with
 // G^ZY).  Two amplitude indices X run in the two lanes of packed f32x2
-// instructions (add/sub/mul/fma.rn.f32x2), which halves the issued
+// instructions (add/sub/fma.rn.f32x2), which halves the issued
 // instructions; E and F are stored with the two X rows of a pair interleaved
 // ({h(x), h(x+1), l(x), l(x+1)}), so that one 16-byte load gives both lanes.
 // Per (X pair, Y, Z) pair of mirror outputs: 19 packed operations for t and
@@ -52,25 +52,26 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     f2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+// The rounded product fl(a b), written as fma(a, b, +0).  ptxas contracts a
+// packed mul.rn.f32x2 whose result feeds an add.rn.f32x2 into one fused
+// operation, which would round a b + c once where TwoSum needs fl(a b)
+// itself (measured on GB300: every case where the two differ); an FMA with
+// a zero addend is left alone.
+__device__ __forceinline__ f2 prod2(f2 a, f2 b) { return fma2(a, b, 0ull); }
 
 // t = a b + c d for float pairs a = aH + aL etc.: (th, tl) with th + tl = t
 // up to the dropped low*low products and the roundings of the cross terms.
 __device__ __forceinline__ void df_dot2(f2 aH, f2 aL, f2 bH, f2 bL, f2 cH, f2 cL, f2 dH,
                                         f2 dL, f2& th, f2& tl) {
     const f2 zero = 0ull;
-    const f2 p1 = mul2(aH, bH);
+    const f2 p1 = prod2(aH, bH);
     const f2 e1 = fma2(aH, bH, sub2(zero, p1));   // aH bH - p1, exact
-    const f2 p2 = mul2(cH, dH);
+    const f2 p2 = prod2(cH, dH);
     const f2 e2 = fma2(cH, dH, sub2(zero, p2));
     const f2 s = add2(p1, p2);                     // TwoSum(p1, p2)
     const f2 z = sub2(s, p1);
@@ -87,7 +88,7 @@ __device__ __forceinline__ void df_dot2(f2 aH, f2 aL, f2 bH, f2 bL, f2 cH, f2 cL
 // (Sh, Sl) -= t g, with thn = -th: the accumulator holds -H so that the
 // negated rounded product qn = fl(-th gH) feeds both TwoProduct and TwoSum.
 __device__ __forceinline__ void df_acc(f2& Sh, f2& Sl, f2 th, f2 tl, f2 thn, f2 gH, f2 gL) {
-    const f2 qn = mul2(thn, gH);       // -fl(th gH)
+    const f2 qn = prod2(thn, gH);      // -fl(th gH)
     const f2 e = fma2(th, gH, qn);     // th gH - fl(th gH), exact
     f2 low = fma2(th, gL, e);
     low = fma2(tl, gH, low);           // t g - fl(th gH), to second order
