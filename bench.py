@@ -67,17 +67,59 @@ def _peaks():
 
 
 # Float64 and float32 CUDA-core peaks of one GB300 at the maximum SM clock:
-# 152 SMs x (FMA lanes per SM) x 2 flops x 2.07 GHz, with the lane counts
-# measured by an FMA-throughput probe (64-bit: 2 per SM per clock; 32-bit: 128).
+# 152 SMs x (FMA lanes per SM) x 2 flops x 2.07 GHz (64-bit: 2 lanes per SM,
+# 32-bit: 128); `bench.py --peaks` measures them with thc_probe_alu.
 FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# float32 operations issued per (I, X, Y, Z) term by each triangle kernel:
+# float64 kernel 3.5 float64 flops (t shared by the mirror outputs); float32
+# kernel 3 FMA-pipe operations; float-pair kernel 43 float32 operations per
+# pair of mirror outputs (19 for t, 12 per accumulation).
+TRI_ISSUED = {"fp64": 3.5, "mixed": 3.0, "fp64tc": 21.5}
 
 # DRAM bytes (read + write) of one triangle launch at o=40, v=200, P=400,
-# G=1200, from one ncu capture of the current kernels (summaries in
-# profiles/residual_fp64_o40_v200_P400_G1200_K600_launches.md and
-# profiles/triangle_f32_o40_v200_P400_G1200_K600.md).  Other sizes: null.
-TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": 97.58e9 + 0.52e9,
+# G=1200, from one ncu capture of the kernel that runs at that precision
+# (None: not captured since the kernel last changed).
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": None,
                           "mixed": 13.49e9 + 0.26e9}
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def triangle_roofline(precision, flops, ms, launches, share):
+    """Roofline of the triangle kernel from its per-step CUDA-event time.
+    flops: the algorithmic count, 5 per (I, X, Y, Z) term."""
+    achieved = (flops / launches) / (ms / launches * 1e-3) / 1e12     # TFLOP/s
+    terms_per_s = achieved * 1e12 / 5.0
+    if precision == "fp64":
+        pipe = FP64_ALU_TFLOPS * 1e12 / 2.0        # float64 FMA-lane operations / s
+        issued = terms_per_s * TRI_ISSUED["fp64"] / 2.0
+        unit_peak, src = FP64_ALU_TFLOPS, "derived: 152 SMs x 2 fp64 FMA lanes x 2 x 2.07 GHz"
+    else:
+        pipe = FP32_ALU_TFLOPS * 1e12 / 2.0        # float32 lane operations / s
+        issued = terms_per_s * TRI_ISSUED[precision]
+        unit_peak, src = FP32_ALU_TFLOPS, "derived: 152 SMs x 128 fp32 lanes x 2 x 2.07 GHz"
+    peak = pipe / TRI_ISSUED[precision] * 5.0 / 1e12 if precision != "fp64" else unit_peak
+    out = {"kernel": {"fp64": "k_triangle_sym64", "mixed": "k_triangle_f32_tma",
+                      "fp64tc": "k_triangle_df"}[precision] + " (Alg. 6 line 11)",
+           "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
+           "achieved_counts": "algorithmic flops, 5 per (I, X, Y, Z) term",
+           "frac_issued": issued / pipe,
+           "frac_issued_counts": "operations the kernel issues per term (%g) / pipe rate"
+                                 % TRI_ISSUED[precision],
+           "frac_algorithmic": achieved / unit_peak,
+           "frac_algorithmic_peak": unit_peak,
+           "traffic": TRIANGLE_TRAFFIC_BYTES[precision] if WORKLOAD_NAME.startswith(
+               "THC-RR-CCSD o=40 v=200 P=400 G=1200") else None,
+           "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+           "share_of_step": share}
+    if precision == "fp64tc":
+        # float64 result from float32 pairs: the bound is the FP32 pipe at
+        # 21.5 operations per term
+        out.update({"peak": peak, "frac": achieved / peak,
+                    "peak_source": src + "; / 21.5 float32 operations per term x 5 flops",
+                    "frac_of_fp64_alu_peak": achieved / FP64_ALU_TFLOPS})
+    else:
+        out.update({"peak": unit_peak, "frac": achieved / unit_peak, "peak_source": src})
+    return out
 
 
 class ClockSampler:
@@ -250,6 +292,36 @@ def run_reference(args):
     return 0
 
 
+def run_peaks():
+    """Roofline denominators and product rates measured through the library:
+    float64 / float32 / packed-pair FMA throughput, and one 4096^3 product
+    per tensor-core mode (CUDA events, milliseconds per product)."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2111_11473_gb300 import binding as b
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = {"fp64_fma_tflops": b.probe_alu(0, stream), "fp32_fma_tflops": b.probe_alu(1, stream),
+           "fp32x2_fma_tflops": b.probe_alu(2, stream),
+           "derived": {"fp64_alu_tflops": FP64_ALU_TFLOPS, "fp32_alu_tflops": FP32_ALU_TFLOPS}}
+    n = 4096
+    bf16 = _peaks().get("bf16_tflops")
+    gemm = {}
+    for mode, name, nprod in ((0, "bf16x3", 3), (1, "bf16x3_with_pack", 3), (2, "bf16x1", 1),
+                              (3, "float64_slices", 36)):
+        ms = b.probe_gemm(mode, n, n, n, 10 if mode < 3 else 3, stream)
+        alg = 2.0 * n ** 3 / (ms * 1e-3) / 1e12
+        gemm[name] = {"ms": ms, "algorithmic_tflops": alg, "bf16_product_tflops": alg * nprod,
+                      "frac_of_measured_bf16": (alg * nprod / bf16) if bf16 else None}
+    out["gemm_4096"] = gemm
+    out["clocks"] = sampler.stop()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _rate(ctx, Zc, t1, sig, sig1, stream, dev, steps=5, warmup=3):
     """Residual evaluations per second (CUDA events on the library's stream)."""
     import torch
@@ -385,10 +457,15 @@ def main():
     ap.add_argument("--fp64-iters", type=int, default=0,
                     help="also run this many float64 and mixed iterations from zero "
                          "and report their energy difference per iteration")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the CUDA-core FMA rates and time 4096^3 tensor-core "
+                         "products (thc_probe_alu, thc_probe_gemm), print one JSON line")
     args = ap.parse_args()
     set_workload(args.workload)
     if args.impl == "reference":
         return run_reference(args)
+    if args.peaks:
+        return run_peaks()
 
     import numpy as np
     import torch
@@ -488,17 +565,7 @@ def main():
     total_ms = max(1e-9, sum(v["ms_per_residual"] for v in steps.values()) *
                    max(1, prof["residuals"]))
     if tri_n > 0:
-        peak_tri = FP64_ALU_TFLOPS if fp64 else FP32_ALU_TFLOPS
-        achieved = (tri_fl / tri_n) / (tri_ms / tri_n * 1e-3) / 1e12
-        roofline = {"kernel": "triangle (Alg. 6 line 11)", "bound": "alu",
-                    "achieved": achieved, "peak": peak_tri, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tri,
-                    "traffic": (TRIANGLE_TRAFFIC_BYTES[args.precision]
-                                if args.workload == DEFAULT_WORKLOAD else None),
-                    "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
-                    "peak_source": ("derived: 152 SMs x %s FMA lanes x 2 x 2.07 GHz"
-                                    % ("2 fp64" if fp64 else "128 fp32")),
-                    "share_of_step": tri_ms / total_ms}
+        roofline = triangle_roofline(args.precision, tri_fl, tri_ms, tri_n, tri_ms / total_ms)
     else:
         # Algs. 4-5 route: the dominant step is a group of batched products.
         ms_d, fl_d, n_d = prof[dom]

@@ -69,8 +69,51 @@ typedef enum {
  * but every product of at least 3e7 flops runs on the tensor cores as exact
  * integer products of 8 slices of 7 bits per operand row (scaled by a power
  * of two per row), combined in float64: each product term is within about
- * 1.2e-16 of its row and column scale, float64 rounding level. */
+ * 1.2e-16 of its row and column scale, float64 rounding level; the triangle
+ * (Alg. 6 line 11) runs in float pairs on the FP32 pipe, each term within
+ * about 2^-45 of |E F G|.  Per-step choices: thc_config.policy. */
 typedef enum { THC_PREC_FP64 = 0, THC_PREC_MIXED = 1, THC_PREC_FP64_TC = 2 } thc_precision;
+
+/* Steps of one residual evaluation (per-step policy, timing and flop counts). */
+enum {
+    THC_STEP_DRESS = 0,      /* T1 dressing of the Cholesky vectors (Eqs. 25-27) */
+    THC_STEP_FOCK = 1,       /* Coulomb/exchange parts of the dressed Fock matrix */
+    THC_STEP_ALG1 = 2,       /* ladders, Alg. 1 (+ Alg. 3 intermediate) */
+    THC_STEP_ALG2_8 = 3,     /* Alg. 2 and Alg. 8 per Cholesky vector */
+    THC_STEP_POST = 4,       /* Alg. 2/3 closing products, Algs. 9 and 10 */
+    THC_STEP_ALG6_GEMM = 5,  /* Alg. 6 lines 1-10 (contractions) */
+    THC_STEP_TRIANGLE = 6,   /* Alg. 6 line 11 (triangle kernel) */
+    THC_STEP_ALG6_POST = 7,  /* Alg. 6 lines 13-16 */
+    THC_STEP_ALG7 = 8,       /* Alg. 7 */
+    THC_STEP_ENERGY = 9,     /* energy */
+    THC_N_STEPS = 10
+};
+
+/* Arithmetic of one step (thc_config.policy[step]); 0 = the context's
+ * precision policy.  Float64 contexts (THC_PREC_FP64, THC_PREC_FP64_TC):
+ *   THC_POL_FP64     float64 products and triangle on the CUDA cores
+ *   THC_POL_FP64_TC  products of at least 3e7 flops as exact integer slices
+ *                    on the tensor cores (float64 accuracy); the triangle
+ *                    (Alg. 6 line 11, THC_STEP_TRIANGLE) in float pairs with
+ *                    error-free transformations on the FP32 pipe, about
+ *                    2^-45 of |E F G| per term
+ * Mixed contexts (THC_PREC_MIXED, float32 storage):
+ *   THC_POL_BF16X3   products as bf16 hi*hi + hi*lo + lo*hi on the tensor
+ *                    cores, float32 accumulation
+ *   THC_POL_BF16     bf16 hi*hi only (about 2^-8 per factor)
+ *   THC_POL_FP32     float32 products on the CUDA cores
+ * The triangle of a mixed context is the float32 kernel (DEFAULT or FP32
+ * only).  A value outside the context's family is THC_ERR_ARG.  Products
+ * outside the residual's steps (initialisation, thc_mp2_density) follow the
+ * context's policy. */
+enum {
+    THC_POL_DEFAULT = 0,
+    THC_POL_FP64 = 1,
+    THC_POL_FP64_TC = 2,
+    THC_POL_BF16X3 = 3,
+    THC_POL_BF16 = 4,
+    THC_POL_FP32 = 5
+};
 
 typedef struct {
     int n_occ;               /* o > 0 */
@@ -106,6 +149,7 @@ typedef struct {
                                 a quarter of the free memory (at most 48 GiB),
                                 else the fewest blocks that do, rounded up to
                                 32 rows */
+    int policy[THC_N_STEPS]; /* per-step arithmetic, THC_POL_* (0 = default) */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */
@@ -316,25 +360,12 @@ thc_status thc_solve_pairs(thc_ctx* ctx, float* X, float* j, float* t, long long
 
 /*
  * Per-step device timing (CUDA events recorded on the context's stream
- * around every step of thc_residual while profiling is on).  flops counts
- * the algorithmic floating-point operations the step issued (2 per
- * multiply-add of every contraction; 5 per (I,X,Y,Z) term of the float32
- * triangle kernel, 3.5 for the float64 one, which shares t between the
- * mirror terms (Y,Z) and (Z,Y)), so flops / ms is the achieved rate of that step.
+ * around every step of thc_residual while profiling is on; steps as in
+ * THC_STEP_*).  flops counts the algorithmic floating-point operations of
+ * the step (2 per multiply-add of every contraction, 5 per (I,X,Y,Z) term of
+ * the triangle whatever kernel runs it), so flops / ms is the achieved rate
+ * of that step.
  */
-enum {
-    THC_STEP_DRESS = 0,      /* T1 dressing of the Cholesky vectors (Eqs. 25-27) */
-    THC_STEP_FOCK = 1,       /* Coulomb/exchange parts of the dressed Fock matrix */
-    THC_STEP_ALG1 = 2,       /* ladders, Alg. 1 (+ Alg. 3 intermediate) */
-    THC_STEP_ALG2_8 = 3,     /* Alg. 2 and Alg. 8 per Cholesky vector */
-    THC_STEP_POST = 4,       /* Alg. 2/3 closing products, Algs. 9 and 10 */
-    THC_STEP_ALG6_GEMM = 5,  /* Alg. 6 lines 1-10 (contractions) */
-    THC_STEP_TRIANGLE = 6,   /* Alg. 6 line 11 (triangle kernel) */
-    THC_STEP_ALG6_POST = 7,  /* Alg. 6 lines 13-16 */
-    THC_STEP_ALG7 = 8,       /* Alg. 7 */
-    THC_STEP_ENERGY = 9,     /* energy */
-    THC_N_STEPS = 10
-};
 
 typedef struct {
     double ms[THC_N_STEPS];         /* accumulated device time per step */
@@ -454,10 +485,36 @@ thc_status thc_selftest_gemm_f64(int cases, unsigned long long seed, double* max
  */
 thc_status thc_selftest_bounded_wait(int complete, void* stream);
 
+/*
+ * thc_probe_alu - measured CUDA-core FMA throughput of the current device
+ * (the denominators of the triangle kernels' rooflines): `kind` 0 = float64
+ * FMA, 1 = float32 FMA, 2 = packed float32 pairs (fma.rn.f32x2).  Eight
+ * independent FMA chains per thread, 8 blocks of 256 threads per SM, one
+ * timed launch after a warm-up (CUDA events on `stream`); *tflops counts
+ * 2 flops per FMA lane.  Diagnostic; no counterpart in the paper.
+ */
+thc_status thc_probe_alu(int kind, double* tflops, void* stream);
+
+/*
+ * thc_probe_gemm - time of one tensor-core product C = A B (M x K times
+ * K x N, row-major, seeded uniform operands in [-1, 1]) averaged over
+ * `iters` products after two warm-up products, CUDA events on `stream`:
+ *   mode 0  float32 operands, bf16 hi*hi + hi*lo + lo*hi, packed operands
+ *           cached (the product kernel alone)
+ *   mode 1  the same with the bf16 hi/lo pack of both operands in every call
+ *   mode 2  bf16 hi*hi only, packed operands cached
+ *   mode 3  float64 operands as exact integer slices (THC_PREC_FP64_TC):
+ *           row exponents, slicing, 8 level products and the float64 pass
+ * *ms = milliseconds per product.  Allocates its operands and workspace.
+ * Errors: THC_ERR_ARG, THC_ERR_OOM, THC_ERR_CUDA, THC_ERR_TIMEOUT.
+ * Diagnostic; no counterpart in the paper.
+ */
+thc_status thc_probe_gemm(int mode, int M, int N, int K, int iters, double* ms, void* stream);
+
 /* Text of the first error recorded on ctx ("" if none).  The pointer stays
  * valid until the next call on ctx or thc_destroy.  ctx may be NULL, which
- * returns the last error of a failed thc_init or thc_energy_noalloc on this
- * thread. */
+ * returns the last error of a failed thc_init, thc_energy_noalloc or
+ * thc_probe_* call on this thread. */
 const char* thc_last_error(const thc_ctx* ctx);
 
 /* Release every device buffer of ctx.  NULL is accepted. */

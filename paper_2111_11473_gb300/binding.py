@@ -25,7 +25,13 @@ class ThcConfig(C.Structure):
                 ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double),
                 ("tc_products", C.c_int), ("alg7_route", C.c_int), ("t2sq_route", C.c_int),
-                ("x_block6", C.c_int)]
+                ("x_block6", C.c_int), ("policy", C.c_int * 10)]
+
+
+# Steps of a residual (THC_STEP_*) and per-step arithmetic (THC_POL_*).
+STEPS = ["dress", "fock", "alg1", "alg2_8", "post", "alg6_gemm", "triangle", "alg6_post",
+         "alg7", "energy"]
+POLICIES = {"default": 0, "fp64": 1, "fp64tc": 2, "bf16x3": 3, "bf16": 4, "fp32": 5}
 
 
 class ThcSolveOpts(C.Structure):
@@ -110,6 +116,9 @@ _SIGNATURES = {
                                     C.POINTER(C.c_int), _VP]),
     "thc_cp_als": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP,
                              C.c_int, _DP, _VP]),
+    "thc_probe_alu": (C.c_int, [C.c_int, C.POINTER(C.c_double), _VP]),
+    "thc_probe_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.POINTER(C.c_double), _VP]),
     "thc_last_error": (C.c_char_p, [_VP]),
     "thc_destroy": (None, [_VP]),
 }
@@ -181,6 +190,31 @@ def selftest_gemm_f64(cases=64, seed=0, stream=None):
     return STATUS.get(status, "?"), mr.value, nf.value
 
 
+def probe_alu(kind: int, stream=None) -> float:
+    """Measured FMA throughput in TFLOP/s: kind 0 float64, 1 float32,
+    2 packed float32 pairs (thc_probe_alu)."""
+    lib = load_library()
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    v = C.c_double(0)
+    status = lib.thc_probe_alu(int(kind), C.byref(v), _VP(st))
+    if status != 0:
+        raise ThcError(status, lib.thc_last_error(None).decode())
+    return v.value
+
+
+def probe_gemm(mode: int, M: int, N: int, K: int, iters: int = 10, stream=None) -> float:
+    """Milliseconds per tensor-core product (thc_probe_gemm): mode 0 bf16x3
+    with cached packs, 1 bf16x3 with the pack, 2 bf16x1, 3 float64 slices."""
+    lib = load_library()
+    st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+    v = C.c_double(0)
+    status = lib.thc_probe_gemm(int(mode), int(M), int(N), int(K), int(iters), C.byref(v),
+                                _VP(st))
+    if status != 0:
+        raise ThcError(status, lib.thc_last_error(None).decode())
+    return v.value
+
+
 def selftest_bounded_wait(complete: bool, stream=None) -> str:
     """Run the library's bounded-wait self-test; returns the status name
     (THC_OK if the wait completed, THC_ERR_TIMEOUT if it expired)."""
@@ -227,9 +261,11 @@ class Context:
 
     def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
                  k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10,
-                 tc_products=3, alg7_route=0, t2sq_route=0, x_block6=0, n_k=None):
+                 tc_products=3, alg7_route=0, t2sq_route=0, x_block6=0, n_k=None,
+                 policy=None):
         """L = None (with n_k = K) leaves the Cholesky vectors to
-        load_cholesky() and finish_init()."""
+        load_cholesky() and finish_init().  policy: {step name: policy name}
+        (STEPS, POLICIES), the per-step arithmetic of thc_config.policy."""
         lib = load_library()
         o, v = len(eps_o), len(eps_v)
         n = o + v
@@ -250,6 +286,8 @@ class Context:
         cfg.alg7_route = alg7_route
         cfg.t2sq_route = t2sq_route
         cfg.x_block6 = x_block6
+        for step, name in (policy or {}).items():
+            cfg.policy[STEPS.index(step)] = POLICIES[name]
         args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)),
                 _Arg(L, (K, n, n)) if L is not None else None,
                 _Arg(x, (n, G)), _Arg(z, (G, G))]

@@ -50,6 +50,18 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "alg7_route must be 0, 1 or 2"};
     if (cfg->t2sq_route < 0 || cfg->t2sq_route > 2)
         return {THC_ERR_ARG, "t2sq_route must be 0, 1 or 2"};
+    const bool f64 = cfg->precision != THC_PREC_MIXED;
+    for (int s = 0; s < THC_N_STEPS; ++s) {
+        const int p = cfg->policy[s];
+        if (p == THC_POL_DEFAULT) continue;
+        const bool ok = f64 ? (p == THC_POL_FP64 || p == THC_POL_FP64_TC)
+                            : (s == THC_STEP_TRIANGLE ? p == THC_POL_FP32
+                                                      : (p == THC_POL_BF16X3 || p == THC_POL_BF16 ||
+                                                         p == THC_POL_FP32));
+        if (!ok)
+            return {THC_ERR_ARG, std::string("policy of step ") + thc_step_name(s) +
+                                     " does not fit the context's precision"};
+    }
     return {};
 }
 

@@ -102,6 +102,7 @@ Err Engine<T>::check_finite(const double* a, long long count, const char* what) 
 
 template <typename T>
 void Engine<T>::seg_begin(int step) {
+    step_now = step;
     // NVTX range per step (visible to ncu's NVTX filters and other tools)
     if (nvtx_open) nvtxRangePop();
     nvtxRangePushA(thc_step_name(step));
@@ -116,6 +117,7 @@ void Engine<T>::seg_begin(int step) {
 
 template <typename T>
 void Engine<T>::seg_end() {
+    step_now = -1;
     if (nvtx_open) {
         nvtxRangePop();
         nvtx_open = false;
@@ -172,12 +174,13 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     if constexpr (std::is_same<T, float>::value) {
         // Large products go to the tensor cores; the rest stays on the CUDA
         // cores (also if the packed operands do not fit the workspace).
-        if (tc_products > 0 && fl >= 3.0e7 && Kd >= 16) {
-            cudaError_t e = gemm_tc(g, tcws, tc_products, st, &pcache);
+        const int tcp = tcws.buf ? step_tcp() : 0;
+        if (tcp > 0 && fl >= 3.0e7 && Kd >= 16) {
+            cudaError_t e = gemm_tc(g, tcws, tcp, st, &pcache);
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
             why = "workspace";
-        } else if (tc_products > 0 && fl >= 3.0e7) {
+        } else if (tcp > 0 && fl >= 3.0e7) {
             why = "K < 16";
         }
     } else {
@@ -188,12 +191,13 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
         const double out = (double)M * N * (reduce ? 1 : batch);
         const double t_tc = 36.0 * fl / 1.2e15 + 8.0 * out * 8.0 / 5e12 + out * 16.0 / 5e12 +
                             14.0 * 5e-6;
-        if (f64tc && fl >= 3.0e7 && Kd >= 16 && t_tc < fl / 1.0e12) {
+        const bool use_tc = step_f64tc();
+        if (use_tc && fl >= 3.0e7 && Kd >= 16 && t_tc < fl / 1.0e12) {
             cudaError_t e = gemm_f64_tc(g, f64ws, st);
             if (e == cudaSuccess) return Err{};
             if (e != cudaErrorMemoryAllocation) THC_CUDA(e);
             why = "workspace";
-        } else if (f64tc && fl >= 3.0e7) {
+        } else if (use_tc && fl >= 3.0e7) {
             why = Kd < 16 ? "K < 16" : "cost model";
         }
     }
@@ -294,6 +298,20 @@ Err Engine<T>::init_begin(const thc_config& cfg, const double* eps_o, const doub
     st = s;
     cfg0 = cfg;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
+    // Per-step arithmetic: the context's policy unless the step names its own.
+    f64tc_default = std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC;
+    for (int s_ = 0; s_ < THC_N_STEPS; ++s_) {
+        int p = cfg.policy[s_];
+        if (p == THC_POL_DEFAULT) {
+            if (std::is_same<T, double>::value)
+                p = f64tc_default ? THC_POL_FP64_TC : THC_POL_FP64;
+            else
+                p = cfg.tc_products == 3 ? THC_POL_BF16X3
+                                         : (cfg.tc_products == 1 ? THC_POL_BF16 : THC_POL_FP32);
+        }
+        if (!std::is_same<T, double>::value && s_ == THC_STEP_TRIANGLE) p = THC_POL_FP32;
+        pol[s_] = p;
+    }
     {
         // Cholesky slab: as many vectors as the per-vector scratch budget holds
         // (six P x P intermediates dominate), at least 16.  The budget is a
@@ -587,7 +605,7 @@ Err Engine<T>::init_finish() {
     }
     if (!t2sq_n5) {
         gall_resident = gall_fits;
-        tri_df = std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC;
+        tri_df = std::is_same<T, double>::value && pol[THC_STEP_TRIANGLE] == THC_POL_FP64_TC;
         if (gall_resident) {
             THC_TRY(Gall.alloc((size_t)G * PP));
             THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0,
@@ -683,7 +701,13 @@ Err Engine<T>::init_finish() {
                 shapes.push_back(sh);
         }
     }
-    if (std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC) {
+    bool any_f64tc = cfg.precision == THC_PREC_FP64_TC, any_bf16 = cfg.tc_products > 0;
+    for (int st_ = 0; st_ < THC_N_STEPS; ++st_) {
+        if (st_ == THC_STEP_TRIANGLE) continue;   // not a product
+        any_f64tc = any_f64tc || pol[st_] == THC_POL_FP64_TC;
+        any_bf16 = any_bf16 || pol[st_] == THC_POL_BF16X3 || pol[st_] == THC_POL_BF16;
+    }
+    if (std::is_same<T, double>::value && any_f64tc) {
         // Slices of the largest product's operands and the float32 level
         // outputs of the largest product, at most a quarter of the free
         // memory (a product that does not fit runs on the CUDA cores).
@@ -714,7 +738,7 @@ Err Engine<T>::init_finish() {
         f64ws.err = tcerr.p;
         f64tc = true;
     }
-    if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && cfg.tc_products > 0) {
+    if (std::is_same<T, float>::value && cfg.precision == THC_PREC_MIXED && any_bf16) {
         // Packed-operand workspace: the largest product of the residual.
         size_t need = 0;
         for (const Shape& sh : shapes)

@@ -92,6 +92,19 @@ struct Engine {
     size_t bytes = 0;
     Profiler prof;
     bool nvtx_open = false;                 // an NVTX step range is open
+    int step_now = -1;                      // step being evaluated (THC_STEP_*), -1 outside
+    int pol[THC_N_STEPS] = {};              // resolved per-step arithmetic (THC_POL_*)
+    bool f64tc_default = false;             // context policy outside the steps
+    // Tensor-core products per contraction of the current step (float engine).
+    int step_tcp() const {
+        if (step_now < 0) return tc_products;
+        const int p = pol[step_now];
+        return p == THC_POL_BF16X3 ? 3 : (p == THC_POL_BF16 ? 1 : 0);
+    }
+    // Float64 products of the current step on the tensor cores.
+    bool step_f64tc() const {
+        return f64tc && (step_now < 0 ? f64tc_default : pol[step_now] == THC_POL_FP64_TC);
+    }
     // Open / close a timed segment of step `step` (no-ops when profiling is off).
     void seg_begin(int step);
     void seg_end();

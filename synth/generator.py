@@ -205,6 +205,8 @@ def random_amplitudes(P: int, o: int, v: int, seed: int,
 CONFIGS = {
     "o5_v20_P60_G120_K60": (5, 20, 60, 120, 60, 0),
     "o40_v200_P400_G1200_K600": (40, 200, 400, 1200, 600, 1),
+    # half the bench size in every dimension (kernel profiles of a few GB)
+    "o20_v100_P200_G600_K300": (20, 100, 200, 600, 300, 1),
     "o100_v600_P1000_G3500_K1500": (100, 600, 1000, 3500, 1500, 2),
     "o250_v2250_P2500_G12500_K7500": (250, 2250, 2500, 12500, 7500, 3),
     # first held-out system of the learned-preconditioner protocol

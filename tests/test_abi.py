@@ -30,7 +30,7 @@ def test_header_declares_the_abi():
                            "thc_mlp_destroy",
                            "thc_mlp_get_params", "thc_mlp_loss_grad", "thc_mlp_num_params",
                            "thc_mlp_predict", "thc_mlp_set_params", "thc_mlp_train",
-                           "thc_mp2_density",
+                           "thc_mp2_density", "thc_probe_alu", "thc_probe_gemm",
                            "thc_profile_enable", "thc_profile_read",
                            "thc_residual", "thc_selftest_bounded_wait", "thc_selftest_gemm", "thc_selftest_gemm_f64",
                            "thc_solve",

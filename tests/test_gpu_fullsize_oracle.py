@@ -19,8 +19,10 @@ Float64 (CUDA-core products and tensor-core integer-slice products): max-abs
 1e-10, sigma also within 1e-11 of max|sigma|, Omega1 within 1e-12 (the
 oracle's textbook Fock matrix adds Coulomb sums of o (pp|qq) ~ 12 Eh, whose
 float64 rounding alone is ~1e-14 there), energy 1e-9 Eh.  Mixed precision (float32,
-bf16x3 products): 1e-4 of max|sigma|, energy 1e-6 relative, the bounds of
-the small-size mixed tests.
+bf16x3 products): 1e-4 of max(max|sigma|, 1e-3), energy 1e-6 relative.  The
+floor stands for the terms of order 1e-3..1 (bare integrals, Fock terms)
+whose float32 rounding sets the error where sigma itself is small (5e-5 at
+the bench state: Omega1 is then off by ~1e-8).
 """
 import numpy as np
 import pytest
@@ -101,7 +103,7 @@ def test_fullsize_residual_matches_oracle(expected, ctx, state):
     print(f"{name} {state}: max|sigma| {scale:.3e}, max|d sigma| {d_sig:.3e} "
           f"({d_sig / scale:.2e} rel), max|d Omega1| {d_r1:.3e}, dE {E - E_ref:.3e}")
     if name == "mixed":
-        assert max(d_sig, d_r1) < MIXED_REL * scale
+        assert max(d_sig, d_r1) < MIXED_REL * max(scale, 1e-3)
         assert abs(E - E_ref) < 1e-6 * max(1e-3, abs(E_ref))
     else:
         assert d_sig < RES_TOL and d_r1 < RES_TOL
