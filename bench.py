@@ -338,6 +338,64 @@ def _rate(ctx, Zc, t1, sig, sig1, stream, dev, steps=5, warmup=3):
     return 1e3 * steps / e0.elapsed_time(e1)
 
 
+PRODUCT_STEPS = ["dress", "fock", "alg1", "alg2_8", "post", "alg6_gemm", "alg6_post", "alg7",
+                 "energy"]
+
+
+def policy_scan(pkg, s, dev, stream, args):
+    """Per-step error of the mixed policy at the float64 converged point:
+    for every step with products, that step in bf16 (hi*hi) and the rest in
+    bf16x3, against the float64 residual and energy at the same (Zc, t1);
+    the residual time of each policy; then solves of the uniform bf16x3
+    policy and of the candidate policy (bf16 in every step whose error stays
+    below 1e-9 Eh and 1e-7 of max|sigma|) to the float64 energy."""
+    import numpy as np
+    import torch
+    from paper_2111_11473_gb300 import precond
+    out = {}
+    with _context(pkg, s, precision=pkg.THC_PREC_FP64_TC, stream=stream) as c:
+        hist = []
+        Zc, t1, rep = c.solve(r_tol=args.fp64_rtol, max_iter=args.max_iter, history=hist,
+                              raise_on_failure=False)
+        ref = c.residual(Zc, t1)
+    f = {"energy": rep.energy, "iters": rep.iters, "wall_s": rep.wall_s, "r_norm": rep.r_norm,
+         "time_to_e_tol_s": precond.time_to(hist, rep.energy, 1e-6)[1]}
+    out["fp64"] = f
+    Zd = torch.from_numpy(Zc).to(dev)
+    td = torch.from_numpy(t1).to(dev)
+    sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
+    sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
+    scale = float(np.abs(ref[0]).max())
+
+    def measure(policy):
+        with _context(pkg, s, precision=pkg.THC_PREC_MIXED, stream=stream, policy=policy) as c:
+            r = c.residual(Zc, t1)
+            rate = _rate(c, Zd, td, sig, sig1, stream, dev)
+        d = r[0] - ref[0]
+        return {"max_abs_dsigma": float(np.abs(d).max()), "norm_dsigma": float(np.linalg.norm(d)),
+                "norm_dsigma1": float(np.linalg.norm(r[1] - ref[1])), "dE": r[2] - ref[2],
+                "ms": 1e3 / rate}
+
+    rows = {"bf16x3": measure(None)}
+    for step in PRODUCT_STEPS:
+        rows[step + "=bf16"] = measure({step: "bf16"})
+    out["residual_at_fp64_solution"] = rows
+    base = rows["bf16x3"]
+    cheap = [st for st in PRODUCT_STEPS
+             if abs(rows[st + "=bf16"]["dE"] - base["dE"]) < 1e-9 and
+             rows[st + "=bf16"]["max_abs_dsigma"] < base["max_abs_dsigma"] + 1e-7 * scale]
+    cand = {st: "bf16" for st in cheap}
+    out["candidate"] = {"steps_bf16": cheap, **measure(cand)}
+    for name, pol in (("bf16x3", None), ("candidate", cand)):
+        with _context(pkg, s, precision=pkg.THC_PREC_MIXED, stream=stream, policy=pol) as c:
+            m = precond.run_solve(c, f["energy"], None, r_tol=args.solve_rtol,
+                                  max_iter=args.max_iter, stop_de=1e-8)
+        out["solve_" + name] = {"energy": m["energy"], "energy_minus_fp64": m["energy"] - f["energy"],
+                                "iters": m["iters"], "wall_s": m["wall_s"],
+                                "time_to_e_tol_s": m["time_to_e_tol_s"]}
+    return out
+
+
 def fp64_vs_mixed_iterations(pkg, s, stream, n_iter):
     """Energy of the float64 and of the mixed-precision solve from zero,
     iteration by iteration (each on its own trajectory), and their difference."""
@@ -457,6 +515,9 @@ def main():
     ap.add_argument("--fp64-iters", type=int, default=0,
                     help="also run this many float64 and mixed iterations from zero "
                          "and report their energy difference per iteration")
+    ap.add_argument("--policy-scan", action="store_true",
+                    help="per-step error and time of the mixed policy at the float64 "
+                         "solution, and solves of the candidate per-step policy")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the CUDA-core FMA rates and time 4096^3 tensor-core "
                          "products (thc_probe_alu, thc_probe_gemm), print one JSON line")
@@ -618,6 +679,8 @@ def main():
         line["solve"] = solve_variants(pkg, s, dev, stream, ctx, args, prec, rate=1e3 / ms)
     if args.fp64_iters > 0:
         line["fp64_vs_mixed"] = fp64_vs_mixed_iterations(pkg, s, stream, args.fp64_iters)
+    if args.policy_scan:
+        line["policy_scan"] = policy_scan(pkg, s, dev, stream, args)
     ctx.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:

@@ -101,8 +101,11 @@ __device__ __forceinline__ void df_acc(f2& Sh, f2& Sl, f2 th, f2 tl, f2 thn, f2 
 
 constexpr int DX = 4;     // amplitude indices X per block (two lane pairs)
 constexpr int DT = 32;    // Y and Z tile
-constexpr int DS = 2;     // grid points per pipeline stage
+constexpr int DS = 4;     // grid points per pipeline stage
 constexpr int DTH = 256;  // threads: 16 x 16, each a 2 x 2 (Y, Z) block
+
+static_assert(DS * 2 * DT == DTH, "one E/F element per thread and stage");
+static_assert(DT * DT == 4 * DTH / 8 * 8 && DTH / DT * 4 == DT, "four G rows per thread");
 
 struct DfStage {
     float4 ey[DS][2][DT];         // E^{x,Y} of the Y tile, {h(x), h(x+1), l(x), l(x+1)}
@@ -124,30 +127,69 @@ __device__ __forceinline__ void cpa8(void* dst, const void* src, bool ok) {
                  "r"(ok ? 8 : 0));
 }
 
-// Stage grid points I0 .. I0 + DS - 1 of the block's tiles (zeros outside).
-__device__ __forceinline__ void df_load(DfStage& st, const float4* E4, const float4* F4,
-                                        const float2* G2, int P, int nXp, int nI, int I0,
-                                        int xp0, int Y0, int Z0) {
-    const long long PP = (long long)P * P, XP = (long long)nXp * P;
-    const int tid = threadIdx.x;
-    for (int e = tid; e < DS * DT * DT; e += DTH) {
-        const int s = e / (DT * DT), r = (e / DT) % DT, c = e % DT;
-        const int I = I0 + s;
-        const bool ok1 = I < nI && Y0 + r < P && Z0 + c < P;
-        const bool ok2 = I < nI && Z0 + r < P && Y0 + c < P;
-        cpa8(&st.g1[s][r][c], ok1 ? G2 + I * PP + (long long)(Y0 + r) * P + Z0 + c : G2, ok1);
-        cpa8(&st.g2[s][r][c], ok2 ? G2 + I * PP + (long long)(Z0 + r) * P + Y0 + c : G2, ok2);
+// Per-thread copy plan of the block's tiles, fixed for the whole launch.
+// G tiles: thread tid copies column c = tid % 32 of rows r0 + 8 q (q < 4) of
+// both tiles for each grid point of a stage; E, F: thread tid copies the
+// element (s, xp, c) = (tid / 64, tid / 32 % 2, tid % 32) of the four arrays.
+struct DfPlan {
+    int g1off[4], g2off[4];   // (Y0 + r) P + Z0 + c, (Z0 + r) P + Y0 + c
+    unsigned gok;             // bit q: g1 row in range, bit 4 + q: g2 row in range
+    long long qoff;           // (xp0 + xp) P
+    int cy, cz;               // Y0 + c, Z0 + c
+    bool qok, yok, zok;
+};
+
+__device__ __forceinline__ DfPlan df_plan(int P, int nXp, int xp0, int Y0, int Z0) {
+    DfPlan pl;
+    const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;
+    pl.gok = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = r0 + 8 * q;
+        pl.g1off[q] = (Y0 + r) * P + Z0 + c;
+        pl.g2off[q] = (Z0 + r) * P + Y0 + c;
+        if (Y0 + r < P && Z0 + c < P) pl.gok |= 1u << q;
+        if (Z0 + r < P && Y0 + c < P) pl.gok |= 1u << (4 + q);
     }
-    for (int e = tid; e < DS * 2 * DT; e += DTH) {
-        const int s = e / (2 * DT), xp = (e / DT) % 2, c = e % DT;
-        const int I = I0 + s, q = xp0 + xp;
-        const bool okx = I < nI && q < nXp;
-        const long long base = I * XP + (long long)q * P;
-        const bool oy = okx && Y0 + c < P, oz = okx && Z0 + c < P;
-        cpa16(&st.ey[s][xp][c], oy ? E4 + base + Y0 + c : E4, oy);
-        cpa16(&st.ez[s][xp][c], oz ? E4 + base + Z0 + c : E4, oz);
-        cpa16(&st.fy[s][xp][c], oy ? F4 + base + Y0 + c : F4, oy);
-        cpa16(&st.fz[s][xp][c], oz ? F4 + base + Z0 + c : F4, oz);
+    const int xp = (tid >> 5) & 1;
+    pl.qoff = (long long)(xp0 + xp) * P;
+    pl.qok = xp0 + xp < nXp;
+    pl.cy = Y0 + c;
+    pl.cz = Z0 + c;
+    pl.yok = Y0 + c < P;
+    pl.zok = Z0 + c < P;
+    return pl;
+}
+
+// Stage grid points I0 .. I0 + DS - 1 of the block's tiles (zeros outside).
+__device__ __forceinline__ void df_load(DfStage& st, const DfPlan& pl, const float4* E4,
+                                        const float4* F4, const float2* G2, int P, int nXp,
+                                        int nI, int I0) {
+    const long long PP = (long long)P * P, XP = (long long)nXp * P;
+    const int tid = threadIdx.x, c = tid & 31, r0 = tid >> 5;
+#pragma unroll
+    for (int s = 0; s < DS; ++s) {
+        const int I = I0 + s;
+        const bool iok = I < nI;
+        const float2* Gi = G2 + (iok ? I * PP : 0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool ok1 = iok && (pl.gok >> q & 1u);
+            const bool ok2 = iok && (pl.gok >> (4 + q) & 1u);
+            cpa8(&st.g1[s][r0 + 8 * q][c], ok1 ? Gi + pl.g1off[q] : G2, ok1);
+            cpa8(&st.g2[s][r0 + 8 * q][c], ok2 ? Gi + pl.g2off[q] : G2, ok2);
+        }
+    }
+    {
+        const int s = tid >> 6, xp = (tid >> 5) & 1;
+        const int I = I0 + s;
+        const bool okx = I < nI && pl.qok;
+        const long long base = (okx ? I * XP + pl.qoff : 0);
+        const bool oy = okx && pl.yok, oz = okx && pl.zok;
+        cpa16(&st.ey[s][xp][c], oy ? E4 + base + pl.cy : E4, oy);
+        cpa16(&st.ez[s][xp][c], oz ? E4 + base + pl.cz : E4, oz);
+        cpa16(&st.fy[s][xp][c], oy ? F4 + base + pl.cy : F4, oy);
+        cpa16(&st.fz[s][xp][c], oz ? F4 + base + pl.cz : F4, oz);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -179,11 +221,12 @@ __global__ void __launch_bounds__(DTH, 1)
 #pragma unroll
             for (int j = 0; j < 2; ++j) h1[a][i][j] = l1[a][i][j] = h2[a][i][j] = l2[a][i][j] = 0ull;
     const int nsteps = (nI + DS - 1) / DS;
-    if (nsteps > 0) df_load(stg[0], E4, F4, G2, P, nXp, nI, 0, xp0, Y0, Z0);
+    const DfPlan plan = df_plan(P, nXp, xp0, Y0, Z0);
+    if (nsteps > 0) df_load(stg[0], plan, E4, F4, G2, P, nXp, nI, 0);
     for (int k = 0; k < nsteps; ++k) {
         const DfStage& cur = stg[k & 1];
         if (k + 1 < nsteps) {
-            df_load(stg[(k + 1) & 1], E4, F4, G2, P, nXp, nI, (k + 1) * DS, xp0, Y0, Z0);
+            df_load(stg[(k + 1) & 1], plan, E4, F4, G2, P, nXp, nI, (k + 1) * DS);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -206,30 +249,29 @@ __global__ void __launch_bounds__(DTH, 1)
                 }
 #pragma unroll
             for (int xp = 0; xp < 2; ++xp) {
-                float4 ey[2], fy[2], ez[2], fz[2];
+                // {h(x), h(x+1)} and {l(x), l(x+1)} as two 64-bit lanes
+                ulonglong2 ey[2], fy[2], ez[2], fz[2];
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    ey[i] = cur.ey[st][xp][ty + 16 * i];
-                    fy[i] = cur.fy[st][xp][ty + 16 * i];
-                    ez[i] = cur.ez[st][xp][tx + 16 * i];
-                    fz[i] = cur.fz[st][xp][tx + 16 * i];
+                    ey[i] = reinterpret_cast<const ulonglong2&>(cur.ey[st][xp][ty + 16 * i]);
+                    fy[i] = reinterpret_cast<const ulonglong2&>(cur.fy[st][xp][ty + 16 * i]);
+                    ez[i] = reinterpret_cast<const ulonglong2&>(cur.ez[st][xp][tx + 16 * i]);
+                    fz[i] = reinterpret_cast<const ulonglong2&>(cur.fz[st][xp][tx + 16 * i]);
                 }
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         f2 th, tl;
-                        df_dot2(pk(ey[i].x, ey[i].y), pk(ey[i].z, ey[i].w),
-                                pk(fz[j].x, fz[j].y), pk(fz[j].z, fz[j].w),
-                                pk(ez[j].x, ez[j].y), pk(ez[j].z, ez[j].w),
-                                pk(fy[i].x, fy[i].y), pk(fy[i].z, fy[i].w), th, tl);
+                        df_dot2(ey[i].x, ey[i].y, fz[j].x, fz[j].y, ez[j].x, ez[j].y, fy[i].x,
+                                fy[i].y, th, tl);
                         const f2 thn = sub2(0ull, th);
                         df_acc(h1[xp][i][j], l1[xp][i][j], th, tl, thn, g1h[i][j], g1l[i][j]);
                         df_acc(h2[xp][i][j], l2[xp][i][j], th, tl, thn, g2h[i][j], g2l[i][j]);
                     }
             }
         }
-        __syncthreads();   // the buffer is refilled two steps later
+        __syncthreads();   // the buffer is refilled by the next step's load
     }
     // On a diagonal pair both accumulators cover the same tile and count
     // every (Y, Z) twice.
