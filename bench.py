@@ -292,6 +292,66 @@ def run_reference(args):
     return 0
 
 
+def run_sharded(args, pkg, dev, stream, dist, world, rank):
+    """One system split over the ranks: every step evaluates each rank's
+    shard of the residual and sums the parts (sigma, Omega1, energy) with one
+    NCCL all-reduce; the state is a generic one at amplitude scale 0.01
+    (a residual's cost does not depend on the values)."""
+    import torch
+    from synth import random_amplitudes
+    s = _system(device=dev)
+    prec = {"fp64": pkg.THC_PREC_FP64, "fp64tc": pkg.THC_PREC_FP64_TC,
+            "mixed": pkg.THC_PREC_MIXED}[args.precision]
+    ctx = _context(pkg, s, dev, precision=prec, stream=stream, shard=(rank, world))
+    Zc0, t10 = random_amplitudes(s.P, s.o, s.v, 7, t2_scale=0.01, t1_scale=0.01)
+    Zc = torch.from_numpy(Zc0).to(dev)
+    t1 = torch.from_numpy(t10).to(dev)
+    sig = torch.empty((s.P, s.P), dtype=torch.float64, device=dev)
+    sig1 = torch.empty((s.o, s.v), dtype=torch.float64, device=dev)
+    flat = torch.empty(s.P * s.P + s.o * s.v + 1, dtype=torch.float64, device=dev)
+
+    def step():
+        _, _, e = ctx.residual(Zc, t1, out=(sig, sig1))
+        flat[:s.P * s.P].copy_(sig.reshape(-1))
+        flat[s.P * s.P:-1].copy_(sig1.reshape(-1))
+        flat[-1] = e
+        dist.all_reduce(flat)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+    energy = float(flat[-1])
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64" if args.precision != "mixed" else "f32+bf16x3",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
+                           "parallelism": f"one system in {world} shards (Cholesky vectors, "
+                                          "Alg. 6 rows; Alg. 7 on the last), NCCL all-reduce "
+                                          "of sigma, Omega1, energy per step",
+                           "state": "generic, amplitude scale 0.01"},
+                "energy": energy, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_peaks():
     """Roofline denominators and product rates measured through the library:
     float64 / float32 / packed-pair FMA throughput, and one 4096^3 product
@@ -518,6 +578,10 @@ def main():
     ap.add_argument("--policy-scan", action="store_true",
                     help="per-step error and time of the mixed policy at the float64 "
                          "solution, and solves of the candidate per-step policy")
+    ap.add_argument("--sharded", action="store_true",
+                    help="under torchrun: one system split over the ranks (thc_config "
+                         "shard_index / shard_count), the parts summed by one NCCL "
+                         "all-reduce per step (strong scaling)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the CUDA-core FMA rates and time 4096^3 tensor-core "
                          "products (thc_probe_alu, thc_probe_gemm), print one JSON line")
@@ -546,6 +610,8 @@ def main():
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.sharded and world > 1:
+        return run_sharded(args, pkg, dev, stream, dist, world, rank)
     s = _system(seed_offset=rank, device=dev)
     prec = {"fp64": pkg.THC_PREC_FP64, "fp64tc": pkg.THC_PREC_FP64_TC,
             "mixed": pkg.THC_PREC_MIXED}[args.precision]

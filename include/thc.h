@@ -150,6 +150,22 @@ typedef struct {
                                 else the fewest blocks that do, rounded up to
                                 32 rows */
     int policy[THC_N_STEPS]; /* per-step arithmetic, THC_POL_* (0 = default) */
+    int shard_index;         /* this context's shard, 0 .. shard_count - 1 */
+    int shard_count;         /* > 1: the context evaluates one shard of the
+                                residual (Sec. III's multi-GPU split): the
+                                Cholesky vectors [K s/n, K (s+1)/n) for Algs.
+                                1, 2, 3, 8, the Fock matrix and the singles
+                                energy, the amplitude indices X in
+                                [P s/n, P (s+1)/n) for Alg. 6, Alg. 7 on the
+                                last shard, the orbital-energy Fock terms on
+                                the first.  thc_residual and thc_energy then
+                                return that shard's part: the sums of sigmaZ,
+                                sigma1 and the energy over all shards are the
+                                unsharded results (every step is linear in
+                                these partial sums).  Only the shard's own
+                                Cholesky vectors are stored.  thc_solve is not
+                                available on a sharded context.  0 or 1 =
+                                unsharded; needs shard_count <= n_k. */
 } thc_config;
 
 /* Fill *cfg with defaults for the given sizes (FP64, automatic blocking). */
@@ -283,6 +299,12 @@ typedef struct {
                             bit-identical to one uninterrupted solve.
                             THC_ERR_ARG with use_mlp or record_pairs, another
                             diis_n, or no stopped solve. */
+    int mlp_accept;      /* acceptance rule of the network's proposals:
+                            0 = the residual norm must drop by at least the
+                            factor the last plain Jacobi + DIIS iteration
+                            achieved (default); 1 = any drop; 2 = always
+                            accept (for tests of the accepted branch and for
+                            diagnostics) */
 } thc_solve_opts;
 
 typedef struct {
@@ -312,24 +334,28 @@ thc_status thc_solve(thc_ctx* ctx, const thc_solve_opts* opts,
 
 /*
  * Learned preconditioner (an addition to the method: the paper does not
- * specify the amplitude update).  A pointwise MLP over the elements (P, Q) of the working basis:
- * 8 features -> tanh(W1 x + b1) -> tanh(W2 a1 + b2) -> y = w3 . a2 + b3, width
- * `hidden` (256).  Features of element (P, Q) at iteration k, with s the RMS
- * of the doubles Jacobi step j = -sigma_q/(e_P + e_Q):
- *   e_P/2, e_Q/2, clip(j/s, 10), clip(dT_prev/s, 10), sign(T) log1p(|T|/s)/5,
- *   log10|r|/10, |e_P - e_Q|/2, 1.
- * The proposed doubles step is j (1 + clamp(y, -0.95, 4)); singles keep
- * Jacobi, and DIIS stores the step taken as its error vector.  In thc_solve
- * a proposal is accepted only if the next residual norm is smaller than the
- * current one by at least the factor the last plain Jacobi + DIIS iteration
- * achieved; otherwise the plain iterate from the same point is evaluated
- * instead (one extra residual), and after two rejections the solve continues
- * without proposals.
+ * specify the amplitude update).  A pointwise MLP over the elements of the
+ * solver state [t1 | T] (singles t_i^a and the doubles core T^PQ in the
+ * working basis): 8 features -> tanh(W1 x + b1) -> tanh(W2 a1 + b2) ->
+ * y = w3 . a2 + b3, width `hidden` (256).  An element's Jacobi step is
+ * j = -res/(eP + eQ) with (eP, eQ) = (e_P, e_Q) for doubles (res = sigma_q^PQ)
+ * and (-eps_i, eps_a) for singles (res = Omega_i^a); with s the RMS of its
+ * block's Jacobi step, its features at iteration k are
+ *   eP/2, eQ/2, clip(j/s, 10), clip(dx_prev/s, 10), sign(x) log1p(|x|/s)/5,
+ *   log10|r|/10, |eP - eQ|/2, +1 (doubles) or -1 (singles).
+ * The proposed step is j (1 + clamp(y, -0.95, 4)) for every element, and
+ * DIIS stores the step taken as its error vector.  In thc_solve a proposal is
+ * accepted by the rule of thc_solve_opts.mlp_accept (default: only if the
+ * next residual norm is smaller than the current one by at least the factor
+ * the last plain Jacobi + DIIS iteration achieved); otherwise the plain
+ * iterate from the same point is evaluated instead (one extra residual), and
+ * after two rejections the solve continues without proposals.
  *
  * Training pairs come from thc_solve with record_pairs > 0: per iteration
- * k >= 2 the features X (n x 8), the scaled Jacobi step j/s and the scaled
- * ideal step t = (T* - T_k)/s, T* the converged core.  Loss:
- *   L = mean_n (j_n (1 + y_n) - t_n)^2,  trained with Adam.
+ * k >= 2, record_pairs doubles elements and a quarter as many singles
+ * elements (drawn with replacement): features X (n x 8), the scaled Jacobi
+ * step j/s and the scaled ideal step t = (x* - x_k)/s, x* the converged state.
+ * Loss:  L = mean_n (j_n (1 + y_n) - t_n)^2,  trained with Adam.
  * Parameters are one float32 vector [W1 (H x 8) | b1 | W2 (H x H) | b2 | w3 | b3]
  * (row-major).  bf16 = 1 runs the H x H layer on the tensor cores with bf16
  * weights/activations and float32 accumulation.  All pointers may be host or

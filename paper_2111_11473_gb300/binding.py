@@ -25,7 +25,8 @@ class ThcConfig(C.Structure):
                 ("k_slab", C.c_int), ("i_chunk", C.c_int), ("x_block", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("lsq_rel_cutoff", C.c_double),
                 ("tc_products", C.c_int), ("alg7_route", C.c_int), ("t2sq_route", C.c_int),
-                ("x_block6", C.c_int), ("policy", C.c_int * 10)]
+                ("x_block6", C.c_int), ("policy", C.c_int * 10), ("shard_index", C.c_int),
+                ("shard_count", C.c_int)]
 
 
 # Steps of a residual (THC_STEP_*) and per-step arithmetic (THC_POL_*).
@@ -38,7 +39,7 @@ class ThcSolveOpts(C.Structure):
     _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
                 ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int),
                 ("history", C.c_void_p), ("mlp", C.c_void_p), ("record_pairs", C.c_int),
-                ("record_seed", C.c_ulonglong), ("resume", C.c_int)]
+                ("record_seed", C.c_ulonglong), ("resume", C.c_int), ("mlp_accept", C.c_int)]
 
 
 class ThcReport(C.Structure):
@@ -262,10 +263,12 @@ class Context:
     def __init__(self, eps_o, eps_v, Y, L, x, z, precision=THC_PREC_FP64, stream=None,
                  k_slab=0, i_chunk=0, x_block=0, workspace_bytes=0, lsq_rel_cutoff=1e-10,
                  tc_products=3, alg7_route=0, t2sq_route=0, x_block6=0, n_k=None,
-                 policy=None):
+                 policy=None, shard=None):
         """L = None (with n_k = K) leaves the Cholesky vectors to
         load_cholesky() and finish_init().  policy: {step name: policy name}
-        (STEPS, POLICIES), the per-step arithmetic of thc_config.policy."""
+        (STEPS, POLICIES), the per-step arithmetic of thc_config.policy.
+        shard: (index, count) makes a context that evaluates one shard of the
+        residual (thc_config.shard_index / shard_count)."""
         lib = load_library()
         o, v = len(eps_o), len(eps_v)
         n = o + v
@@ -288,6 +291,8 @@ class Context:
         cfg.x_block6 = x_block6
         for step, name in (policy or {}).items():
             cfg.policy[STEPS.index(step)] = POLICIES[name]
+        if shard is not None:
+            cfg.shard_index, cfg.shard_count = int(shard[0]), int(shard[1])
         args = [_Arg(eps_o, (o,)), _Arg(eps_v, (v,)), _Arg(Y, (n, P)),
                 _Arg(L, (K, n, n)) if L is not None else None,
                 _Arg(x, (n, G)), _Arg(z, (G, G))]
@@ -354,7 +359,7 @@ class Context:
 
     def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
               use_mlp=False, verbose=False, raise_on_failure=True, history=None, mlp=None,
-              record_pairs=0, record_seed=0, resume=False):
+              record_pairs=0, record_seed=0, resume=False, mlp_accept=0):
         """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero.
 
         If ``history`` is a list, (energy, |r|, seconds) per iteration is
@@ -376,6 +381,7 @@ class Context:
         opts.mlp = mlp._h.value if mlp is not None else None
         opts.record_pairs, opts.record_seed = int(record_pairs), int(record_seed)
         opts.resume = int(bool(resume))
+        opts.mlp_accept = int(mlp_accept)
         rep = ThcReport()
         st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
         if history is not None:

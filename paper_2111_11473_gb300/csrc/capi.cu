@@ -50,6 +50,9 @@ thc::Err check_config(const thc_config* cfg) {
         return {THC_ERR_ARG, "alg7_route must be 0, 1 or 2"};
     if (cfg->t2sq_route < 0 || cfg->t2sq_route > 2)
         return {THC_ERR_ARG, "t2sq_route must be 0, 1 or 2"};
+    if (cfg->shard_count < 0 || cfg->shard_count > cfg->n_k || cfg->shard_index < 0 ||
+        (cfg->shard_count <= 1 ? cfg->shard_index != 0 : cfg->shard_index >= cfg->shard_count))
+        return {THC_ERR_ARG, "shard_index must lie in 0 .. shard_count - 1, shard_count <= n_k"};
     const bool f64 = cfg->precision != THC_PREC_MIXED;
     for (int s = 0; s < THC_N_STEPS; ++s) {
         const int p = cfg->policy[s];
@@ -146,6 +149,7 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts) {
     opts->record_pairs = 0;
     opts->record_seed = 0;
     opts->resume = 0;
+    opts->mlp_accept = 0;
     return THC_OK;
 }
 
@@ -238,6 +242,11 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
     c->err.clear();
     if (thc::Err r = ready(c); !r.ok()) return fail(c, r);
     if (!opts || !Zc_inout || !t1_inout) return fail(c, {THC_ERR_ARG, "NULL argument"});
+    if (c->cfg.shard_count > 1)
+        return fail(c, {THC_ERR_UNSUPPORTED, "thc_solve needs the whole residual: a sharded "
+                                             "context evaluates one shard"});
+    if (opts->mlp_accept < 0 || opts->mlp_accept > 2)
+        return fail(c, {THC_ERR_ARG, "mlp_accept must be 0, 1 or 2"});
     if (thc::Err e = solver_of(c); !e.ok()) return fail(c, e);
     thc_report rep{};
     thc::Mlp* mlp = opts->mlp ? &opts->mlp->m : nullptr;

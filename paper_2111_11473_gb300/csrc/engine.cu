@@ -287,7 +287,7 @@ Err Engine<T>::init(const thc_config& cfg, const double* eps_o, const double* ep
                     cudaStream_t s) {
     THC_TRY(init_begin(cfg, eps_o, eps_v, Yh, xh, zh, s));
     if (!Lh) return Err{};   // the caller supplies the Cholesky vectors
-    THC_TRY(load_cholesky(0, K, Lh));
+    THC_TRY(load_cholesky(0, Kglob, Lh));
     return init_finish();
 }
 
@@ -298,6 +298,16 @@ Err Engine<T>::init_begin(const thc_config& cfg, const double* eps_o, const doub
     st = s;
     cfg0 = cfg;
     o = cfg.n_occ; v = cfg.n_vir; n = o + v; P = cfg.n_p; G = cfg.n_g; K = cfg.n_k;
+    // Shard: a contiguous range of Cholesky vectors and of Alg. 6 rows X.
+    Kglob = K;
+    nsh = cfg.shard_count > 1 ? cfg.shard_count : 1;
+    ish = nsh > 1 ? cfg.shard_index : 0;
+    K0 = (int)((long long)Kglob * ish / nsh);
+    K = (int)((long long)Kglob * (ish + 1) / nsh) - K0;
+    x_lo = (int)((long long)P * ish / nsh);
+    x_hi = (int)((long long)P * (ish + 1) / nsh);
+    do_alg7 = ish == nsh - 1;
+    f_terms = ish == 0;
     // Per-step arithmetic: the context's policy unless the step names its own.
     f64tc_default = std::is_same<T, double>::value && cfg.precision == THC_PREC_FP64_TC;
     for (int s_ = 0; s_ < THC_N_STEPS; ++s_) {
@@ -325,9 +335,9 @@ Err Engine<T>::init_begin(const thc_config& cfg, const double* eps_o, const doub
             budget = std::max<long long>(budget, std::min<long long>(16LL << 30,
                                                                      (long long)(free_b / 10)));
         const long long fit = budget / (per * (long long)sizeof(T));
-        kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, cfg.n_k)
+        kb = cfg.k_slab > 0 ? std::min(cfg.k_slab, K)
                             : (int)std::max<long long>(1, std::min<long long>(
-                                  cfg.n_k, std::max<long long>(16, fit)));
+                                  K, std::max<long long>(16, fit)));
     }
     const long long ov = (long long)o * v, vt = (long long)v * (v + 1) / 2;
 
@@ -382,10 +392,19 @@ Err Engine<T>::init_begin(const thc_config& cfg, const double* eps_o, const doub
 template <typename T>
 Err Engine<T>::load_cholesky(int k0, int nk, const double* Lh) {
     if (!pending) return Err{THC_ERR_ARG, "the Cholesky vectors are already set"};
-    if (!Lh || k0 < 0 || nk <= 0 || (long long)k0 + nk > K)
+    if (!Lh || k0 < 0 || nk <= 0 || (long long)k0 + nk > Kglob)
         return Err{THC_ERR_ARG, "Cholesky vector range outside 0 .. K - 1"};
     const long long ov = (long long)o * v, nn = (long long)n * n,
                     vt = (long long)v * (v + 1) / 2;
+    // Only the shard's own vectors [K0, K0 + K) are stored, at k - K0.
+    {
+        const long long lo = std::max<long long>(k0, K0);
+        const long long hi = std::min<long long>((long long)k0 + nk, (long long)K0 + K);
+        if (lo >= hi) return Err{};
+        Lh += (lo - k0) * nn;
+        k0 = (int)(lo - K0);
+        nk = (int)(hi - lo);
+    }
     if (!lstage.p) {
         THC_TRY(lstage.alloc((size_t)kb * nn));
         if (!std::is_same<T, double>::value) THC_TRY(lstageT.alloc((size_t)kb * nn));
@@ -835,8 +854,8 @@ Err Engine<T>::alg6(T* sgm) {
     THC_TRY(mm((int)ov, P, P, rm(KRy.p, P), rm(Tc.p, P), A6.p, P, 1, 0));
     // Blocks of x6 amplitude indices X: every line from 4 on is local to the
     // X rows of C_i, D_a, E, F and H (G_I^YZ is shared by all blocks).
-    for (int X0 = 0; X0 < P; X0 += x6) {
-        const int nX = std::min(x6, P - X0);
+    for (int X0 = x_lo; X0 < x_hi; X0 += x6) {
+        const int nX = std::min(x6, x_hi - X0);
         const long long xP = (long long)nX * P;
         seg_begin(THC_STEP_ALG6_GEMM);
         // C_i^XY (line 4) and D_a^XY (line 5) for the block's X
@@ -1108,11 +1127,14 @@ Err Engine<T>::residual_dev(bool want_energy) {
     THC_TRY(mm(P, P, P, rm(Ccross.p, P), tr(ST.p, P), sgm, P, -1, 1));
 
     // Dressed Fock matrix  F^ = dress(f) + 2 J - X  (see fock_slab)
+    // (on a sharded context the orbital-energy terms dress(f) belong to the
+    // first shard; J and X are the shard's partial sums over its vectors)
+    const double fw = f_terms ? 1.0 : 0.0;
     THC_CUDA(eps_t1(epsT.p, t1.p, o, v, E1.p, st));
-    THC_CUDA(lincomb(Foo.p, oo2, 1, foo.p, 2, Joo.p, -1, Xoo.p, st));
+    THC_CUDA(lincomb(Foo.p, oo2, fw, foo.p, 2, Joo.p, -1, Xoo.p, st));
     THC_CUDA(lincomb(Fov.p, ov, 2, Jov.p, -1, Xov.p, 0, (const T*)nullptr, st));
-    THC_CUDA(lincomb(Fvo.p, ov, 1, E1.p, 2, Jvo.p, -1, Xvo.p, st));
-    THC_CUDA(lincomb(Fvv.p, vv2, 1, fvv.p, 2, Jvv.p, -1, Xvv.p, st));
+    THC_CUDA(lincomb(Fvo.p, ov, fw, E1.p, 2, Jvo.p, -1, Xvo.p, st));
+    THC_CUDA(lincomb(Fvv.p, vv2, fw, fvv.p, 2, Jvv.p, -1, Xvv.p, st));
 
     // Alg. 9: E = o o (y_v^T Fb_vv y_v) - v o (y_o^T Fb_oo^T y_o), sigma += E B^T + B E^T
     THC_CUDA(lincomb(xoo.p, oo2, 1, Foo.p, 1, xoo.p, 0, (const T*)nullptr, st));
@@ -1131,8 +1153,12 @@ Err Engine<T>::residual_dev(bool want_energy) {
     THC_CUDA(lincomb(sg1, ov, 1, sg1, 1, D8.p, 1, FvoT.p, st));
 
     // Algs. 6 and 7 (T2^2 terms through the THC ovov integrals)
-    THC_TRY(t2sq_n5 ? alg45(sgm) : alg6(sgm));
-    THC_TRY(alg7(sgm));
+    if (t2sq_n5) {
+        if (ish == 0) THC_TRY(alg45(sgm));
+    } else {
+        THC_TRY(alg6(sgm));
+    }
+    if (do_alg7) THC_TRY(alg7(sgm));
 
     seg_begin(THC_STEP_POST);
     if constexpr (!std::is_same<T, double>::value) {

@@ -84,6 +84,11 @@ enum class MMKind { SIMT, TC_BF16X3 };
 template <typename T>
 struct Engine {
     int o = 0, v = 0, n = 0, P = 0, G = 0, K = 0;
+    // Shard of a multi-GPU split: Cholesky vectors [K0, K0 + K) of Kglob
+    // (K is the local count), Alg. 6 rows [x_lo, x_hi), Alg. 7 and the
+    // orbital-energy Fock terms on one shard each.
+    int Kglob = 0, K0 = 0, x_lo = 0, x_hi = 0, nsh = 1, ish = 0;
+    bool do_alg7 = true, f_terms = true;
     int kb = 0, ic = 0, xb = 0;
     int x6 = 0;                             // amplitude indices X per Alg. 6 block
     bool gall_resident = false;

@@ -142,25 +142,41 @@ struct TcArgs {
     int nprod;
     int a_bcast, b_bcast;  // operand shared by every batch: packed once, batch coord 0
     int* err;
+    // nlev > 0: the slice levels of one float64 product in one launch.  Tiles
+    // of level q are numbered from lev_end[q - 1] to lev_end[q] - 1; level q
+    // has lev_ksteps[q] K steps in lev_splits[q] chunks, reads B from K
+    // element lev_bk[q] on and writes its partials to lev_C[q].
+    int nlev;
+    int lev_ksteps[8], lev_splits[8], lev_bk[8];
+    long long lev_end[8];
+    float* lev_C[8];
 };
 
 struct TileCoord {
-    int m0, n0, bo, split, k_lo, nk;
+    int m0, n0, bo, split, k_lo, nk, lev;
 };
 
 __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, long long t, int BN) {
     TileCoord c;
+    int splits = a.splits, ksteps = a.ksteps;
+    c.lev = 0;
+    if (a.nlev > 0) {
+        while (c.lev < a.nlev - 1 && t >= a.lev_end[c.lev]) ++c.lev;
+        if (c.lev > 0) t -= a.lev_end[c.lev - 1];
+        splits = a.lev_splits[c.lev];
+        ksteps = a.lev_ksteps[c.lev];
+    }
     const int nbk = (int)(t % a.nblocks);
     long long r = t / a.nblocks;
     const int mbk = (int)(r % a.mblocks);
     r /= a.mblocks;
-    c.bo = (int)(r / a.splits);
-    c.split = (int)(r % a.splits);
+    c.bo = (int)(r / splits);
+    c.split = (int)(r % splits);
     c.m0 = mbk * BM;
     c.n0 = nbk * BN;
-    const int chunk = (a.ksteps + a.splits - 1) / a.splits;
+    const int chunk = (ksteps + splits - 1) / splits;
     c.k_lo = c.split * chunk;
-    c.nk = max(0, min(a.ksteps, c.k_lo + chunk) - c.k_lo);
+    c.nk = max(0, min(ksteps, c.k_lo + chunk) - c.k_lo);
     return c;
 }
 
@@ -248,12 +264,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (it >= ST && !mbar_wait_or_fail(&sm.empty[s], (uint32_t)(((it / ST) - 1) & 1), fail))
                         break;
                     const int kc = (c.k_lo + i) * BK;
+                    const int kb = kc + (args.nlev > 0 ? args.lev_bk[c.lev] : 0);
                     mbar_expect_tx(&sm.full[s], stage_bytes);
                     tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, c.m0, ba);
-                    tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, c.n0, bb);
+                    tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kb, c.n0, bb);
                     if (args.nprod == 3) {
                         tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, c.m0, ba);
-                        tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, c.n0, bb);
+                        tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kb, c.n0, bb);
                     }
                     last[s] = it;
                 }
@@ -317,8 +334,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int buf = tl & 1;
             if (!mbar_wait_or_fail(&sm.acc_full[buf], (uint32_t)((tl >> 1) & 1), fail)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            float* Cb = args.C + (long long)c.bo * args.cbs +
-                        (args.splits > 1 ? (long long)c.split * args.nbo * args.cbs : 0);
+            const int nsp = args.nlev > 0 ? args.lev_splits[c.lev] : args.splits;
+            float* Cb = (args.nlev > 0 ? args.lev_C[c.lev] : args.C) + (long long)c.bo * args.cbs +
+                        (nsp > 1 ? (long long)c.split * args.nbo * args.cbs : 0);
             const int i_base = c.m0 + q * 32;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -1127,20 +1145,30 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     a.crs = swap ? 1 : Nr;
     a.ccs = swap ? Mr : 1;
     a.cbs = (long long)Mr * Nr;
-    for (int q = 0; q < kLevels; ++q) {
-        const int l = q + 2;
+    // All levels in one persistent launch: level l reads K elements
+    // [0, (l - 1) Ktot) of A's slice row and [(9 - l) Ktot, 8 Ktot) of B's,
+    // through one map per operand over the whole pitched row.
+    {
         CUtensorMap maps[4];
-        const long long kext = (l - 1) * Ktot;
-        if ((e = make_map_pitch(&maps[0], slA, kext, pitch, RpA, nba, BM)) != cudaSuccess) return e;
-        if ((e = make_map_pitch(&maps[2], slB + (kSlices + 1 - l) * Ktot, kext, pitch, RpB, nbb,
-                                BN)) != cudaSuccess)
-            return e;
+        if ((e = make_map_pitch(&maps[0], slA, pitch, pitch, RpA, nba, BM)) != cudaSuccess) return e;
+        if ((e = make_map_pitch(&maps[2], slB, pitch, pitch, RpB, nbb, BN)) != cudaSuccess) return e;
         maps[1] = maps[0];
         maps[3] = maps[2];
-        a.ksteps = (int)(kext / BK);
-        a.splits = lv.splits[q];
-        a.ntiles = tiles * lv.splits[q];
-        a.C = ws.part + lv.off[q];
+        a.nlev = kLevels;
+        long long end = 0;
+        for (int q = 0; q < kLevels; ++q) {
+            const int l = q + 2;
+            a.lev_ksteps[q] = (int)((l - 1) * Ktot / BK);
+            a.lev_splits[q] = lv.splits[q];
+            a.lev_bk[q] = (int)((kSlices + 1 - l) * Ktot);
+            end += tiles * lv.splits[q];
+            a.lev_end[q] = end;
+            a.lev_C[q] = ws.part + lv.off[q];
+        }
+        a.ksteps = a.lev_ksteps[kLevels - 1];
+        a.splits = 1;
+        a.ntiles = end;
+        a.C = ws.part;
         if (BN == 32) e = launch_tc<32>(maps, a, s);
         else if (BN == 64) e = launch_tc<64>(maps, a, s);
         else e = launch_tc<128>(maps, a, s);

@@ -121,35 +121,66 @@ __device__ __forceinline__ float clipf(double x, double c) {
     return (float)fmin(c, fmax(-c, x));
 }
 
-__global__ void k_features(const double* sq, const double* e, const double* Tq,
-                           const double* dprev, const long long* idx, long long n, int r,
-                           double s, double logr, float* X, float* jj) {
+// Element el of the state x = [t1 (o v) | T (r r)]: residual, denominator of
+// its Jacobi step and the two orbital-like energies whose sum it is
+// (singles (i, a): -eps_i and eps_a; doubles (P, Q): e_P and e_Q).
+struct ElemView {
+    double res, eP, eQ;
+};
+
+__device__ __forceinline__ ElemView elem(const double* sig1, const double* eps, const double* sq,
+                                         const double* e, int o, int v, int r, long long el) {
+    const long long ov = (long long)o * v;
+    ElemView w;
+    if (el < ov) {
+        const int i = (int)(el / v), a = (int)(el % v);
+        w.res = sig1[el];
+        w.eP = -eps[i];
+        w.eQ = eps[o + a];
+    } else {
+        const long long q = el - ov;
+        const int p = (int)(q / r), qq = (int)(q % r);
+        w.res = sq[q];
+        w.eP = e[p];
+        w.eQ = e[qq];
+    }
+    return w;
+}
+
+__global__ void k_features(const double* sig1, const double* eps, const double* sq,
+                           const double* e, const double* x, const double* dprev,
+                           const long long* idx, long long n, int o, int v, int r, double s1,
+                           double s2, double logr, float* X, float* jj) {
+    const long long ov = (long long)o * v;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long el = idx ? idx[k] : k;
-        const int p = (int)(el / r), q = (int)(el % r);
-        const double jac = -sq[el] / (e[p] + e[q]);
-        const double t = Tq[el] / s;
-        float* x = X + k * kMlpFeatures;
-        x[0] = (float)(0.5 * e[p]);
-        x[1] = (float)(0.5 * e[q]);
-        x[2] = clipf(jac / s, 10.0);
-        x[3] = dprev ? clipf(dprev[el] / s, 10.0) : 0.f;
-        x[4] = (float)(copysign(log1p(fabs(t)), t) * 0.2);
-        x[5] = (float)(0.1 * logr);
-        x[6] = (float)(0.5 * fabs(e[p] - e[q]));
-        x[7] = 1.f;
+        const ElemView w = elem(sig1, eps, sq, e, o, v, r, el);
+        const bool singles = el < ov;
+        const double s = singles ? s1 : s2;
+        const double jac = -w.res / (w.eP + w.eQ);
+        const double t = x[el] / s;
+        float* f = X + k * kMlpFeatures;
+        f[0] = (float)(0.5 * w.eP);
+        f[1] = (float)(0.5 * w.eQ);
+        f[2] = clipf(jac / s, 10.0);
+        f[3] = dprev ? clipf(dprev[el] / s, 10.0) : 0.f;
+        f[4] = (float)(copysign(log1p(fabs(t)), t) * 0.2);
+        f[5] = (float)(0.1 * logr);
+        f[6] = (float)(0.5 * fabs(w.eP - w.eQ));
+        f[7] = singles ? -1.f : 1.f;
         jj[k] = (float)(jac / s);
     }
 }
 
-__global__ void k_apply(const double* sq, const double* e, const float* y, int r, double* step) {
-    const long long tot = (long long)r * r;
+__global__ void k_apply(const double* sig1, const double* eps, const double* sq, const double* e,
+                        const float* y, int o, int v, int r, double* step) {
+    const long long tot = (long long)o * v + (long long)r * r;
     for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < tot;
          el += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(el / r), q = (int)(el % r);
+        const ElemView w = elem(sig1, eps, sq, e, o, v, r, el);
         const double f = 1.0 + fmin(4.0, fmax(-0.95, (double)y[el]));
-        step[el] = -sq[el] / (e[p] + e[q]) * f;
+        step[el] = -w.res / (w.eP + w.eQ) * f;
     }
 }
 
@@ -162,17 +193,20 @@ unsigned long long splitmix(unsigned long long& s) {
 
 }  // namespace
 
-cudaError_t mlp_features(const double* sq, const double* e, const double* Tq,
-                         const double* dprev, const long long* idx, long long n, int r,
-                         double s, double log_rnorm, float* X, float* jj, cudaStream_t st) {
-    k_features<<<nbl(n), NT, 0, st>>>(sq, e, Tq, dprev, idx, n, r, s, log_rnorm, X, jj);
+cudaError_t mlp_features(const double* sig1, const double* eps, const double* sq,
+                         const double* e, const double* x, const double* dprev,
+                         const long long* idx, long long n, int o, int v, int r, double s1,
+                         double s2, double log_rnorm, float* X, float* jj, cudaStream_t st) {
+    k_features<<<nbl(n), NT, 0, st>>>(sig1, eps, sq, e, x, dprev, idx, n, o, v, r, s1, s2,
+                                      log_rnorm, X, jj);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t mlp_apply(const double* sq, const double* e, const float* y, int r, double* step,
-                      cudaStream_t st) {
-    k_apply<<<nbl((long long)r * r), NT, 0, st>>>(sq, e, y, r, step);
+cudaError_t mlp_apply(const double* sig1, const double* eps, const double* sq, const double* e,
+                      const float* y, int o, int v, int r, double* step, cudaStream_t st) {
+    k_apply<<<nbl((long long)o * v + (long long)r * r), NT, 0, st>>>(sig1, eps, sq, e, y, o, v, r,
+                                                                     step);
     count_launches(1);
     return cudaGetLastError();
 }

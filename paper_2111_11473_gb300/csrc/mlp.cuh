@@ -52,17 +52,22 @@ struct Mlp {
     float* b3() const { return w3() + H; }
 };
 
-// Features of the working-basis elements for one solver iteration.
+// Features of the elements of the solver state x = [t1 (o v) | T (r r)] for
+// one iteration (T in the working basis).
+//   sig1 o x v  singles residual;  eps  o + v orbital energies
 //   sq   r x r  projected residual C^T sigma C;   e  r  working-basis eigenvalues
-//   Tq   r x r  current T;  dprev r x r  previous step (x_k - x_{k-1}), or null
-//   idx  element indices (p * r + q) or null for all r^2 elements
-// X (n x F) features, jj (n) scaled Jacobi step; s = RMS of the Jacobi step.
-cudaError_t mlp_features(const double* sq, const double* e, const double* Tq,
-                         const double* dprev, const long long* idx, long long n, int r,
-                         double s, double log_rnorm, float* X, float* jj, cudaStream_t st);
+//   x    state;  dprev  previous step (x_k - x_{k-1}), or null
+//   idx  element indices into x, or null for all o v + r^2 elements
+// X (n x F) features, jj (n) scaled Jacobi step; s1, s2 = RMS of the singles
+// and doubles Jacobi steps.
+cudaError_t mlp_features(const double* sig1, const double* eps, const double* sq,
+                         const double* e, const double* x, const double* dprev,
+                         const long long* idx, long long n, int o, int v, int r, double s1,
+                         double s2, double log_rnorm, float* X, float* jj, cudaStream_t st);
 
-// step[k] = -sq/(e_P + e_Q) * (1 + clamp(y)) for all r^2 elements.
-cudaError_t mlp_apply(const double* sq, const double* e, const float* y, int r, double* step,
-                      cudaStream_t st);
+// step[el] = (Jacobi step of el) * (1 + clamp(y[el], -0.95, 4)) for every
+// element of the state.
+cudaError_t mlp_apply(const double* sig1, const double* eps, const double* sq, const double* e,
+                      const float* y, int o, int v, int r, double* step, cudaStream_t st);
 
 }  // namespace thc

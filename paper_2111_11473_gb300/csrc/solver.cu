@@ -374,18 +374,22 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             THC_TRY(xprev.alloc(len));
             THC_TRY(saved_x.alloc(len));
             THC_TRY(saved_j.alloc(len));
-            THC_TRY(dprev.alloc(rr));
-            THC_TRY(smlp.alloc(rr));
+            THC_TRY(dprev.alloc(len));
+            THC_TRY(smlp.alloc(len));
         }
     }
-    if (use_mlp && feat.n < (size_t)rr * kMlpFeatures) {
-        THC_TRY(feat.alloc((size_t)rr * kMlpFeatures));
-        THC_TRY(jjb.alloc(rr));
-        THC_TRY(yb.alloc(rr));
+    if (use_mlp && feat.n < (size_t)len * kMlpFeatures) {
+        THC_TRY(feat.alloc((size_t)len * kMlpFeatures));
+        THC_TRY(jjb.alloc(len));
+        THC_TRY(yb.alloc(len));
     }
     n_rec = 0;
-    if (nrec > 0 && cap_rec < nrec * max_iter) {
-        cap_rec = nrec * max_iter;
+    // Pairs per iteration: nrec doubles elements and a quarter as many
+    // singles elements (all of them if there are fewer).
+    const long long nrec1 = nrec > 0 ? std::min<long long>(ov, (nrec + 3) / 4) : 0;
+    const long long nrec_it = nrec + nrec1;
+    if (nrec > 0 && cap_rec < nrec_it * max_iter) {
+        cap_rec = nrec_it * max_iter;
         THC_TRY(recX.alloc((size_t)cap_rec * kMlpFeatures));
         THC_TRY(recJ.alloc(cap_rec));
         THC_TRY(recT.alloc(cap_rec));
@@ -393,7 +397,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         THC_TRY(recS.alloc(cap_rec));
         THC_TRY(recIdx.alloc(cap_rec));
     }
-    std::vector<long long> hidx(nrec);
+    std::vector<long long> hidx(nrec_it);
     unsigned long long rng = 0x2545F4914F6CDD1DULL ^ (unsigned long long)opts.record_seed;
     bool have_prev = false, last_was_mlp = false, mlp_off = false;
     double last_norm = resume_last_norm, rho_plain = resume_rho;
@@ -472,7 +476,10 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             last_was_mlp = false;
             // A proposal stands only if the residual norm drops, and by at
             // least the factor the last plain Jacobi + DIIS iteration achieved.
-            if (norm < last_norm * std::min(1.0, rho_plain)) {
+            const bool accept = opts.mlp_accept == 2 ||
+                                (opts.mlp_accept == 1 ? norm < last_norm
+                                                      : norm < last_norm * std::min(1.0, rho_plain));
+            if (accept) {
                 ++n_acc;
             } else {
                 // Rejected: replace the proposal in the DIIS history by the
@@ -509,46 +516,52 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
         THC_CUDA(cudaGetLastError());
         bool mlp_used = false;
         if ((nrec > 0 || use_mlp) && it >= 2) {
-            // scale of this iteration's doubles Jacobi step, previous step
+            // scales of this iteration's singles and doubles Jacobi steps,
+            // previous step
+            k_multidot<<<1, 256, 0, st>>>(step.p, step.p, ov, dots.p + 7);
             k_multidot<<<1, 256, 0, st>>>(step.p + ov, step.p + ov, rr, dots.p + 8);
-            k_sub<<<nb(rr), 256, 0, st>>>(x.p + ov, xprev.p + ov, rr, dprev.p);
-            count_launches(2);
+            k_sub<<<nb(len), 256, 0, st>>>(x.p, xprev.p, len, dprev.p);
+            count_launches(3);
             THC_CUDA(cudaGetLastError());
-            double ss = 0;
-            THC_CUDA(cudaMemcpyAsync(&ss, dots.p + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+            double ss[2] = {0, 0};
+            THC_CUDA(cudaMemcpyAsync(ss, dots.p + 7, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
             THC_CUDA(cudaStreamSynchronize(st));
-            const double sc = std::max(std::sqrt(ss / (double)rr), 1e-300);
+            const double sc1 = std::max(std::sqrt(ss[0] / (double)ov), 1e-300);
+            const double sc = std::max(std::sqrt(ss[1] / (double)rr), 1e-300);
             const double lr = std::log10(std::max(norm, 1e-300));
             const double* dp = have_prev ? dprev.p : nullptr;
-            if (nrec > 0 && n_rec + nrec <= cap_rec) {
-                for (long long k = 0; k < nrec; ++k) {
+            if (nrec > 0 && n_rec + nrec_it <= cap_rec) {
+                for (long long k = 0; k < nrec_it; ++k) {
                     rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17;
-                    hidx[k] = (long long)(rng % (unsigned long long)rr);
+                    hidx[k] = k < nrec ? ov + (long long)(rng % (unsigned long long)rr)
+                                       : (long long)(rng % (unsigned long long)ov);
                 }
                 long long* di = recIdx.p + n_rec;
-                THC_CUDA(cudaMemcpyAsync(di, hidx.data(), sizeof(long long) * nrec,
+                THC_CUDA(cudaMemcpyAsync(di, hidx.data(), sizeof(long long) * nrec_it,
                                          cudaMemcpyHostToDevice, st));
-                THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, di, nrec, r, sc, lr,
-                                      recX.p + n_rec * kMlpFeatures, recJ.p + n_rec, st));
-                k_gather64<<<nb(nrec), 256, 0, st>>>(x.p + ov, di, nrec, recTk.p + n_rec);
+                THC_CUDA(mlp_features(eng.sig1.p, epsd.p, sq.p, e.p, x.p, dp, di, nrec_it, o, v, r,
+                                      sc1, sc, lr, recX.p + n_rec * kMlpFeatures, recJ.p + n_rec,
+                                      st));
+                k_gather64<<<nb(nrec_it), 256, 0, st>>>(x.p, di, nrec_it, recTk.p + n_rec);
                 k_fill64<<<nb(nrec), 256, 0, st>>>(recS.p + n_rec, nrec, sc);
-                count_launches(2);
+                k_fill64<<<nb(nrec1), 256, 0, st>>>(recS.p + n_rec + nrec, nrec1, sc1);
+                count_launches(3);
                 THC_CUDA(cudaGetLastError());
                 // hidx is reused next iteration: the copy must finish first
                 THC_CUDA(cudaStreamSynchronize(st));
-                n_rec += nrec;
+                n_rec += nrec_it;
             }
             if (use_mlp && !mlp_off) {
-                THC_CUDA(mlp_features(sq.p, e.p, x.p + ov, dp, nullptr, rr, r, sc, lr, feat.p,
-                                      jjb.p, st));
+                THC_CUDA(mlp_features(eng.sig1.p, epsd.p, sq.p, e.p, x.p, dp, nullptr, len, o, v,
+                                      r, sc1, sc, lr, feat.p, jjb.p, st));
                 // Rows are independent: at most 2^20 per pass bounds the
                 // network's activation buffers (4 x rows x width floats).
                 const long long chunk = 1LL << 20;
-                for (long long r0 = 0; r0 < rr; r0 += chunk)
-                    THC_TRY(mlp->forward(feat.p + r0 * kMlpFeatures, std::min(chunk, rr - r0),
+                for (long long r0 = 0; r0 < len; r0 += chunk)
+                    THC_TRY(mlp->forward(feat.p + r0 * kMlpFeatures, std::min(chunk, len - r0),
                                          yb.p + r0));
-                THC_CUDA(mlp_apply(sq.p, e.p, yb.p, r, smlp.p, st));
-                k_add<<<nb(rr), 256, 0, st>>>(x.p + ov, smlp.p, rr, xnew.p + ov);
+                THC_CUDA(mlp_apply(eng.sig1.p, epsd.p, sq.p, e.p, yb.p, o, v, r, smlp.p, st));
+                k_add<<<nb(len), 256, 0, st>>>(x.p, smlp.p, len, xnew.p);
                 count_launches(1);
                 THC_CUDA(cudaGetLastError());
                 mlp_used = true;
@@ -561,9 +574,9 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
             have_prev = true;
         }
         // DIIS error vector = the step actually taken: the proposal replaces
-        // the doubles part of the Jacobi step when one is made.
+        // the Jacobi step when one is made.
         if (mlp_used)
-            THC_CUDA(cudaMemcpyAsync(step.p + ov, smlp.p, sizeof(double) * rr,
+            THC_CUDA(cudaMemcpyAsync(step.p, smlp.p, sizeof(double) * len,
                                      cudaMemcpyDeviceToDevice, st));
         last_norm = norm;
         last_was_mlp = mlp_used;
@@ -584,7 +597,7 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
     THC_CUDA(cudaMemcpyAsync(t1_io, eng.t1d.p, sizeof(double) * ov, cudaMemcpyDefault, st));
     THC_CUDA(cudaStreamSynchronize(st));
     if (converged && n_rec > 0) {
-        k_targets<<<nb(n_rec), 256, 0, st>>>(x.p + ov, recIdx.p, recTk.p, recS.p, n_rec, recT.p);
+        k_targets<<<nb(n_rec), 256, 0, st>>>(x.p, recIdx.p, recTk.p, recS.p, n_rec, recT.p);
         count_launches(1);
         THC_CUDA(cudaGetLastError());
         THC_CUDA(cudaStreamSynchronize(st));

@@ -61,3 +61,52 @@ def test_learned_vs_plain(trained, seed):
     assert abs(c["energy_diff"]) < 1e-6
     assert l["mlp_rejected"] <= 2
     assert l["iters"] <= p["iters"] + 4
+
+
+def _net_with_bias(pkg, b3):
+    """A network whose output is the constant b3 (all other weights zero)."""
+    net = pkg.Mlp(hidden=64, seed=3, bf16=False)
+    p = np.zeros(len(net.get_params()), dtype=np.float32)
+    p[-1] = b3
+    net.set_params(p)
+    return net
+
+
+def test_accepted_identity_proposals_reproduce_plain_solve():
+    """Zero network output: every proposal is exactly the Jacobi step.  Forced
+    acceptance (mlp_accept = 2) then goes through the accepted branch at every
+    iteration from the second on, storing the proposal as DIIS error vector,
+    and must reproduce the plain Jacobi + DIIS solve bit for bit."""
+    import __graft_entry__ as g
+    g.build()
+    import paper_2111_11473_gb300 as pkg
+    s = make_system(6, 30, 60, 180, 90, 101)
+    net = _net_with_bias(pkg, 0.0)
+    with pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z) as ctx:
+        h0, h1 = [], []
+        Z0, t0, r0 = ctx.solve(r_tol=1e-9, max_iter=60, history=h0)
+        Z1, t1, r1 = ctx.solve(r_tol=1e-9, max_iter=60, history=h1, use_mlp=True, mlp=net,
+                               mlp_accept=2)
+    net.close()
+    print(f"\nplain {r0.iters} iters, forced-accept identity {r1.iters} iters, "
+          f"accepted {r1.mlp_accepted}")
+    assert r1.mlp_accepted == r1.iters - 2 and r1.mlp_rejected == 0
+    assert r1.iters == r0.iters
+    assert [h[:2] for h in h0] == [h[:2] for h in h1]
+    assert np.array_equal(Z0, Z1) and np.array_equal(t0, t1) and r0.energy == r1.energy
+
+
+def test_accepted_scaled_proposals_keep_the_converged_energy():
+    """Every step scaled by 1.5 and accepted: DIIS stores the scaled steps as
+    error vectors and the solve still converges to the plain energy."""
+    import paper_2111_11473_gb300 as pkg
+    s = make_system(6, 30, 60, 180, 90, 101)
+    net = _net_with_bias(pkg, 0.5)
+    with pkg.Context(s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z) as ctx:
+        _, _, r0 = ctx.solve(r_tol=1e-9, max_iter=80)
+        _, _, r1 = ctx.solve(r_tol=1e-9, max_iter=80, use_mlp=True, mlp=net, mlp_accept=2)
+    net.close()
+    print(f"\nplain {r0.iters} iters, scaled proposals {r1.iters} iters "
+          f"(accepted {r1.mlp_accepted}), dE {r1.energy - r0.energy:.2e}")
+    assert r1.status == "THC_OK" and r1.mlp_accepted > 0
+    assert abs(r1.energy - r0.energy) < 1e-9
