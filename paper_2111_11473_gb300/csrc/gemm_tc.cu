@@ -1047,20 +1047,358 @@ void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slic
     *expo_elems = (size_t)((Rm + Rn) * nbo);
 }
 
+// ---------------------------------------------------------------------------
+// Fused float64 product: one persistent kernel per product.  For every
+// 64-wide K step it loads the 8 slices of a 128-row A tile and of a 64-row B
+// tile once and issues the MMAs of all 36 digit pairs (t, u), t + u <= 9,
+// into eight level accumulators in tensor memory (level l = t + u at columns
+// (l - 2) 64 .. (l - 2) 64 + 63: all 512 columns).  A level accumulator
+// collects (l - 1) 64 products of |a_t b_u| < 2^14 per K step, so it is
+// drained after c_l = floor(16 / (l - 1)) steps (at most 1024 products: an
+// exact float32 integer) and restarted.  The epilogue warps combine every
+// drain exactly in registers (levels 2-6 in int64, 7-9 in float32 below
+// 2^-57 of the product's scale, as in k_f64_accumulate) and write the tile
+// once in float64: no float32 level outputs go through memory.
+// Roles: warp 0 streams slices with TMA (B slices of a K step double-
+// buffered, A slices through a 4-deep ring), warp 1 issues the MMAs, warps
+// 2-9 drain: warp w reads TMEM lanes 32 (w % 4) .. + 31 and columns
+// 32 ((w - 2) / 4) .. + 31 of a level.  Every wait is bounded.
+namespace {
+
+constexpr int FN = 64;                    // tile columns (B rows)
+constexpr int FA = 4;                     // A-slice ring depth
+constexpr int kF64EpiWarps = 8;
+constexpr int kF64Threads = 64 + 32 * kF64EpiWarps;
+
+struct F64Smem {
+    __nv_bfloat16 b[2][kSlices][FN * BK];   // B slices of one K step
+    __nv_bfloat16 a[FA][BM * BK];           // A slices, one per ring entry
+    uint64_t bfull[2], bempty[2], afull[FA], aempty[FA];
+    uint64_t lfull[kLevels], lempty[kLevels];
+    uint64_t drain;
+    uint32_t tmem;
+    int fail;
+};
+
+struct F64Args {
+    int M, N;                // real accumulator rows (A side) and columns (B side)
+    int nbo, mblocks, nblocks, ksteps, splits;
+    long long ntiles;        // mblocks * nblocks * nbo * splits
+    int a_bcast, b_bcast;
+    long long Ktot;          // slice segment length
+    const int* eA;           // row exponent fields [bo][RpA], [bo][RpB]
+    const int* eB;
+    int RpA, RpB;
+    double* C;               // output, or float64 partials when splits > 1
+    long long crs, ccs, cbs;
+    double alpha, beta;
+    int* err;
+};
+
+struct F64Coord {
+    int m0, n0, bo, split, k_lo, nk;
+};
+
+__device__ __forceinline__ F64Coord f64_coord(const F64Args& a, long long t) {
+    F64Coord c;
+    const int nbk = (int)(t % a.nblocks);
+    long long r = t / a.nblocks;
+    const int mbk = (int)(r % a.mblocks);
+    r /= a.mblocks;
+    c.bo = (int)(r / a.splits);
+    c.split = (int)(r % a.splits);
+    c.m0 = mbk * BM;
+    c.n0 = nbk * FN;
+    const int chunk = (a.ksteps + a.splits - 1) / a.splits;
+    c.k_lo = c.split * chunk;
+    c.nk = max(0, min(a.ksteps, c.k_lo + chunk) - c.k_lo);
+    return c;
+}
+
+// K steps per exact chunk of level q + 2: (l - 1) 64 c <= 1024.
+__device__ __forceinline__ int f64_chunk_steps(int q) { return 16 / (q + 1); }
+
+__global__ void __launch_bounds__(kF64Threads, 1)
+    k_gemm_f64s(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const F64Args args) {
+    extern __shared__ __align__(1024) unsigned char f64_raw[];
+    F64Smem& sm = *reinterpret_cast<F64Smem*>((reinterpret_cast<uintptr_t>(f64_raw) + 1023) &
+                                              ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int* fail = &sm.fail;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&sm.bfull[s], 1);
+            mbar_init(&sm.bempty[s], 1);
+        }
+        for (int s = 0; s < FA; ++s) {
+            mbar_init(&sm.afull[s], 1);
+            mbar_init(&sm.aempty[s], 1);
+        }
+        for (int q = 0; q < kLevels; ++q) {
+            mbar_init(&sm.lfull[q], 1);
+            mbar_init(&sm.lempty[q], kF64EpiWarps);
+        }
+        mbar_init(&sm.drain, 1);
+        sm.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&sm.tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = sm.tmem;
+    const long long Kt = args.Ktot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            long long bit = 0, ait = 0;
+            long long blast[2] = {-1, -1}, alast[FA];
+            for (int s = 0; s < FA; ++s) alast[s] = -1;
+            for (long long t = blockIdx.x; t < args.ntiles && !*fail; t += gridDim.x) {
+                const F64Coord c = f64_coord(args, t);
+                const int ba = args.a_bcast ? 0 : c.bo, bb = args.b_bcast ? 0 : c.bo;
+                bool ok = true;
+                for (int i = 0; i < c.nk && ok; ++i) {
+                    const int kc = (c.k_lo + i) * BK;
+                    const int bs = (int)(bit & 1);
+                    if (bit >= 2 && !mbar_wait_or_fail(&sm.bempty[bs], (uint32_t)(((bit >> 1) - 1) & 1), fail)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&sm.bfull[bs], (uint32_t)(kSlices * FN * BK * 2));
+                    for (int u = 1; u <= kSlices; ++u)   // slice u sits in segment 8 - u
+                        tma_load_3d(sm.b[bs][u - 1], &tmB, &sm.bfull[bs],
+                                    (int)((kSlices - u) * Kt) + kc, c.n0, bb);
+                    blast[bs] = bit++;
+                    for (int ts = 1; ts <= kSlices; ++ts) {
+                        const int as = (int)(ait % FA);
+                        if (ait >= FA && !mbar_wait_or_fail(&sm.aempty[as], (uint32_t)(((ait / FA) - 1) & 1), fail)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&sm.afull[as], (uint32_t)(BM * BK * 2));
+                        tma_load_3d(sm.a[as], &tmA, &sm.afull[as], (int)((ts - 1) * Kt) + kc, c.m0, ba);
+                        alast[as] = ait++;
+                    }
+                }
+                if (!ok) break;
+            }
+            // Every load issued has landed before the CTA exits.
+            for (int s = 0; s < 2; ++s)
+                if (blast[s] >= 0) mbar_wait(&sm.bfull[s], (uint32_t)((blast[s] >> 1) & 1));
+            for (int s = 0; s < FA; ++s)
+                if (alast[s] >= 0) mbar_wait(&sm.afull[s], (uint32_t)((alast[s] / FA) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = instr_desc(BM, FN);
+            long long bit = 0, ait = 0;
+            // Per level q (bit q): usedm = a chunk has been started before
+            // (its successor waits for the drain), parm = parity of the next
+            // lempty wait, inchunk = the current chunk has K steps already.
+            unsigned usedm = 0, parm = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < args.ntiles && ok && !*fail; t += gridDim.x) {
+                const F64Coord c = f64_coord(args, t);
+                int cnt[kLevels];
+#pragma unroll
+                for (int q = 0; q < kLevels; ++q) cnt[q] = 0;
+                for (int i = 0; i < c.nk && ok; ++i) {
+                    const int bs = (int)(bit & 1);
+                    if (!mbar_wait_or_fail(&sm.bfull[bs], (uint32_t)((bit >> 1) & 1), fail)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    unsigned startedm = 0;
+#pragma unroll
+                    for (int q = 0; q < kLevels; ++q)
+                        if (cnt[q] > 0) startedm |= 1u << q;
+                    for (int ts = 1; ts <= kSlices && ok; ++ts) {
+                        const int as = (int)(ait % FA);
+                        if (!mbar_wait_or_fail(&sm.afull[as], (uint32_t)((ait / FA) & 1), fail)) {
+                            ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint32_t aa = smem_u32(sm.a[as]);
+                        for (int u = 1; u <= kSlices + 1 - ts; ++u) {
+                            const int q = ts + u - 2;
+                            const unsigned qb = 1u << q;
+                            const bool started = (startedm & qb) != 0;
+                            if (!started) {
+                                // a new chunk: the previous one has been drained
+                                if ((usedm & qb) &&
+                                    !mbar_wait_or_fail(&sm.lempty[q], (parm >> q) & 1u, fail)) {
+                                    ok = false;
+                                    break;
+                                }
+                                if (usedm & qb) parm ^= qb;
+                                usedm |= qb;
+                                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                            }
+                            const uint32_t bb = smem_u32(sm.b[bs][u - 1]);
+                            const uint32_t dst = tmem + (uint32_t)(q * FN);
+#pragma unroll
+                            for (int kk = 0; kk < BK / UK; ++kk) {
+                                const uint32_t off = kk * UK * 2;
+                                mma_bf16(dst, smem_desc(aa + off), smem_desc(bb + off), idesc,
+                                         (started || kk > 0) ? 1u : 0u);
+                            }
+                            startedm |= qb;
+                        }
+                        mma_commit(&sm.aempty[as]);
+                        ++ait;
+                    }
+                    if (!ok) break;
+                    mma_commit(&sm.bempty[bs]);
+                    ++bit;
+#pragma unroll
+                    for (int q = 0; q < kLevels; ++q) {
+                        ++cnt[q];
+                        if (cnt[q] == f64_chunk_steps(q) || i == c.nk - 1) {
+                            mma_commit(&sm.lfull[q]);
+                            cnt[q] = 0;
+                        }
+                    }
+                }
+            }
+            // All MMAs issued have completed before TMEM is freed.
+            mma_commit(&sm.drain);
+            mbar_wait(&sm.drain, 0);
+        }
+    } else {
+        // Epilogue: drains and the float64 combination of the tile.
+        const int q4 = warp & 3, half = (warp - 2) >> 2;
+        unsigned dpar = 0;   // bit q: parity of the next lfull wait of level q
+        for (long long t = blockIdx.x; t < args.ntiles; t += gridDim.x) {
+            const F64Coord c = f64_coord(args, t);
+            long long H[32];
+            float T[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                H[j] = 0;
+                T[j] = 0.f;
+            }
+            int cnt[kLevels];
+#pragma unroll
+            for (int q = 0; q < kLevels; ++q) cnt[q] = 0;
+            bool ok = true;
+            for (int i = 0; i < c.nk && ok; ++i) {
+#pragma unroll
+                for (int q = 0; q < kLevels; ++q) {
+                    ++cnt[q];
+                    if (!ok || (cnt[q] != f64_chunk_steps(q) && i != c.nk - 1)) continue;
+                    cnt[q] = 0;
+                    if (!mbar_wait_or_fail(&sm.lfull[q], (dpar >> q) & 1u, fail)) {
+                        ok = false;
+                        continue;
+                    }
+                    dpar ^= 1u << q;
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    uint32_t r[32];
+                    const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) +
+                                           (uint32_t)(q * FN + half * 32);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+                        " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+                          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+                          "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.lempty[q]);
+                    const int l = q + 2;
+                    if (l <= 6) {
+                        const int sh = 7 * (6 - l);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            H[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                    } else {
+                        const float w = l == 7 ? 1.f : (l == 8 ? 0.0078125f : 0.00006103515625f);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) T[j] = fmaf(__uint_as_float(r[j]), w, T[j]);
+                    }
+                }
+            }
+            if (!ok) break;
+            // C(i, j) = alpha 2^(e_r + e_c - 42) (H + 2^-7 T) [+ beta C]
+            const int i = c.m0 + q4 * 32 + lane;
+            if (i >= args.M) continue;
+            const int fa = args.eA[(long long)(args.a_bcast ? 0 : c.bo) * args.RpA + i];
+            const int* eb = args.eB + (long long)(args.b_bcast ? 0 : c.bo) * args.RpB;
+            double* Cb = args.C + (long long)c.bo * args.cbs +
+                         (args.splits > 1 ? (long long)c.split * args.nbo * args.cbs : 0) +
+                         (long long)i * args.crs;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int col = c.n0 + half * 32 + j;
+                if (col >= args.N) continue;
+                const int fb = eb[col];
+                double v = 0.0;
+                if (fa > 0 && fb > 0)
+                    v = fma((double)T[j], 0.0078125, (double)H[j]) *
+                        pow2((fa - 1022) + (fb - 1022) - 42);
+                double* p = Cb + (long long)col * args.ccs;
+                if (args.splits > 1) *p = v;
+                else *p = (args.beta != 0.0 ? args.beta * *p : 0.0) + args.alpha * v;
+            }
+        }
+    }
+    __syncthreads();
+    if (sm.fail && threadIdx.x == 0) atomicExch(args.err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(512));
+}
+
+// C = beta C + alpha sum_split part[split] (float64 split-K partials of the
+// fused kernel, in accumulator orientation: element (b, i, j) at
+// part[(split nbo + b) M N + i N + j]).
+__global__ void k_f64_splitsum(const double* part, int splits, int nbo, int M, int N, double* C,
+                               long long crs, long long ccs, long long cbs, double alpha,
+                               double beta) {
+    const long long MN = (long long)M * N, tot = MN * nbo;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e / MN);
+        const long long r = e % MN;
+        const int i = (int)(r / N), j = (int)(r % N);
+        double s = 0.0;
+        for (int sp = 0; sp < splits; ++sp) s += part[(long long)sp * tot + e];
+        double* p = C + (long long)b * cbs + (long long)i * crs + (long long)j * ccs;
+        *p = (beta != 0.0 ? beta * *p : 0.0) + alpha * s;
+    }
+}
+
+}  // namespace
+
 cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     const bool swap = g.N > g.M;
     const int Mr = swap ? g.N : g.M, Nr = swap ? g.M : g.N;
-    int BN = 128;
-    if (Nr <= 32) BN = 32;
-    else if (Nr <= 64) BN = 64;
     const long long Kp = rup(std::max(g.K, 1), BK);
     const int nb = g.batch;
     const int nbo = g.reduce ? 1 : nb;
     const long long Ktot = g.reduce ? Kp * nb : Kp;
-    const long long RpA = rup(Mr, BM), RpB = rup(Nr, BN);
+    const long long RpA = rup(Mr, BM), RpB = rup(Nr, FN);
     View<double> va = g.A, vb{g.B.p, g.B.cs, g.B.rs};
     long long sa = g.sAb, sb = g.sBb;
     if (swap) {
@@ -1074,37 +1412,18 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     const long long sliceA = RpA * pitch * nba, sliceB = RpB * pitch * nbb;
     if ((size_t)(sliceA + sliceB) > ws.slice_elems) return cudaErrorMemoryAllocation;
     if ((size_t)(RpA * nba + RpB * nbb) > ws.expo_elems) return cudaErrorMemoryAllocation;
-    const int mblocks = (int)(RpA / BM), nblocks = (int)(RpB / BN);
+    if (pitch > INT32_MAX) return cudaErrorMemoryAllocation;
+    const int mblocks = (int)(RpA / BM), nblocks = (int)(RpB / FN);
     const long long tiles = (long long)mblocks * nblocks * nbo;
-    const long long MNb = (long long)Mr * Nr * nbo;
-    // Splits per level: exact K chunks, more when the tiles alone do not
-    // fill the GPU; every level's float32 outputs must fit the partial
-    // buffer together (one float64 pass).
-    F64Levels lv{};
-    long long used = 0;
-    for (int q = 0; q < kLevels; ++q) {
-        const int l = q + 2;
-        const int exact = level_splits(l, Ktot);
-        const int ksteps = (int)((l - 1) * Ktot / BK);
-        int sp = exact;
-        if (tiles * sp < 152 && ksteps >= 8)
-            sp = std::max<int>(sp, (int)std::min<long long>({(152 + tiles - 1) / tiles,
-                                                             ksteps / 4, 32}));
-        lv.splits[q] = sp;
-        lv.off[q] = used;
-        used += (long long)sp * MNb;
-    }
-    for (int q = kLevels - 1; q >= 0 && (size_t)used > ws.part_elems; --q) {
-        // drop the balancing splits, deepest levels first
-        const int exact = level_splits(q + 2, Ktot);
-        used -= (long long)(lv.splits[q] - exact) * MNb;
-        lv.splits[q] = exact;
-    }
-    if ((size_t)used > ws.part_elems || lv.splits[0] > 2048) return cudaErrorMemoryAllocation;
-    used = 0;
-    for (int q = 0; q < kLevels; ++q) {
-        lv.off[q] = used;
-        used += (long long)lv.splits[q] * MNb;
+    const int ksteps = (int)(Ktot / BK);
+    const long long sms = device_sms();
+    // Split K when the tiles alone leave SMs idle; the float64 partials of
+    // the splits share the workspace of the float32 level outputs.
+    int splits = 1;
+    if (tiles < sms && ksteps >= 4) {
+        splits = (int)std::min<long long>({(sms + tiles - 1) / tiles, ksteps / 2, 32});
+        const long long per = (long long)Mr * Nr * nbo;
+        while (splits > 1 && (size_t)(per * splits) > ws.part_elems / 2) --splits;
     }
 
     __nv_bfloat16* slA = ws.slices;
@@ -1129,69 +1448,58 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
         count_launches(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    TcArgs a{};
+    CUtensorMap mA, mB;
+    if ((e = make_map_pitch(&mA, slA, pitch, pitch, RpA, nba, BM)) != cudaSuccess) return e;
+    if ((e = make_map_pitch(&mB, slB, pitch, pitch, RpB, nbb, FN)) != cudaSuccess) return e;
+    F64Args a{};
     a.M = Mr;
     a.N = Nr;
     a.nbo = nbo;
-    a.nprod = 1;
-    a.a_bcast = a_bc ? 1 : 0;
-    a.b_bcast = b_bc ? 1 : 0;
-    a.err = ws.err;
-    a.alpha = 1.f;
-    a.beta = 0.f;
     a.mblocks = mblocks;
     a.nblocks = nblocks;
-    // Level outputs in the orientation of C (element (m, n) at m N + n).
-    a.crs = swap ? 1 : Nr;
-    a.ccs = swap ? Mr : 1;
-    a.cbs = (long long)Mr * Nr;
-    // All levels in one persistent launch: level l reads K elements
-    // [0, (l - 1) Ktot) of A's slice row and [(9 - l) Ktot, 8 Ktot) of B's,
-    // through one map per operand over the whole pitched row.
-    {
-        CUtensorMap maps[4];
-        if ((e = make_map_pitch(&maps[0], slA, pitch, pitch, RpA, nba, BM)) != cudaSuccess) return e;
-        if ((e = make_map_pitch(&maps[2], slB, pitch, pitch, RpB, nbb, BN)) != cudaSuccess) return e;
-        maps[1] = maps[0];
-        maps[3] = maps[2];
-        a.nlev = kLevels;
-        long long end = 0;
-        for (int q = 0; q < kLevels; ++q) {
-            const int l = q + 2;
-            a.lev_ksteps[q] = (int)((l - 1) * Ktot / BK);
-            a.lev_splits[q] = lv.splits[q];
-            a.lev_bk[q] = (int)((kSlices + 1 - l) * Ktot);
-            end += tiles * lv.splits[q];
-            a.lev_end[q] = end;
-            a.lev_C[q] = ws.part + lv.off[q];
-        }
-        a.ksteps = a.lev_ksteps[kLevels - 1];
-        a.splits = 1;
-        a.ntiles = end;
-        a.C = ws.part;
-        if (BN == 32) e = launch_tc<32>(maps, a, s);
-        else if (BN == 64) e = launch_tc<64>(maps, a, s);
-        else e = launch_tc<128>(maps, a, s);
-        if (e != cudaSuccess) return e;
+    a.ksteps = ksteps;
+    a.splits = splits;
+    a.ntiles = tiles * splits;
+    a.a_bcast = a_bc ? 1 : 0;
+    a.b_bcast = b_bc ? 1 : 0;
+    a.Ktot = Ktot;
+    a.eA = eA;
+    a.eB = eB;
+    a.RpA = (int)RpA;
+    a.RpB = (int)RpB;
+    a.alpha = g.alpha;
+    a.beta = g.beta;
+    a.err = ws.err;
+    // accumulator (i, j) is C's (m, n), or (n, m) when the operands were swapped
+    const long long crs = swap ? 1 : g.ldc, ccs = swap ? g.ldc : 1;
+    const long long cbs = g.reduce ? 0 : g.sCb;
+    double* part = reinterpret_cast<double*>(ws.part);
+    if (splits > 1) {
+        a.C = part;
+        a.crs = Nr;
+        a.ccs = 1;
+        a.cbs = (long long)Mr * Nr;
+    } else {
+        a.C = g.C;
+        a.crs = crs;
+        a.ccs = ccs;
+        a.cbs = cbs;
     }
-    const long long MN = (long long)Mr * Nr;
-    if (MN >= (1LL << 32) || nbo > 65535) return cudaErrorMemoryAllocation;
-    const dim3 rgrid((unsigned)std::min<long long>((MN + 255) / 256, 152 * 16 / nbo + 1),
-                     (unsigned)nbo);
-    int maxs = 0;
-    for (int q = 0; q < kLevels; ++q) maxs = std::max(maxs, lv.splits[q]);
-    if (maxs <= 2)
-        k_f64_accumulate<2><<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
-                                                  (int)RpA, a_bc ? 1 : 0, eB, (int)RpB,
-                                                  b_bc ? 1 : 0, g.C, g.ldc,
-                                                  g.reduce ? 0 : g.sCb, g.alpha, g.beta);
-    else
-        k_f64_accumulate<0><<<rgrid, 256, 0, s>>>(ws.part, lv, nbo, g.M, g.N, swap ? 1 : 0, eA,
-                                                  (int)RpA, a_bc ? 1 : 0, eB, (int)RpB,
-                                                  b_bc ? 1 : 0, g.C, g.ldc,
-                                                  g.reduce ? 0 : g.sCb, g.alpha, g.beta);
+    const int smem = (int)sizeof(F64Smem) + 1024;
+    if ((e = smem_optin((const void*)k_gemm_f64s, smem)) != cudaSuccess) return e;
+    const unsigned grid = (unsigned)std::min<long long>(a.ntiles, sms);
+    k_gemm_f64s<<<grid, kF64Threads, smem, s>>>(mA, mB, a);
     count_launches(1);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (splits > 1) {
+        const long long tot = (long long)Mr * Nr * nbo;
+        const unsigned blocks = (unsigned)std::min<long long>((tot + 255) / 256, sms * 16);
+        k_f64_splitsum<<<blocks, 256, 0, s>>>(part, splits, nbo, Mr, Nr, g.C, crs, ccs, cbs,
+                                              g.alpha, g.beta);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 // ---------------------------------------------------------------------------
