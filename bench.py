@@ -224,7 +224,11 @@ def _context(pkg, s, dev=None, **kw):
         tens = [torch.from_numpy(a).to(dev) for a in (s.eps_o, s.eps_v, s.Y, s.L, s.x, s.z)]
         return pkg.Context(*tens, **kw)
     ctx = pkg.Context(s.eps_o, s.eps_v, s.Y, None, s.x, s.z, n_k=s.K, **kw)
-    for k0, Lk in s.cholesky_slabs(nk=32):
+    lo, hi = 0, s.K
+    if kw.get("shard") is not None:
+        from paper_2111_11473_gb300.shard import shard_bounds
+        lo, hi = shard_bounds(s.K, *kw["shard"])
+    for k0, Lk in s.cholesky_slabs(nk=32, k_lo=lo, k_hi=hi):
         ctx.load_cholesky(k0, Lk)
         del Lk
     torch.cuda.empty_cache()
@@ -290,6 +294,51 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serial_shard_check(pkg, s, dev, stream, ctx, args):
+    """The float64 residual (tensor-core products) at the mixed solve's
+    converged point, evaluated as the sum of `args.fp64_check_shards` shard
+    contexts made one after another on this GPU, so that only a part of the
+    float64 Cholesky vectors is on the device at a time; compared with the
+    mixed residual and energy at the same point."""
+    import numpy as np
+    import torch
+    hist = []
+    Zc, t1, rep = ctx.solve(r_tol=args.solve_rtol, e_tol=1e-8, max_iter=args.max_iter,
+                            history=hist, raise_on_failure=False)
+    mixed = ctx.residual(Zc, t1)
+    ctx.close()   # the float64 shard contexts need the device memory
+    n = args.fp64_check_shards
+    parts, shards = [], []
+    for i in range(n):
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        c = _context(pkg, s, dev, precision=pkg.THC_PREC_FP64_TC, stream=stream, shard=(i, n))
+        init_s = time.perf_counter() - t0
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        parts.append(c.residual(Zc, t1))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        shards.append({"init_s": init_s, "residual_ms": e0.elapsed_time(e1),
+                       "device_gb_in_use": torch.cuda.mem_get_info(dev)[1] / 1e9 -
+                                           torch.cuda.mem_get_info(dev)[0] / 1e9})
+        c.close()
+    sig = sum(p[0] for p in parts)
+    sig1 = sum(p[1] for p in parts)
+    E = sum(p[2] for p in parts)
+    return {"mixed_solve": {"iters": rep.iters, "status": rep.status, "energy": rep.energy,
+                            "r_norm": rep.r_norm, "wall_s": rep.wall_s},
+            "fp64_residual_ms": sum(x["residual_ms"] for x in shards),
+            "shards": shards,
+            "energy_fp64": E, "energy_mixed": mixed[2], "dE_mixed_minus_fp64": mixed[2] - E,
+            "max_abs_dsigma": float(np.abs(mixed[0] - sig).max()),
+            "max_abs_sigma_fp64": float(np.abs(sig).max()),
+            "norm_dsigma1": float(np.linalg.norm(mixed[1] - sig1)),
+            "norm_sigma1_fp64": float(np.linalg.norm(sig1))}
 
 
 def run_sharded(args, pkg, dev, stream, dist, world, rank):
@@ -582,6 +631,10 @@ def main():
                     help="under torchrun: one system split over the ranks (thc_config "
                          "shard_index / shard_count), the parts summed by one NCCL "
                          "all-reduce per step (strong scaling)")
+    ap.add_argument("--fp64-check-shards", type=int, default=0,
+                    help="with --precision mixed: evaluate the float64 residual at the mixed "
+                         "solve's converged point as the sum of this many shard contexts made "
+                         "one after another (systems whose float64 Cholesky vectors do not fit)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the CUDA-core FMA rates and time 4096^3 tensor-core "
                          "products (thc_probe_alu, thc_probe_gemm), print one JSON line")
@@ -747,6 +800,8 @@ def main():
         line["fp64_vs_mixed"] = fp64_vs_mixed_iterations(pkg, s, stream, args.fp64_iters)
     if args.policy_scan:
         line["policy_scan"] = policy_scan(pkg, s, dev, stream, args)
+    if args.fp64_check_shards > 0:
+        line["fp64_check"] = serial_shard_check(pkg, s, dev, stream, ctx, args)
     ctx.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:

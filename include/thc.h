@@ -305,6 +305,9 @@ typedef struct {
                             achieved (default); 1 = any drop; 2 = always
                             accept (for tests of the accepted branch and for
                             diagnostics) */
+    int mlp_blocks;      /* blocks whose step the network scales: 1 = singles,
+                            2 = doubles, 3 or 0 = both (default); the other
+                            block keeps the Jacobi step */
 } thc_solve_opts;
 
 typedef struct {

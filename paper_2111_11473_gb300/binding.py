@@ -39,7 +39,8 @@ class ThcSolveOpts(C.Structure):
     _fields_ = [("r_tol", C.c_double), ("e_tol", C.c_double), ("max_iter", C.c_int),
                 ("diis_n", C.c_int), ("use_mlp", C.c_int), ("verbose", C.c_int),
                 ("history", C.c_void_p), ("mlp", C.c_void_p), ("record_pairs", C.c_int),
-                ("record_seed", C.c_ulonglong), ("resume", C.c_int), ("mlp_accept", C.c_int)]
+                ("record_seed", C.c_ulonglong), ("resume", C.c_int), ("mlp_accept", C.c_int),
+                ("mlp_blocks", C.c_int)]
 
 
 class ThcReport(C.Structure):
@@ -359,7 +360,7 @@ class Context:
 
     def solve(self, Zc=None, t1=None, r_tol=1e-8, e_tol=0.0, max_iter=100, diis_n=8,
               use_mlp=False, verbose=False, raise_on_failure=True, history=None, mlp=None,
-              record_pairs=0, record_seed=0, resume=False, mlp_accept=0):
+              record_pairs=0, record_seed=0, resume=False, mlp_accept=0, mlp_blocks=3):
         """Run thc_solve; Zc and t1 (numpy, updated in place) start at zero.
 
         If ``history`` is a list, (energy, |r|, seconds) per iteration is
@@ -382,6 +383,7 @@ class Context:
         opts.record_pairs, opts.record_seed = int(record_pairs), int(record_seed)
         opts.resume = int(bool(resume))
         opts.mlp_accept = int(mlp_accept)
+        opts.mlp_blocks = int(mlp_blocks)
         rep = ThcReport()
         st = self._lib.thc_solve(self._h, C.byref(opts), zc.ptr, tt.ptr, C.byref(rep))
         if history is not None:

@@ -150,6 +150,7 @@ thc_status thc_solve_opts_default(thc_solve_opts* opts) {
     opts->record_seed = 0;
     opts->resume = 0;
     opts->mlp_accept = 0;
+    opts->mlp_blocks = 3;
     return THC_OK;
 }
 
@@ -247,6 +248,8 @@ thc_status thc_solve(thc_ctx* c, const thc_solve_opts* opts, double* Zc_inout,
                                              "context evaluates one shard"});
     if (opts->mlp_accept < 0 || opts->mlp_accept > 2)
         return fail(c, {THC_ERR_ARG, "mlp_accept must be 0, 1 or 2"});
+    if (opts->mlp_blocks < 0 || opts->mlp_blocks > 3)
+        return fail(c, {THC_ERR_ARG, "mlp_blocks must be 0 .. 3"});
     if (thc::Err e = solver_of(c); !e.ok()) return fail(c, e);
     thc_report rep{};
     thc::Mlp* mlp = opts->mlp ? &opts->mlp->m : nullptr;

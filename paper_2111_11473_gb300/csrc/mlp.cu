@@ -174,12 +174,13 @@ __global__ void k_features(const double* sig1, const double* eps, const double* 
 }
 
 __global__ void k_apply(const double* sig1, const double* eps, const double* sq, const double* e,
-                        const float* y, int o, int v, int r, double* step) {
-    const long long tot = (long long)o * v + (long long)r * r;
+                        const float* y, int o, int v, int r, int blocks, double* step) {
+    const long long ov = (long long)o * v, tot = ov + (long long)r * r;
     for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < tot;
          el += (long long)gridDim.x * blockDim.x) {
         const ElemView w = elem(sig1, eps, sq, e, o, v, r, el);
-        const double f = 1.0 + fmin(4.0, fmax(-0.95, (double)y[el]));
+        const bool on = (el < ov ? (blocks & 1) : (blocks & 2)) != 0;
+        const double f = on ? 1.0 + fmin(4.0, fmax(-0.95, (double)y[el])) : 1.0;
         step[el] = -w.res / (w.eP + w.eQ) * f;
     }
 }
@@ -204,9 +205,10 @@ cudaError_t mlp_features(const double* sig1, const double* eps, const double* sq
 }
 
 cudaError_t mlp_apply(const double* sig1, const double* eps, const double* sq, const double* e,
-                      const float* y, int o, int v, int r, double* step, cudaStream_t st) {
+                      const float* y, int o, int v, int r, int blocks, double* step,
+                      cudaStream_t st) {
     k_apply<<<nbl((long long)o * v + (long long)r * r), NT, 0, st>>>(sig1, eps, sq, e, y, o, v, r,
-                                                                     step);
+                                                                     blocks, step);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -65,9 +65,11 @@ cudaError_t mlp_features(const double* sig1, const double* eps, const double* sq
                          const long long* idx, long long n, int o, int v, int r, double s1,
                          double s2, double log_rnorm, float* X, float* jj, cudaStream_t st);
 
-// step[el] = (Jacobi step of el) * (1 + clamp(y[el], -0.95, 4)) for every
-// element of the state.
+// step[el] = (Jacobi step of el) * (1 + clamp(y[el], -0.95, 4)) for the
+// elements of the blocks selected by `blocks` (bit 0 singles, bit 1
+// doubles), the plain Jacobi step elsewhere.
 cudaError_t mlp_apply(const double* sig1, const double* eps, const double* sq, const double* e,
-                      const float* y, int o, int v, int r, double* step, cudaStream_t st);
+                      const float* y, int o, int v, int r, int blocks, double* step,
+                      cudaStream_t st);
 
 }  // namespace thc

@@ -560,7 +560,8 @@ Err Solver::run(Engine<T>& eng, const thc_solve_opts& opts, double* Zc_io, doubl
                 for (long long r0 = 0; r0 < len; r0 += chunk)
                     THC_TRY(mlp->forward(feat.p + r0 * kMlpFeatures, std::min(chunk, len - r0),
                                          yb.p + r0));
-                THC_CUDA(mlp_apply(eng.sig1.p, epsd.p, sq.p, e.p, yb.p, o, v, r, smlp.p, st));
+                THC_CUDA(mlp_apply(eng.sig1.p, epsd.p, sq.p, e.p, yb.p, o, v, r,
+                                   opts.mlp_blocks > 0 ? opts.mlp_blocks : 3, smlp.p, st));
                 k_add<<<nb(len), 256, 0, st>>>(x.p, smlp.p, len, xnew.p);
                 count_launches(1);
                 THC_CUDA(cudaGetLastError());

@@ -125,16 +125,17 @@ class DeviceSystem:
     def n(self) -> int:
         return self.o + self.v
 
-    def cholesky_slabs(self, nk: int = 32):
+    def cholesky_slabs(self, nk: int = 32, k_lo: int = 0, k_hi=None):
         """Yield (k0, L[k0:k0+nk]) as float64 (nk, n, n) device tensors with
         L[k, p, q] = sum_I x[p, I] x[q, I] R[I, k] formed in float32 and
-        symmetrised."""
+        symmetrised, for the vectors k_lo .. k_hi - 1 (default: all)."""
         import torch
         dev = self.Rt.device
         xf = torch.from_numpy(self.x).to(dev, torch.float32)
         n = self.n
-        for k0 in range(0, self.K, nk):
-            kk = min(nk, self.K - k0)
+        k_hi = self.K if k_hi is None else k_hi
+        for k0 in range(k_lo, k_hi, nk):
+            kk = min(nk, k_hi - k0)
             # M[k, q, I] = R[I, k] x[q, I];  L[k] = M[k] x^T
             M = self.Rt[k0:k0 + kk].to(torch.float32)[:, None, :] * xf[None, :, :]
             Lk = (M.reshape(kk * n, self.G) @ xf.T).reshape(kk, n, n)
