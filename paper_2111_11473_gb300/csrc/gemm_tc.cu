@@ -1417,13 +1417,26 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     const long long tiles = (long long)mblocks * nblocks * nbo;
     const int ksteps = (int)(Ktot / BK);
     const long long sms = device_sms();
-    // Split K when the tiles alone leave SMs idle; the float64 partials of
-    // the splits share the workspace of the float32 level outputs.
+    // Split K so that the work items fill whole waves of SMs: the split
+    // count (at most 32, at least 8 K steps each) with the best ratio of
+    // items to SM slots in the waves they take; the float64 partials of the
+    // splits share the workspace of the float32 level outputs.
     int splits = 1;
-    if (tiles < sms && ksteps >= 4) {
-        splits = (int)std::min<long long>({(sms + tiles - 1) / tiles, ksteps / 2, 32});
+    {
         const long long per = (long long)Mr * Nr * nbo;
-        while (splits > 1 && (size_t)(per * splits) > ws.part_elems / 2) --splits;
+        auto fill = [&](long long sp) {
+            const long long items = tiles * sp;
+            return (double)items / (double)(((items + sms - 1) / sms) * sms);
+        };
+        double best = fill(1);
+        for (int sp = 2; sp <= 32 && ksteps / sp >= 8; ++sp) {
+            if ((size_t)(per * sp) > ws.part_elems / 2) break;
+            const double f = fill(sp);
+            if (f > best + 0.02) {
+                best = f;
+                splits = sp;
+            }
+        }
     }
 
     __nv_bfloat16* slA = ws.slices;
