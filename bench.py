@@ -73,15 +73,22 @@ FP64_ALU_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # float32 operations issued per (I, X, Y, Z) term by each triangle kernel:
 # float64 kernel 3.5 float64 flops (t shared by the mirror outputs); float32
-# kernel 3 FMA-pipe operations; float-pair kernel 43 float32 operations per
-# pair of mirror outputs (19 for t, 12 per accumulation).
-TRI_ISSUED = {"fp64": 3.5, "mixed": 3.0, "fp64tc": 21.5}
+# kernel over X pairs (P a multiple of 4) 2 FMA-pipe lane operations (one
+# packed multiply and three packed FMAs per pair of X and pair of mirror
+# outputs), 3 for the unpaired float32 kernel; float-pair kernel 43 float32
+# operations per pair of mirror outputs (19 for t, 12 per accumulation).
+TRI_ISSUED = {"fp64": 3.5, "mixed": 2.0, "fp64tc": 21.5}
+TRI_KERNEL = {"fp64": "k_triangle_sym64", "mixed": "k_triangle_pair", "fp64tc": "k_triangle_df"}
+
+
+def _mixed_triangle_unpaired():
+    """The paired float32 triangle needs P % 4 == 0 and P <= 6144."""
+    return WORKLOAD is not None and not (WORKLOAD["P"] % 4 == 0 and WORKLOAD["P"] <= 6144)
 
 # DRAM bytes (read + write) of one triangle launch at o=40, v=200, P=400,
 # G=1200, from one ncu capture of the kernel that runs at that precision
 # (None: not captured since the kernel last changed).
-TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": None,
-                          "mixed": 13.49e9 + 0.26e9}
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": None, "mixed": None}
 
 
 def triangle_roofline(precision, flops, ms, launches, share):
@@ -89,22 +96,25 @@ def triangle_roofline(precision, flops, ms, launches, share):
     flops: the algorithmic count, 5 per (I, X, Y, Z) term."""
     achieved = (flops / launches) / (ms / launches * 1e-3) / 1e12     # TFLOP/s
     terms_per_s = achieved * 1e12 / 5.0
+    n_issued = TRI_ISSUED[precision]
+    kernel = TRI_KERNEL[precision]
+    if precision == "mixed" and _mixed_triangle_unpaired():
+        n_issued, kernel = 3.0, "k_triangle_f32"
     if precision == "fp64":
         pipe = FP64_ALU_TFLOPS * 1e12 / 2.0        # float64 FMA-lane operations / s
         issued = terms_per_s * TRI_ISSUED["fp64"] / 2.0
         unit_peak, src = FP64_ALU_TFLOPS, "derived: 152 SMs x 2 fp64 FMA lanes x 2 x 2.07 GHz"
     else:
         pipe = FP32_ALU_TFLOPS * 1e12 / 2.0        # float32 lane operations / s
-        issued = terms_per_s * TRI_ISSUED[precision]
+        issued = terms_per_s * n_issued
         unit_peak, src = FP32_ALU_TFLOPS, "derived: 152 SMs x 128 fp32 lanes x 2 x 2.07 GHz"
-    peak = pipe / TRI_ISSUED[precision] * 5.0 / 1e12 if precision != "fp64" else unit_peak
-    out = {"kernel": {"fp64": "k_triangle_sym64", "mixed": "k_triangle_f32_tma",
-                      "fp64tc": "k_triangle_df"}[precision] + " (Alg. 6 line 11)",
+    peak = pipe / n_issued * 5.0 / 1e12 if precision != "fp64" else unit_peak
+    out = {"kernel": kernel + " (Alg. 6 line 11)",
            "bound": "alu", "achieved": achieved, "unit": "TFLOP/s",
            "achieved_counts": "algorithmic flops, 5 per (I, X, Y, Z) term",
            "frac_issued": issued / pipe,
            "frac_issued_counts": "operations the kernel issues per term (%g) / pipe rate"
-                                 % TRI_ISSUED[precision],
+                                 % n_issued,
            "frac_algorithmic": achieved / unit_peak,
            "frac_algorithmic_peak": unit_peak,
            "traffic": TRIANGLE_TRAFFIC_BYTES[precision] if WORKLOAD_NAME.startswith(

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libthc.so")
 
-SOURCES = ["gemm_simt.cu", "gemm_tc.cu", "kernels.cu", "triangle_df.cu", "engine.cu", "solver.cu",
+SOURCES = ["gemm_simt.cu", "gemm_tc.cu", "kernels.cu", "triangle_df.cu", "triangle_pair.cu", "engine.cu", "solver.cu",
            "mlp.cu", "noalloc.cu", "cp_als.cu", "probe.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",

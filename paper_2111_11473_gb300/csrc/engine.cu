@@ -503,9 +503,7 @@ Err Engine<T>::init_finish() {
     THC_TRY(mm(P, P, v, tr(yv, P), rm(yv, P), vv.p, P, 1, 0));
     THC_CUDA(hadamard2(S.p, PP, oo.p, vv.p, (const T*)nullptr, (const T*)nullptr, st));
     THC_TRY(KRy.alloc(ov * P));
-    THC_TRY(KRx.alloc(ov * G));
     THC_CUDA(khatri_rao(yo, yv, o, v, P, KRy.p, st));
-    THC_CUDA(khatri_rao(xo, xv, o, v, G, KRx.p, st));
 
     // ---- energy weight  Wen = 2 sum_A a_A a_A^T - sum_A E_A^T o E_A   (float64)
     THC_TRY(Atil.alloc((size_t)P * K));
@@ -525,25 +523,74 @@ Err Engine<T>::init_finish() {
     count_launches(1);
     THC_CUDA(cudaGetLastError());
 
-    // ---- Alg. 6 fixed parts: B_ia^I = sum_J x_i^J x_a^J z^IJ (line 2),
-    //      U[i][I][Z] = sum_a B_ia^I y_a^Z, G_I^YZ = sum_i y_i^Y U[i][I][Z] (line 10)
-    THC_TRY(B6.alloc(ov * G));
-    THC_TRY(mm((int)ov, G, G, rm(KRx.p, G), rm(z.p, G), B6.p, G, 1, 0));
-    THC_TRY(U6.alloc((size_t)o * G * P));
-    THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p, P, 1, 0, o, (long long)v * G, 0,
-               (long long)G * P));
-    // ---- Alg. 7 exchange route.  Dense route: Kx[(ia),(jb)] = (ib|ja)
-    //      = sum_J B[(i,b),J] x_j^J x_a^J, one v x v block per (i, j).
+    // ---- Alg. 7 route.  Dense route: Kx[(ia),(jb)] = (ib|ja) =
+    //      sum_J B[(i,b),J] x_j^J x_a^J, when it takes at most 16 GiB.
     {
         const double kx_bytes = (double)ov * ov * sizeof(T);
         alg7_dense = cfg.alg7_route == 2 ||
                      (cfg.alg7_route == 0 && kx_bytes <= 16.0 * (1LL << 30));
-        if (alg7_dense) {
-            THC_TRY(Kx.alloc((size_t)ov * ov));
-            THC_TRY(W7.alloc((size_t)P * ov));
-            for (int i = 0; i < o; ++i)
-                THC_TRY(mm(v, v, G, rm(KRx.p, G), tr(B6.p + (long long)i * v * G, G),
-                           Kx.p + (long long)i * v * ov, ov, 1, 0, o, (long long)v * G, 0, v));
+    }
+    // ---- Float64 products of init (B, U, Kx below) on the tensor cores:
+    //      a workspace of at most an eighth of the free memory (24 GiB at
+    //      most; larger products are cut into pieces), released before the
+    //      residual's own workspace is sized.
+    struct Shape { long long M, N, K, b; };
+    const long long per_i = (long long)v * G;   // x o x and B elements per occupied orbital
+    const int ci = alg7_dense ? o
+                              : (int)std::max<long long>(
+                                    1, std::min<long long>(o, (4LL << 30) / (2 * per_i * TB)));
+    const bool init_f64tc = std::is_same<T, double>::value && f64tc_default;
+    if (init_f64tc) {
+        std::vector<Shape> ishapes = {{(long long)ci * v, G, G, 1}, {G, P, v, ci}};
+        if (alg7_dense) ishapes.push_back({v, v, G, o});
+        size_t sl = 0, pt = 0, ex = 0;
+        for (const Shape& sh : ishapes) {
+            size_t a_ = 0, b_ = 0, c_ = 0;
+            gemm_f64_tc_sizes((int)sh.M, (int)sh.N, (int)sh.K, (int)sh.b, false, &a_, &b_, &c_);
+            sl = std::max(sl, a_);
+            pt = std::max(pt, b_);
+            ex = std::max(ex, c_);
+        }
+        size_t cap = 24ull << 30, free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 8);
+        sl = std::min(sl, cap / 4 * 3 / sizeof(__nv_bfloat16));
+        pt = std::min(pt, cap / 4 / sizeof(float));
+        THC_TRY(f64sl.alloc(sl));
+        THC_TRY(f64part.alloc(pt));
+        THC_TRY(f64exp.alloc(ex));
+        THC_TRY(tcerr.alloc(1));
+        THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
+        f64ws = F64TcWorkspace{f64sl.p, f64sl.n, f64part.p, f64part.n, f64exp.p, f64exp.n,
+                               tcerr.p};
+        f64tc = true;
+    }
+
+    // ---- Alg. 6 fixed parts: B_ia^I = sum_J x_i^J x_a^J z^IJ (line 2),
+    //      U[i][I][Z] = sum_a B_ia^I y_a^Z, G_I^YZ = sum_i y_i^Y U[i][I][Z] (line 10)
+    THC_TRY(U6.alloc((size_t)o * G * P));
+    if (alg7_dense) {
+        THC_TRY(KRx.alloc(ov * G));
+        THC_CUDA(khatri_rao(xo, xv, o, v, G, KRx.p, st));
+        THC_TRY(B6.alloc(ov * G));
+        THC_TRY(mm((int)ov, G, G, rm(KRx.p, G), rm(z.p, G), B6.p, G, 1, 0));
+        THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p, P, 1, 0, o, (long long)v * G,
+                   0, (long long)G * P));
+        THC_TRY(Kx.alloc((size_t)ov * ov));
+        THC_TRY(W7.alloc((size_t)P * ov));
+        for (int i = 0; i < o; ++i)
+            THC_TRY(mm(v, v, G, rm(KRx.p, G), tr(B6.p + (long long)i * v * G, G),
+                       Kx.p + (long long)i * v * ov, ov, 1, 0, o, (long long)v * G, 0, v));
+    } else {
+        // x o x and B for ci occupied orbitals at a time (at most 4 GiB for
+        // both): neither is ever held whole.
+        THC_TRY(KRx.alloc((size_t)ci * per_i));
+        THC_TRY(B6.alloc((size_t)ci * per_i));
+        for (int i0 = 0; i0 < o; i0 += ci) {
+            const int nc = std::min(ci, o - i0);
+            THC_CUDA(khatri_rao(xo + (long long)i0 * G, xv, nc, v, G, KRx.p, st));
+            THC_TRY(mm(nc * v, G, G, rm(KRx.p, G), rm(z.p, G), B6.p, G, 1, 0));
+            THC_TRY(mm(G, P, v, View<T>{B6.p, 1, G}, rm(yv, P), U6.p + (long long)i0 * G * P, P,
+                       1, 0, nc, (long long)v * G, 0, (long long)G * P));
         }
     }
     // B is needed only to build U (and Kx); x o x only on the dense route
@@ -551,6 +598,13 @@ Err Engine<T>::init_finish() {
     THC_CUDA(cudaStreamSynchronize(st));
     B6.release();
     if (!alg7_dense) KRx.release();
+    if (init_f64tc) {
+        f64sl.release();
+        f64part.release();
+        f64exp.release();
+        f64ws = F64TcWorkspace{};
+        f64tc = false;
+    }
 
     // ---- Alg. 6 blocking.  G_I^YZ is resident when it fits; otherwise it
     //      is rebuilt per grid chunk (and per X block).  X blocks: H (x6 P^2),
@@ -625,6 +679,7 @@ Err Engine<T>::init_finish() {
     if (!t2sq_n5) {
         gall_resident = gall_fits;
         tri_df = std::is_same<T, double>::value && pol[THC_STEP_TRIANGLE] == THC_POL_FP64_TC;
+        tri_pair = std::is_same<T, float>::value && triangle_pair_ok(P);
         if (gall_resident) {
             THC_TRY(Gall.alloc((size_t)G * PP));
             THC_TRY(mm(P, P, o, tr(yo, P), View<T>{U6.p, (long long)G * P, 1}, Gall.p, P, 1, 0,
@@ -644,11 +699,13 @@ Err Engine<T>::init_finish() {
             THC_TRY(F4.alloc(pairs));
         }
         const long long xP = (long long)x6 * P;
+        // slabs of C_i, D_a, E and F: an even number of rows for the paired triangle
+        const long long xPs = (long long)(tri_pair ? x6 + (x6 & 1) : x6) * P;
         THC_TRY(A6.alloc(ov * P));
-        THC_TRY(C6.alloc((size_t)o * xP));
-        THC_TRY(D6.alloc((size_t)v * xP));
-        THC_TRY(Ech.alloc((size_t)ic * xP));
-        THC_TRY(Fch.alloc((size_t)ic * xP));
+        THC_TRY(C6.alloc((size_t)o * xPs));
+        THC_TRY(D6.alloc((size_t)v * xPs));
+        THC_TRY(Ech.alloc((size_t)ic * xPs));
+        THC_TRY(Fch.alloc((size_t)ic * xPs));
         THC_TRY(H.alloc((size_t)x6 * PP));
         THC_TRY(M6.alloc((size_t)x6 * o * P));
         THC_TRY(I6.alloc((size_t)x6 * ov));
@@ -687,11 +744,10 @@ Err Engine<T>::init_finish() {
     THC_TRY(E7.alloc((size_t)xb * G * G));
     THC_TRY(P7.alloc((size_t)xb * o * G));
     if (!alg7_dense) THC_TRY(G7.alloc((size_t)P * ov));   // G_ia^X for every X
-    THC_TRY(tcerr.alloc(1));
+    if (!tcerr.p) THC_TRY(tcerr.alloc(1));
     THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
     // Products of the residual on the routes in use (the tensor-core
     // workspaces are sized from the largest).
-    struct Shape { long long M, N, K, b; };
     std::vector<Shape> shapes;
     {
         const long long xP = (long long)x6 * P;
@@ -727,9 +783,9 @@ Err Engine<T>::init_finish() {
         any_bf16 = any_bf16 || pol[st_] == THC_POL_BF16X3 || pol[st_] == THC_POL_BF16;
     }
     if (std::is_same<T, double>::value && any_f64tc) {
-        // Slices of the largest product's operands and the float32 level
-        // outputs of the largest product, at most a quarter of the free
-        // memory (a product that does not fit runs on the CUDA cores).
+        // Slices of the largest product's operands and its float64 split-K
+        // partials, each at most a quarter of the free memory (a larger
+        // product is cut into pieces that fit).
         size_t sl = 0, pt = 0, ex = 0;
         for (const Shape& sh : shapes) {
             size_t a = 0, b = 0, c = 0;
@@ -742,8 +798,10 @@ Err Engine<T>::init_finish() {
         }
         {
             size_t free_b = 0, total_b = 0;
-            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
                 pt = std::min(pt, free_b / 4 / sizeof(float));
+                sl = std::min(sl, free_b / 4 / sizeof(__nv_bfloat16));
+            }
         }
         THC_TRY(f64sl.alloc(sl));
         THC_TRY(f64part.alloc(pt));
@@ -856,13 +914,22 @@ Err Engine<T>::alg6(T* sgm) {
     // X rows of C_i, D_a, E, F and H (G_I^YZ is shared by all blocks).
     for (int X0 = x_lo; X0 < x_hi; X0 += x6) {
         const int nX = std::min(x6, x_hi - X0);
-        const long long xP = (long long)nX * P;
+        // row slabs of C_i, D_a, E, F: nX rows, or nX rounded up to even
+        // with the rows of each pair interleaved for the paired triangle
+        const long long xP = (long long)(tri_pair ? nX + (nX & 1) : nX) * P;
         seg_begin(THC_STEP_ALG6_GEMM);
         // C_i^XY (line 4) and D_a^XY (line 5) for the block's X
         THC_TRY(mm(nX, P, v, tr(yv + X0, P), rm(A6.p, P), C6.p, P, 1, 0, o, 0, (long long)v * P,
                    xP));
         THC_TRY(mm(nX, P, o, tr(yo + X0, P), View<T>{A6.p, (long long)v * P, 1}, D6.p, P, 1, 0,
                    v, 0, P, xP));
+        if constexpr (std::is_same<T, float>::value) {
+            if (tri_pair) {
+                // E and F inherit the column order of C_i and D_a (lines 8-9)
+                THC_CUDA(pair_rows(C6.p, o, xP, nX, P, st));
+                THC_CUDA(pair_rows(D6.p, v, xP, nX, P, st));
+            }
+        }
         THC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(T) * nX * PP, st));
         for (int I0 = 0; I0 < G; I0 += ic) {
             const int nI = std::min(ic, G - I0);
@@ -900,6 +967,10 @@ Err Engine<T>::alg6(T* sgm) {
                                          nX, nI, st));
                 else
                     THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+            } else if (tri_pair) {
+                THC_CUDA(triangle_pair(H.p, reinterpret_cast<const float2*>(Ech.p),
+                                       reinterpret_cast<const float2*>(Fch.p), Gp, P, nX, nI, st,
+                                       tcerr.p));
             } else {
                 THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
             }

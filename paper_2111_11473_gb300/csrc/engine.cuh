@@ -32,7 +32,8 @@ struct DBuf {
             p = nullptr;
             n = 0;
             return Err{e == cudaErrorMemoryAllocation ? THC_ERR_OOM : THC_ERR_CUDA,
-                       std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+                       "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                           " bytes: " + cudaGetErrorString(e)};
         }
         return Err{};
     }
@@ -170,6 +171,9 @@ struct Engine {
     // policy): E and F as float pairs with interleaved row pairs; G_I^YZ
     // (Gall or Gch) is replaced in place by its float pairs.
     bool tri_df = false;
+    // Mixed triangle over X pairs in packed lanes (C_i, D_a, E, F with the rows
+    // of a pair interleaved, slabs of an even number of rows).
+    bool tri_pair = false;
     DBuf<float4> E4, F4;
     // Alg. 7 scratch (C7, D7: P x G on the dense route, G x P transposed on
     // the blocked route).

@@ -142,30 +142,15 @@ struct TcArgs {
     int nprod;
     int a_bcast, b_bcast;  // operand shared by every batch: packed once, batch coord 0
     int* err;
-    // nlev > 0: the slice levels of one float64 product in one launch.  Tiles
-    // of level q are numbered from lev_end[q - 1] to lev_end[q] - 1; level q
-    // has lev_ksteps[q] K steps in lev_splits[q] chunks, reads B from K
-    // element lev_bk[q] on and writes its partials to lev_C[q].
-    int nlev;
-    int lev_ksteps[8], lev_splits[8], lev_bk[8];
-    long long lev_end[8];
-    float* lev_C[8];
 };
 
 struct TileCoord {
-    int m0, n0, bo, split, k_lo, nk, lev;
+    int m0, n0, bo, split, k_lo, nk;
 };
 
 __device__ __forceinline__ TileCoord tile_coord(const TcArgs& a, long long t, int BN) {
     TileCoord c;
-    int splits = a.splits, ksteps = a.ksteps;
-    c.lev = 0;
-    if (a.nlev > 0) {
-        while (c.lev < a.nlev - 1 && t >= a.lev_end[c.lev]) ++c.lev;
-        if (c.lev > 0) t -= a.lev_end[c.lev - 1];
-        splits = a.lev_splits[c.lev];
-        ksteps = a.lev_ksteps[c.lev];
-    }
+    const int splits = a.splits, ksteps = a.ksteps;
     const int nbk = (int)(t % a.nblocks);
     long long r = t / a.nblocks;
     const int mbk = (int)(r % a.mblocks);
@@ -264,13 +249,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (it >= ST && !mbar_wait_or_fail(&sm.empty[s], (uint32_t)(((it / ST) - 1) & 1), fail))
                         break;
                     const int kc = (c.k_lo + i) * BK;
-                    const int kb = kc + (args.nlev > 0 ? args.lev_bk[c.lev] : 0);
                     mbar_expect_tx(&sm.full[s], stage_bytes);
                     tma_load_3d(sm.a_hi[s], &ta_hi, &sm.full[s], kc, c.m0, ba);
-                    tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kb, c.n0, bb);
+                    tma_load_3d(sm.b_hi[s], &tb_hi, &sm.full[s], kc, c.n0, bb);
                     if (args.nprod == 3) {
                         tma_load_3d(sm.a_lo[s], &ta_lo, &sm.full[s], kc, c.m0, ba);
-                        tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kb, c.n0, bb);
+                        tma_load_3d(sm.b_lo[s], &tb_lo, &sm.full[s], kc, c.n0, bb);
                     }
                     last[s] = it;
                 }
@@ -334,9 +318,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int buf = tl & 1;
             if (!mbar_wait_or_fail(&sm.acc_full[buf], (uint32_t)((tl >> 1) & 1), fail)) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int nsp = args.nlev > 0 ? args.lev_splits[c.lev] : args.splits;
-            float* Cb = (args.nlev > 0 ? args.lev_C[c.lev] : args.C) + (long long)c.bo * args.cbs +
-                        (nsp > 1 ? (long long)c.split * args.nbo * args.cbs : 0);
+            float* Cb = args.C + (long long)c.bo * args.cbs +
+                        (args.splits > 1 ? (long long)c.split * args.nbo * args.cbs : 0);
             const int i_base = c.m0 + q * 32;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -792,7 +775,6 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
 namespace {
 
 constexpr int kSlices = 8;
-constexpr int kChunkSteps = 16;            // 16 x 64 = 1024 K per exact partial sum
 constexpr int kLevels = kSlices;           // l = 2 .. kSlices + 1
 
 // Biased exponent field of |x| (0 for zero; subnormals count as field 1).
@@ -919,97 +901,9 @@ __global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs
     }
 }
 
-// Split counts and partial offsets of the levels l = 2 .. 9.
-struct F64Levels {
-    int splits[kLevels];
-    long long off[kLevels];
-};
-
 __device__ __forceinline__ double pow2(int k) {
     return (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(k + 1023) << 52)
                                      : scalbn(1.0, k);
-}
-
-// One output of k_f64_accumulate; MAXS > 0: every level has at most MAXS
-// splits (the split loops unroll, so all loads can issue up front).
-template <int MAXS>
-__device__ __forceinline__ void f64_accumulate_one(const float* part, const F64Levels& lv,
-                                                   unsigned e, int b, unsigned MN, long long pbs,
-                                                   int N, int swap, const int* ea,
-                                                   const int* eb, double* C, long long ldc,
-                                                   long long cbs, double alpha, double beta) {
-    const unsigned u = e / (unsigned)N, w = e - u * (unsigned)N;
-    // accumulator row i (A side) and column j (B side)
-    const int fa = swap ? ea[w] : ea[u];
-    const int fb = swap ? eb[u] : eb[w];
-    double acc = 0.0;
-    if (fa > 0 && fb > 0) {
-        const float* pb = part + (long long)b * MN + e;
-        long long H = 0;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {   // levels 2 .. 6
-            const float* p = pb + lv.off[q];
-            long long sl = 0;
-            if constexpr (MAXS > 0) {
-#pragma unroll
-                for (int sp = 0; sp < MAXS; ++sp)
-                    if (sp < lv.splits[q]) sl += __float2int_rn(p[sp * pbs]);
-            } else {
-                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += __float2int_rn(p[sp * pbs]);
-            }
-            H = H * 128 + sl;
-        }
-        float T = 0.f;
-#pragma unroll
-        for (int q = kLevels - 1; q >= 5; --q) {   // levels 9 .. 7
-            const float* p = pb + lv.off[q];
-            float sl = 0.f;
-            if constexpr (MAXS > 0) {
-#pragma unroll
-                for (int sp = 0; sp < MAXS; ++sp)
-                    if (sp < lv.splits[q]) sl += p[sp * pbs];
-            } else {
-                for (int sp = 0; sp < lv.splits[q]; ++sp) sl += p[sp * pbs];
-            }
-            T = fmaf(T, 0.0078125f, sl);
-        }
-        // level-6 units: H + 2^-7 T;  2^(-42) 2^(e_r + e_c), e = field - 1022
-        const double h = fma((double)T, 0.0078125, (double)H);
-        acc = h * pow2((fa - 1022) + (fb - 1022) - 42);
-    }
-    double* c = C + (long long)b * cbs + (long long)u * ldc + w;
-    *c = (beta != 0.0 ? beta * *c : 0.0) + alpha * acc;
-}
-
-// C(b, u, w) = beta C + alpha 2^(e_r + e_c) sum_l 2^(-7l) S_l(b, u, w), S_l
-// the sum of the level's splits, in C's own orientation (u < M rows, w < N
-// contiguous columns of the product as called; the level outputs are written
-// the same way, so every access runs along w).  Levels 2-6 are combined
-// exactly in int64 (S_2 2^28 + ... + S_6, below 2^63 for up to 2048 splits of
-// integers below 2^24); levels 7-9, which sit 2^-35 and further below level
-// 2, in float32, whose rounding there is below 2^-57 of the product scale.
-// Grid: x over M N, y over the batches; every thread takes two outputs a
-// grid-width apart per step, whose loads are independent (memory-latency
-// bound: the pipes are far from busy).
-template <int MAXS>
-__global__ void __launch_bounds__(256, 4) k_f64_accumulate(
-    const float* part, F64Levels lv, int nbo, int M, int N, int swap, const int* eA, int RpA,
-    int a_bc, const int* eB, int RpB, int b_bc, double* C, long long ldc, long long cbs,
-    double alpha, double beta) {
-    const int b = blockIdx.y;
-    const unsigned MN = (unsigned)M * (unsigned)N;
-    const long long pbs = (long long)MN * nbo;     // split stride of the level outputs
-    const int* ea = eA + (long long)(a_bc ? 0 : b) * RpA;
-    const int* eb = eB + (long long)(b_bc ? 0 : b) * RpB;
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += 2 * stride) {
-        const unsigned e2 = e + stride;
-        f64_accumulate_one<MAXS>(part, lv, e, b, MN, pbs, N, swap, ea, eb, C, ldc, cbs, alpha,
-                                 beta);
-        if (e2 < MN)
-            f64_accumulate_one<MAXS>(part, lv, e2, b, MN, pbs, N, swap, ea, eb, C, ldc, cbs,
-                                     alpha, beta);
-    }
 }
 
 // 3-D map over bf16 rows of `pitch` elements of which the first kext are read.
@@ -1025,10 +919,10 @@ cudaError_t make_map_pitch(CUtensorMap* map, const __nv_bfloat16* base, long lon
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Exact-chunk splits of level l (K of (l - 1) Ktot).
-inline int level_splits(int l, long long Ktot) {
-    const long long steps = (l - 1) * Ktot / BK;
-    return (int)std::max<long long>(1, (steps + kChunkSteps - 1) / kChunkSteps);
+// Largest split-K count of the fused product: at most 32 chunks of at least
+// 8 K steps.
+inline int max_f64_splits(long long Ktot) {
+    return (int)std::max<long long>(1, std::min<long long>(32, Ktot / BK / 8));
 }
 
 }  // namespace
@@ -1040,10 +934,8 @@ void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slic
     const long long nbo = reduce ? 1 : batch;
     const long long Rm = rup(M, 128), Rn = rup(N, 128);
     *slice_elems = (size_t)(kSlices * (Rm + Rn) * Ktot * nbo);
-    // every level's float32 outputs (exact splits only)
-    long long sp = 0;
-    for (int l = 2; l <= kSlices + 1; ++l) sp += level_splits(l, Ktot);
-    *part_elems = (size_t)(sp * nbo * (long long)M * N);
+    // float64 split-K partials of the fused product, counted in floats
+    *part_elems = (size_t)(2LL * max_f64_splits(Ktot) * nbo * (long long)M * N);
     *expo_elems = (size_t)((Rm + Rn) * nbo);
 }
 
@@ -1057,7 +949,7 @@ void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slic
 // drained after c_l = floor(16 / (l - 1)) steps (at most 1024 products: an
 // exact float32 integer) and restarted.  The epilogue warps combine every
 // drain exactly in registers (levels 2-6 in int64, 7-9 in float32 below
-// 2^-57 of the product's scale, as in k_f64_accumulate) and write the tile
+// 2^-57 of the product's scale) and write the tile
 // once in float64: no float32 level outputs go through memory.
 // Roles: warp 0 streams slices with TMA (B slices of a K step double-
 // buffered, A slices through a 4-deep ring), warp 1 issues the MMAs, warps
@@ -1388,8 +1280,82 @@ __global__ void k_f64_splitsum(const double* part, int splits, int nbo, int M, i
 
 }  // namespace
 
+namespace {
+
+// Workspace a product takes in one piece: slices, exponents, and the slice
+// row pitch (which must fit a 32-bit coordinate).
+struct F64Need {
+    long long slices, expo, pitch;
+};
+
+F64Need f64_need(const Gemm<double>& g) {
+    const bool swap = g.N > g.M;
+    const int Mr = swap ? g.N : g.M, Nr = swap ? g.M : g.N;
+    const long long Kp = rup(std::max(g.K, 1), BK);
+    const int nb = g.batch;
+    const int nbo = g.reduce ? 1 : nb;
+    const long long Ktot = g.reduce ? Kp * nb : Kp;
+    const long long RpA = rup(Mr, BM), RpB = rup(Nr, FN);
+    const long long sa = swap ? g.sBb : g.sAb, sb = swap ? g.sAb : g.sBb;
+    const bool a_bc = !g.reduce && nb > 1 && sa == 0;
+    const bool b_bc = !g.reduce && nb > 1 && sb == 0;
+    const long long nba = a_bc ? 1 : nbo, nbb = b_bc ? 1 : nbo;
+    const long long pitch = kSlices * Ktot;
+    return F64Need{(RpA * nba + RpB * nbb) * pitch, RpA * nba + RpB * nbb, pitch};
+}
+
+bool f64_fits(const Gemm<double>& g, const F64TcWorkspace& ws) {
+    const F64Need n = f64_need(g);
+    return (size_t)n.slices <= ws.slice_elems && (size_t)n.expo <= ws.expo_elems &&
+           n.pitch <= INT32_MAX;
+}
+
+cudaError_t gemm_f64_tc_one(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s);
+
+}  // namespace
+
+// A product whose slices do not fit the workspace is cut into pieces that
+// do: batches first (a batch-reduced product accumulates its later pieces
+// into C with beta = 1), then the rows or the columns of C, whichever are
+// more, in halves rounded to the 128-row tile.
 cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+    if (f64_fits(g, ws)) return gemm_f64_tc_one(g, ws, s);
+    Gemm<double> g1 = g, g2 = g;
+    if (g.batch > 1) {
+        const int b1 = g.batch / 2;
+        g1.batch = b1;
+        g2.batch = g.batch - b1;
+        g2.A.p = g.A.p + (long long)b1 * g.sAb;
+        g2.B.p = g.B.p + (long long)b1 * g.sBb;
+        if (g.reduce) {
+            g2.beta = 1.0;
+        } else {
+            g2.C = g.C + (long long)b1 * g.sCb;
+        }
+    } else if (g.M >= g.N && g.M > BM) {
+        const int m1 = (int)rup((g.M + 1) / 2, BM);
+        g1.M = m1;
+        g2.M = g.M - m1;
+        g2.A.p = g.A.p + (long long)m1 * g.A.rs;
+        g2.C = g.C + (long long)m1 * g.ldc;
+    } else if (g.N > BM) {
+        const int n1 = (int)rup((g.N + 1) / 2, BM);
+        g1.N = n1;
+        g2.N = g.N - n1;
+        g2.B.p = g.B.p + (long long)n1 * g.B.cs;
+        g2.C = g.C + n1;
+    } else {
+        return cudaErrorMemoryAllocation;   // a single tile row and column do not fit
+    }
+    cudaError_t e = gemm_f64_tc(g1, ws, s);
+    if (e != cudaSuccess) return e;
+    return gemm_f64_tc(g2, ws, s);
+}
+
+namespace {
+
+cudaError_t gemm_f64_tc_one(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s) {
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     const bool swap = g.N > g.M;
@@ -1420,7 +1386,7 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     // Split K so that the work items fill whole waves of SMs: the split
     // count (at most 32, at least 8 K steps each) with the best ratio of
     // items to SM slots in the waves they take; the float64 partials of the
-    // splits share the workspace of the float32 level outputs.
+    // splits go to the workspace's partial buffer.
     int splits = 1;
     {
         const long long per = (long long)Mr * Nr * nbo;
@@ -1514,6 +1480,8 @@ cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStr
     }
     return e;
 }
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Randomised self-test: tensor-core products against the CUDA-core products
@@ -1737,7 +1705,15 @@ cudaError_t gemm_f64_tc_selftest(int cases, unsigned long long seed, double* max
         h.C = C2;
         h.ws = simt;
         h.ws_elems = cap;
-        if ((e = gemm_f64_tc(g, ws, st))) break;
+        // Every third case gets a third of the slice workspace it needs, so
+        // that the product is cut into pieces.
+        F64TcWorkspace wsc = ws;
+        if (c % 3 == 2) {
+            const long long Kp = rup(std::max(g.K, 1), BK);
+            wsc.slice_elems = (size_t)std::max<long long>(f64_need(g).slices / 3,
+                                                          2LL * BM * kSlices * Kp);
+        }
+        if ((e = gemm_f64_tc(g, wsc, st))) break;
         if ((e = gemm_simt(h, st))) break;
         if ((e = cudaMemsetAsync(red, 0, 16, st))) break;
         k_max_abs_diff64<<<256, 256, 0, st>>>(C1, C2, nC, red);

@@ -96,6 +96,20 @@ cudaError_t split_df(const double* in, long long n, float2* out, cudaStream_t s)
 cudaError_t triangle_df(double* H, const float4* E4, const float4* F4, const float2* G2, int P,
                         int nX, int nI, cudaStream_t s);
 
+// Float32 triangle over X pairs in packed lanes (triangle_pair.cu), for P a
+// multiple of 4 and at most kPairMaxP.  E2, F2: nI x ceil(nX/2) x P float2
+// {E^{2q,Y}, E^{2q+1,Y}} (16-byte aligned); G: nI x P x P; H: nX x P x P,
+// accumulated into.  err (device int) receives 1 if a bounded wait expired.
+constexpr int kPairMaxP = 6144;
+bool triangle_pair_ok(int P);
+cudaError_t triangle_pair(float* H, const float2* E2, const float2* F2, const float* G, int P,
+                          int nX, int nI, cudaStream_t s, int* err);
+// In place: for each of nslab slabs at A + b stride (stride >= nX rounded up
+// to even, times P), rows 2q, 2q + 1 of P floats become the interleaved
+// pairs of triangle_pair's layout (0 in the second lane of an odd last row).
+cudaError_t pair_rows(float* A, long long nslab, long long stride, int nX, int P,
+                      cudaStream_t s);
+
 // Deterministic float64 sums.
 // out[0] = sum_i a[i] b[i]
 template <typename T>

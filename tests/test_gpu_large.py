@@ -35,16 +35,17 @@ def test_alg6_x_blocks_match_oracle(x6, route):
     assert np.abs(sig - sig.T).max() < 1e-12 * max(1.0, np.abs(sig).max())
 
 
-@pytest.mark.parametrize("case,x6", [((8, 60, 120, 200, 80, 13), 32),   # TMA kernel, ragged 24
-                                     ((8, 60, 120, 200, 80, 13), 64),
-                                     ((7, 37, 70, 90, 45, 11), 32)],     # P % 4 != 0 kernel
-                         ids=["P120x32", "P120x64", "P70x32"])
+@pytest.mark.parametrize("case,x6,ic", [((8, 60, 120, 200, 80, 13), 32, 0),   # paired kernel, ragged 24
+                                        ((8, 60, 120, 200, 80, 13), 64, 0),
+                                        ((8, 60, 120, 200, 80, 13), 31, 37),  # odd row blocks
+                                        ((7, 37, 70, 90, 45, 11), 32, 0)],    # P % 4 != 0 kernel
+                         ids=["P120x32", "P120x64", "P120x31ic37", "P70x32"])
 @pytest.mark.parametrize("tcp", [3, 0])
-def test_mixed_alg6_x_blocks_within_bound(case, x6, tcp):
+def test_mixed_alg6_x_blocks_within_bound(case, x6, ic, tcp):
     import paper_2111_11473_gb300 as pkg
     s, Zc, t1, sig_ref, r1_ref, E_ref = oracle_case(*case)
     with context(s, precision=pkg.THC_PREC_MIXED, tc_products=tcp, x_block6=x6,
-                 alg7_route=1) as ctx:
+                 alg7_route=1, i_chunk=ic) as ctx:
         sig, sig1, E = ctx.residual(Zc, t1)
     scale = max(np.abs(sig_ref).max(), np.abs(r1_ref).max())
     err = max(np.abs(sig - sig_ref).max(), np.abs(sig1 - r1_ref).max())
