@@ -524,25 +524,27 @@ Err Engine<T>::init_finish() {
     THC_CUDA(cudaGetLastError());
 
     // ---- Alg. 7 route.  Dense route: Kx[(ia),(jb)] = (ib|ja) =
-    //      sum_J B[(i,b),J] x_j^J x_a^J, when it takes at most 16 GiB.
+    //      sum_J B[(i,b),J] x_j^J x_a^J, when it takes at most 16 GiB; built
+    //      only by the shard that evaluates Alg. 7.
     {
         const double kx_bytes = (double)ov * ov * sizeof(T);
         alg7_dense = cfg.alg7_route == 2 ||
                      (cfg.alg7_route == 0 && kx_bytes <= 16.0 * (1LL << 30));
     }
+    const bool dense_init = alg7_dense && do_alg7;
     // ---- Float64 products of init (B, U, Kx below) on the tensor cores:
     //      a workspace of at most an eighth of the free memory (24 GiB at
     //      most; larger products are cut into pieces), released before the
     //      residual's own workspace is sized.
     struct Shape { long long M, N, K, b; };
     const long long per_i = (long long)v * G;   // x o x and B elements per occupied orbital
-    const int ci = alg7_dense ? o
+    const int ci = dense_init ? o
                               : (int)std::max<long long>(
                                     1, std::min<long long>(o, (4LL << 30) / (2 * per_i * TB)));
     const bool init_f64tc = std::is_same<T, double>::value && f64tc_default;
     if (init_f64tc) {
         std::vector<Shape> ishapes = {{(long long)ci * v, G, G, 1}, {G, P, v, ci}};
-        if (alg7_dense) ishapes.push_back({v, v, G, o});
+        if (dense_init) ishapes.push_back({v, v, G, o});
         size_t sl = 0, pt = 0, ex = 0;
         for (const Shape& sh : ishapes) {
             size_t a_ = 0, b_ = 0, c_ = 0;
@@ -568,7 +570,7 @@ Err Engine<T>::init_finish() {
     // ---- Alg. 6 fixed parts: B_ia^I = sum_J x_i^J x_a^J z^IJ (line 2),
     //      U[i][I][Z] = sum_a B_ia^I y_a^Z, G_I^YZ = sum_i y_i^Y U[i][I][Z] (line 10)
     THC_TRY(U6.alloc((size_t)o * G * P));
-    if (alg7_dense) {
+    if (dense_init) {
         THC_TRY(KRx.alloc(ov * G));
         THC_CUDA(khatri_rao(xo, xv, o, v, G, KRx.p, st));
         THC_TRY(B6.alloc(ov * G));
@@ -597,7 +599,7 @@ Err Engine<T>::init_finish() {
     // (C^XI of the blocked route comes from its per-X intermediates).
     THC_CUDA(cudaStreamSynchronize(st));
     B6.release();
-    if (!alg7_dense) KRx.release();
+    if (!dense_init) KRx.release();
     if (init_f64tc) {
         f64sl.release();
         f64part.release();
@@ -733,24 +735,26 @@ Err Engine<T>::init_finish() {
     xb = cfg.x_block > 0 ? std::min(cfg.x_block, P)
                          : (int)std::max<long long>(1, std::min<long long>(
                                std::min(P, 32), (8LL << 30) / ((long long)G * G * TB)));
-    THC_TRY(R7.alloc((size_t)P * ov));
-    THC_TRY(S7.alloc((size_t)P * ov));
-    THC_TRY(C7.alloc((size_t)P * G));
-    THC_TRY(D7.alloc((size_t)P * G));
-    THC_TRY(Yv.alloc((size_t)xb * o * P));
-    THC_TRY(M7.alloc((size_t)xb * o * P));
-    THC_TRY(Yo.alloc((size_t)xb * v * P));
-    THC_TRY(N7.alloc((size_t)xb * o * G));
-    THC_TRY(E7.alloc((size_t)xb * G * G));
-    THC_TRY(P7.alloc((size_t)xb * o * G));
-    if (!alg7_dense) THC_TRY(G7.alloc((size_t)P * ov));   // G_ia^X for every X
+    if (do_alg7) {   // only the shard that evaluates Alg. 7
+        THC_TRY(R7.alloc((size_t)P * ov));
+        THC_TRY(S7.alloc((size_t)P * ov));
+        THC_TRY(C7.alloc((size_t)P * G));
+        THC_TRY(D7.alloc((size_t)P * G));
+        THC_TRY(Yv.alloc((size_t)xb * o * P));
+        THC_TRY(M7.alloc((size_t)xb * o * P));
+        THC_TRY(Yo.alloc((size_t)xb * v * P));
+        THC_TRY(N7.alloc((size_t)xb * o * G));
+        THC_TRY(E7.alloc((size_t)xb * G * G));
+        THC_TRY(P7.alloc((size_t)xb * o * G));
+        if (!alg7_dense) THC_TRY(G7.alloc((size_t)P * ov));   // G_ia^X for every X
+    }
     if (!tcerr.p) THC_TRY(tcerr.alloc(1));
     THC_CUDA(cudaMemsetAsync(tcerr.p, 0, sizeof(int), st));
     // Products of the residual on the routes in use (the tensor-core
     // workspaces are sized from the largest).
     std::vector<Shape> shapes;
     {
-        const long long xP = (long long)x6 * P;
+        const long long xP = (long long)(tri_pair ? x6 + (x6 & 1) : x6) * P;
         shapes = {
             {P, P, (long long)kb * P, 1}, {(long long)P * kb, P, P, 1}, {P, P, o, kb},
             {P, P, v, kb}, {v, P, v, kb}, {o, G, v, xb}, {G, G, o, xb}, {o, G, G, xb},
