@@ -901,52 +901,9 @@ __global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs
     }
 }
 
-// The float64 epilogue below runs on the integer pipes: GB300 issues float64
-// arithmetic at 1/64 of the float32 rate, which made the conversions and
-// scalings of a tile's 8192 outputs (five float64 operations each) take
-// longer than the tile's tensor-core work on products with short K.
-
-// (-1)^neg x 2^e for an integer |x| < 2^63, rounded to nearest even; the
-// exponent goes straight into the bit pattern (outside the normal range:
-// scalbn on the float64 pipe, which does not occur for operands of ordinary
-// size).
-__device__ __forceinline__ double i64_scaled(long long x, int e, unsigned neg) {
-    if (x == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)((x < 0) ^ neg) << 63;
-    unsigned long long a = x < 0 ? 0ULL - (unsigned long long)x : (unsigned long long)x;
-    int p = 63 - __clzll((long long)a);       // leading one
-    if (p > 52) {
-        const int s = p - 52;                  // 1 .. 10
-        const unsigned long long rb = (a >> (s - 1)) & 1ULL;
-        const unsigned long long st = a & ((1ULL << (s - 1)) - 1ULL);
-        a >>= s;
-        if (rb && (st || (a & 1ULL))) {
-            ++a;
-            if (a >> 53) {
-                a >>= 1;
-                ++p;
-            }
-        }
-    } else {
-        a <<= (52 - p);
-    }
-    const unsigned long long frac = a & 0xfffffffffffffULL;
-    const int be = p + e + 1023;
-    if (be < 1 || be > 2046)
-        return scalbn(__longlong_as_double((long long)(sgn | (1023ULL << 52) | frac)), p + e);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
-}
-
-// (-1)^neg t 2^e, exact (t is a sum of multiples of 2^-14, never subnormal).
-__device__ __forceinline__ double f32_scaled(float t, int e, unsigned neg) {
-    const unsigned b = __float_as_uint(t);
-    const int ex = (int)((b >> 23) & 0xffu);
-    if (ex == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)((b >> 31) ^ neg) << 63;
-    const unsigned long long frac = (unsigned long long)(b & 0x7fffffu) << 29;
-    const int be = ex - 127 + e + 1023;
-    if (be < 1 || be > 2046) return neg ? -scalbn((double)t, e) : scalbn((double)t, e);
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | frac));
+__device__ __forceinline__ double pow2(int k) {
+    return (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(k + 1023) << 52)
+                                     : scalbn(1.0, k);
 }
 
 // 3-D map over bf16 rows of `pitch` elements of which the first kext are read.
@@ -1027,8 +984,6 @@ struct F64Args {
     double* C;               // output, or float64 partials when splits > 1
     long long crs, ccs, cbs;
     double alpha, beta;
-    int alpha_pow2;          // alpha = (-1)^alpha_neg 2^alpha_e, folded into the epilogue
-    int alpha_e, alpha_neg;
     int* err;
 };
 
@@ -1281,22 +1236,17 @@ __global__ void __launch_bounds__(kF64Threads, 1)
             double* Cb = args.C + (long long)c.bo * args.cbs +
                          (args.splits > 1 ? (long long)c.split * args.nbo * args.cbs : 0) +
                          (long long)i * args.crs;
-            // a power-of-two alpha goes into the exponent and the sign
-            const bool fold = args.splits == 1 && args.alpha_pow2;
-            const int ea = (fa - 1022) - 1022 - 42 + (fold ? args.alpha_e : 0);
-            const unsigned an = fold ? (unsigned)args.alpha_neg : 0u;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int col = c.n0 + half * 32 + j;
                 if (col >= args.N) continue;
                 const int fb = eb[col];
-                // (H + 2^-7 T) 2^(e_r + e_c - 42): one float64 addition
                 double v = 0.0;
                 if (fa > 0 && fb > 0)
-                    v = i64_scaled(H[j], ea + fb, an) + f32_scaled(T[j], ea + fb - 7, an);
+                    v = fma((double)T[j], 0.0078125, (double)H[j]) *
+                        pow2((fa - 1022) + (fb - 1022) - 42);
                 double* p = Cb + (long long)col * args.ccs;
                 if (args.splits > 1) *p = v;
-                else if (fold) *p = args.beta != 0.0 ? fma(args.beta, *p, v) : v;
                 else *p = (args.beta != 0.0 ? args.beta * *p : 0.0) + args.alpha * v;
             }
         }
@@ -1498,13 +1448,6 @@ cudaError_t gemm_f64_tc_one(const Gemm<double>& g, const F64TcWorkspace& ws, cud
     a.RpB = (int)RpB;
     a.alpha = g.alpha;
     a.beta = g.beta;
-    {
-        int ex = 0;
-        const double m = std::frexp(g.alpha, &ex);   // alpha = m 2^ex, |m| in [0.5, 1)
-        a.alpha_pow2 = (m == 0.5 || m == -0.5) ? 1 : 0;
-        a.alpha_e = ex - 1;
-        a.alpha_neg = g.alpha < 0 ? 1 : 0;
-    }
     a.err = ws.err;
     // accumulator (i, j) is C's (m, n), or (n, m) when the operands were swapped
     const long long crs = swap ? 1 : g.ldc, ccs = swap ? g.ldc : 1;
@@ -1618,7 +1561,7 @@ cudaError_t gemm_tc_selftest(int cases, unsigned long long seed, double* max_rel
         const bool ta = st_next(s) & 1, tb = st_next(s) & 1;
         const int nprod = (st_next(s) % 3 == 0) ? 1 : 3;
         g.beta = (st_next(s) & 1) ? 0.5 : 0.0;
-        // a general alpha and powers of two (folded into the epilogue's exponent)
+        // a general alpha and powers of two
         g.alpha = (c & 1) ? 1.25 : ((c & 2) ? -0.5 : 2.0);
         while ((long long)g.batch * g.M * g.K > cap || (long long)g.batch * g.K * g.N > cap ||
                (long long)g.batch * g.M * g.N > cap)
@@ -1740,7 +1683,7 @@ cudaError_t gemm_f64_tc_selftest(int cases, unsigned long long seed, double* max
         const bool ta = st_next(s) & 1, tb = st_next(s) & 1;
         const int spread = (st_next(s) % 3 == 0) ? 40 : 0;
         g.beta = (st_next(s) & 1) ? 0.5 : 0.0;
-        // a general alpha and powers of two (folded into the epilogue's exponent)
+        // a general alpha and powers of two
         g.alpha = (c & 1) ? 1.25 : ((c & 2) ? -0.5 : 2.0);
         while ((long long)g.batch * g.M * g.K > cap || (long long)g.batch * g.K * g.N > cap ||
                (long long)g.batch * g.M * g.N > cap)

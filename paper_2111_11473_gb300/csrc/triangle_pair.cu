@@ -17,6 +17,10 @@
 // and Z = 16 (w % 2) + 4 lz + (0..3): 64 packed accumulators per thread.
 // One thread streams the operands with 3-D TMA boxes (128-byte swizzle)
 // through a ring of QS stages of QI grid points; every wait is bounded.
+// Measured at P = 400, 400 rows X, 300 grid points: two stages of six grid
+// points 2.54 ms, three of four 2.69, four of three 2.88, five or six of two
+// 3.30, eight of one 4.28 (per-stage waits and refills, issued by one thread
+// of a compute warp, are the overhead that larger stages amortise).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,10 +34,16 @@ namespace {
 
 typedef unsigned long long f2;   // two float32 lanes: low word = lane 0 (X = 2q)
 
-constexpr int QT = 32;   // Y and Z tile
-constexpr int QP = 8;    // X pairs per block
-constexpr int QI = 2;    // grid points per stage
-constexpr int QS = 5;    // ring stages
+#ifndef THC_PAIR_QI
+#define THC_PAIR_QI 6
+#endif
+#ifndef THC_PAIR_QS
+#define THC_PAIR_QS 2
+#endif
+constexpr int QT = 32;            // Y and Z tile
+constexpr int QP = 8;             // X pairs per block
+constexpr int QI = THC_PAIR_QI;   // grid points per stage
+constexpr int QS = THC_PAIR_QS;   // ring stages
 constexpr long long kQWait = 4000000000LL;
 
 struct QSmem {
