@@ -650,7 +650,7 @@ Err Engine<T>::init_finish() {
     // ---- Route for Eqs. 32-33: Alg. 6 (O(N^4), triangle on the CUDA cores)
     //      or Algs. 4 and 5 (O(N^5), batched products).  Automatic: the
     //      smaller estimated time from rates measured on GB300 at o=40
-    //      (mixed: triangle 32 TFLOP/s, Alg. 6 products 100, Algs. 4-5
+    //      (mixed: triangle 45 TFLOP/s, Alg. 6 products 100, Algs. 4-5
     //      products 35; float64: 0.85 for every operation) plus 10 us per
     //      product launched (it decides at small sizes).
     {
@@ -673,7 +673,7 @@ Err Engine<T>::init_finish() {
                                                  std::floor(2.0 * (1LL << 30) /
                                                             (dG * dG * sizeof(T)))));
         const double n45 = 13.0 * dO * (std::ceil(dO / nb) + std::ceil(dV / nb)) + 2.0;
-        const double t6 = (mixed ? f6_tri / 32e12 + f6_mm / 100e12 : (f6_tri + f6_mm) / 0.85e12) +
+        const double t6 = (mixed ? f6_tri / 45e12 + f6_mm / 100e12 : (f6_tri + f6_mm) / 0.85e12) +
                           n6 * 10e-6;
         const double t45 = (mixed ? f45 / 35e12 : f45 / 0.85e12) + n45 * 10e-6;
         t2sq_n5 = cfg.t2sq_route == 2 || (cfg.t2sq_route == 0 && t45 < t6);

@@ -17,10 +17,11 @@
 // and Z = 16 (w % 2) + 4 lz + (0..3): 64 packed accumulators per thread.
 // One thread streams the operands with 3-D TMA boxes (128-byte swizzle)
 // through a ring of QS stages of QI grid points; every wait is bounded.
-// Measured at P = 400, 400 rows X, 300 grid points: two stages of six grid
-// points 2.54 ms, three of four 2.69, four of three 2.88, five or six of two
-// 3.30, eight of one 4.28 (per-stage waits and refills, issued by one thread
-// of a compute warp, are the overhead that larger stages amortise).
+// The last warp to finish with a stage issues its refill.  Measured at
+// P = 400, 400 rows X, 1200 grid points: two stages of six grid points
+// 8.54 ms (0.56 of the FP32 peak in algorithmic flops), three of four 9.33,
+// four of three 9.89, five of two 10.57; with the refills issued by one
+// thread of warp 0 instead, 9.16, 9.85, 10.6 and 12.2 ms.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -56,7 +57,8 @@ struct QSmem {
     float g1[QS][QI][QT][QT];   // G^YZ, rows Y
     float g2[QS][QI][QT][QT];   // G^ZY, rows Z
     unsigned long long full[QS];
-    unsigned long long empty[QS];
+    unsigned cnt[QS];     // warps done with the stage, over all its uses
+    int last[QS];         // last step issued into the stage
     int fail;
 };
 
@@ -77,16 +79,6 @@ __device__ __forceinline__ bool q_wait(unsigned long long* bar, unsigned parity)
         if (done) return true;
         if (clock64() - t0 > kQWait) return false;
     }
-}
-
-__device__ __forceinline__ bool q_test(unsigned long long* bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(su32(bar)), "r"(parity));
-    return done != 0;
 }
 
 __device__ __forceinline__ void q_tma(void* dst, const CUtensorMap* m, unsigned long long* bar,
@@ -161,7 +153,8 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < QS; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&sm.full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(su32(&sm.empty[s])));
+            sm.cnt[s] = 0;
+            sm.last[s] = -1;
         }
         sm.fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -170,6 +163,7 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     auto issue = [&](int k) {
         const int s = k % QS, I0 = k * QI;
+        sm.last[s] = k;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
                          su32(&sm.full[s])),
                      "r"(stage_bytes));
@@ -183,9 +177,8 @@ __global__ void __launch_bounds__(256, 1)
         q_tma(&sm.g1[s][0][0][0], &tmG, &sm.full[s], Z0, Y0, I0);
         q_tma(&sm.g2[s][0][0][0], &tmG, &sm.full[s], Y0, Z0, I0);
     };
-    int next = 0;   // next step to load (thread 0 only)
     if (threadIdx.x == 0)
-        for (; next < QS - 1 && next < nst; ++next) issue(next);
+        for (int j = 0; j < QS && j < nst; ++j) issue(j);
 
     f2 a1[2][4][4], a2[2][4][4];   // [p][yy][zz]: H^{X,Y,Z} and H^{X,Z,Y}
 #pragma unroll
@@ -198,27 +191,6 @@ __global__ void __launch_bounds__(256, 1)
     int k = 0;
     for (; k < nst; ++k) {
         const int s = k % QS;
-        // Refill every stage whose consumers are done, without blocking, up
-        // to QS - 1 steps ahead; block (bounded) only if step k itself has
-        // not been issued yet.
-        if (threadIdx.x == 0) {
-            while (next < nst && next <= k + QS - 1) {
-                const bool need = next <= k;
-                if (next >= QS) {
-                    const unsigned par = ((next / QS) - 1) & 1;
-                    if (need) {
-                        if (!q_wait(&sm.empty[next % QS], par)) {
-                            atomicExch(&sm.fail, 1);
-                            break;
-                        }
-                    } else if (!q_test(&sm.empty[next % QS], par)) {
-                        break;
-                    }
-                }
-                issue(next);
-                ++next;
-            }
-        }
         if (!q_wait(&sm.full[s], (k / QS) & 1)) atomicExch(&sm.fail, 1);
         if (*(volatile int*)&sm.fail) break;
 #pragma unroll 1
@@ -273,16 +245,28 @@ __global__ void __launch_bounds__(256, 1)
                     }
             }
         }
+        // The last warp to finish with the stage refills it at once with
+        // step k + QS (its reads are ordered before the copy by the fences
+        // and the atomic).
         __syncwarp();
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&sm.empty[s]))
-                         : "memory");
+        if (lane == 0) {
+            __threadfence_block();
+            const unsigned done = atomicAdd(&sm.cnt[s], 1u);
+            if (done % 8u == 7u && k + QS < nst) {
+                __threadfence_block();
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                issue(k + QS);
+            }
+        }
     }
     __syncthreads();
     if (*(volatile int*)&sm.fail) {
         if (threadIdx.x == 0) {
             // let the copies already issued land before the block exits
-            for (int j = k; j < next; ++j) (void)q_wait(&sm.full[j % QS], (j / QS) & 1);
+            for (int s = 0; s < QS; ++s) {
+                const int j = *(volatile int*)&sm.last[s];
+                if (j >= k) (void)q_wait(&sm.full[s], (j / QS) & 1);
+            }
             atomicExch(err, 1);
         }
         return;
