@@ -82,8 +82,8 @@ TRI_KERNEL = {"fp64": "k_triangle_sym64", "mixed": "k_triangle_pair", "fp64tc": 
 
 
 def _mixed_triangle_unpaired():
-    """The paired float32 triangle needs P % 4 == 0 and P <= 6144."""
-    return WORKLOAD is not None and not (WORKLOAD["P"] % 4 == 0 and WORKLOAD["P"] <= 6144)
+    """The paired float32 triangle needs P % 4 == 0 and P <= 28000."""
+    return WORKLOAD is not None and not (WORKLOAD["P"] % 4 == 0 and WORKLOAD["P"] <= 28000)
 
 # DRAM bytes (read + write) of one triangle launch at o=40, v=200, P=400,
 # G=1200, from one ncu capture of the kernel that runs at that precision

@@ -970,13 +970,13 @@ Err Engine<T>::alg6(T* sgm) {
                     THC_CUDA(triangle_df(H.p, E4.p, F4.p, reinterpret_cast<const float2*>(Gp), P,
                                          nX, nI, st));
                 else
-                    THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+                    THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st));
             } else if (tri_pair) {
                 THC_CUDA(triangle_pair(H.p, reinterpret_cast<const float2*>(Ech.p),
                                        reinterpret_cast<const float2*>(Fch.p), Gp, P, nX, nI, st,
                                        tcerr.p));
             } else {
-                THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st, tcerr.p));
+                THC_CUDA(triangle(H.p, Ech.p, Fch.p, Gp, P, nX, nI, st));
             }
             seg_end();
         }

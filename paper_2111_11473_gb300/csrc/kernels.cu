@@ -485,277 +485,6 @@ __global__ void __launch_bounds__(512, 1) k_triangle_f32(float* H, const float* 
     }
 }
 
-// TMA-fed float32 triangle kernel (P a multiple of 4, so that every row of
-// E, F and G starts on a 16-byte boundary).  Same 32^3 tile and 8 x 8 register
-// tile as k_triangle_f32; one thread issues five 3-D TMA box copies per stage
-// (E and F rows for the Y and Z ranges, the G tile) of TI grid points with
-// 128-byte swizzle, through a TSTG-deep mbarrier ring; each warp releases a
-// stage with one arrive.  Reads undo the swizzle: 16-byte chunk c of row r
-// sits at chunk c ^ (r & 7), which also makes the row-per-lane loads
-// conflict-free.  All waits are bounded by a clock64 budget.
-constexpr int TI = 2, TSTG = 4;
-constexpr long long kTriWait = 4000000000LL;
-
-struct TriTmaSmem {
-    float ey[TSTG][TI][TT * TT];
-    float ez[TSTG][TI][TT * TT];
-    float fy[TSTG][TI][TT * TT];
-    float fz[TSTG][TI][TT * TT];
-    float g[TSTG][TI][TT * TT];
-    unsigned long long full[TSTG];
-    unsigned long long empty[TSTG];
-    int fail;
-};
-
-__device__ __forceinline__ unsigned tri_su32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool tri_wait(unsigned long long* bar, unsigned parity) {
-    const unsigned a = tri_su32(bar);
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.b32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity));
-        if (done) return true;
-        if (clock64() - t0 > kTriWait) return false;
-    }
-}
-
-__device__ __forceinline__ bool tri_test(unsigned long long* bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(tri_su32(bar)), "r"(parity));
-    return done != 0;
-}
-
-__device__ __forceinline__ void tri_tma(void* dst, const CUtensorMap* m, unsigned long long* bar,
-                                        int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(tri_su32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2),
-        "r"(tri_su32(bar))
-        : "memory");
-}
-
-// Same load on a 32-bit shared-memory address (tile base in bytes).
-__device__ __forceinline__ float4 tri_lds4(unsigned tile, int r, int chunk) {
-    float4 v;
-    const unsigned a = tile + (unsigned)(r * TT * 4) + ((unsigned)(chunk ^ (r & 7)) << 4);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(a));
-    return v;
-}
-
-// Packed float pairs for the FP32x2 FMA path (fma.rn.f32x2 issues two
-// float32 FMAs as one instruction; the FMA pipe rate is unchanged, the issue
-// slots are halved).
-__device__ __forceinline__ unsigned long long tri_pack(float lo, float hi) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-
-__device__ __forceinline__ void tri_unpack(unsigned long long v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-
-__device__ __forceinline__ unsigned long long tri_mul2(unsigned long long a, unsigned long long b) {
-    unsigned long long d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-__device__ __forceinline__ unsigned long long tri_fma2(unsigned long long a, unsigned long long b,
-                                                       unsigned long long c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-__global__ void __launch_bounds__(256, 1)
-    k_triangle_f32_tma(float* H, const __grid_constant__ CUtensorMap tmE,
-                       const __grid_constant__ CUtensorMap tmF,
-                       const __grid_constant__ CUtensorMap tmG, int P, int nX, int nI,
-                       int* err) {
-    extern __shared__ __align__(1024) unsigned char tri_raw[];
-    TriTmaSmem& sm = *reinterpret_cast<TriTmaSmem*>(
-        (reinterpret_cast<uintptr_t>(tri_raw) + 1023) & ~uintptr_t(1023));
-    const int Z0 = blockIdx.x * TT, Y0 = blockIdx.y * TT, X0 = blockIdx.z * TT;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // 8 warps = 4 (Y, 8 each) x 2 (Z, 16 each).  Lane = (lx, lz): the thread
-    // owns X = lx + 8j (j < 4), Z = z_base + 4 lz + (0..3), Y = y_base + (0..7).
-    const int y_base = (warp >> 1) * 8, zc = (warp & 1) * 4 + (lane >> 3);
-    const int lx = lane & 7;
-    const int nst = (nI + TI - 1) / TI;
-    const unsigned stage_bytes = 5u * TI * TT * TT * 4u;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < TSTG; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tri_su32(&sm.full[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(tri_su32(&sm.empty[s])));
-        }
-        sm.fail = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
-    __syncthreads();
-    auto issue = [&](int k) {
-        const int s = k % TSTG, I0 = k * TI;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
-                         tri_su32(&sm.full[s])),
-                     "r"(stage_bytes));
-        tri_tma(&sm.ey[s][0][0], &tmE, &sm.full[s], Y0, X0, I0);
-        tri_tma(&sm.ez[s][0][0], &tmE, &sm.full[s], Z0, X0, I0);
-        tri_tma(&sm.fy[s][0][0], &tmF, &sm.full[s], Y0, X0, I0);
-        tri_tma(&sm.fz[s][0][0], &tmF, &sm.full[s], Z0, X0, I0);
-        tri_tma(&sm.g[s][0][0], &tmG, &sm.full[s], Z0, Y0, I0);
-    };
-    int next = 0;   // next step to load (thread 0 only)
-    if (threadIdx.x == 0)
-        for (; next < TSTG - 1 && next < nst; ++next) issue(next);
-
-    // Accumulators as packed float pairs along Z: acc[j][y][zp] holds
-    // (Z, Z + 1) = (z_base + 2 zp, z_base + 2 zp + 1) of row (X_j, Y_y).
-    unsigned long long acc[4][8][2];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int y = 0; y < 8; ++y)
-#pragma unroll
-            for (int zp = 0; zp < 2; ++zp) acc[j][y][zp] = 0ull;
-
-    for (int k = 0; k < nst; ++k) {
-        const int s = k % TSTG;
-        // Refill every stage whose consumers are done, without blocking, up
-        // to TSTG - 1 steps ahead; block (bounded) only if step k itself has
-        // not been issued yet.
-        if (threadIdx.x == 0) {
-            while (next < nst && next <= k + TSTG - 1) {
-                const bool need = next <= k;
-                if (next >= TSTG) {
-                    const unsigned par = ((next / TSTG) - 1) & 1;
-                    if (need) {
-                        if (!tri_wait(&sm.empty[next % TSTG], par)) {
-                            atomicExch(&sm.fail, 1);
-                            break;
-                        }
-                    } else if (!tri_test(&sm.empty[next % TSTG], par)) {
-                        break;
-                    }
-                }
-                issue(next);
-                ++next;
-            }
-        }
-        if (!tri_wait(&sm.full[s], (k / TSTG) & 1)) atomicExch(&sm.fail, 1);
-        if (*(volatile int*)&sm.fail) break;
-#pragma unroll 1
-        for (int ii = 0; ii < TI; ++ii) {
-            if (k * TI + ii >= nI) break;
-            // 32-bit shared addresses of this step's five tiles.
-            const unsigned ey_t = tri_su32(sm.ey[s][ii]), ez_t = tri_su32(sm.ez[s][ii]);
-            const unsigned fy_t = tri_su32(sm.fy[s][ii]), fz_t = tri_su32(sm.fz[s][ii]);
-            const unsigned g_t = tri_su32(sm.g[s][ii]);
-            // G^YZ of the thread's 8 Y x 4 Z, loaded once for its four X rows.
-            unsigned long long g2[8][2];
-#pragma unroll
-            for (int y = 0; y < 8; ++y) {
-                const float4 g4 = tri_lds4(g_t, y_base + y, zc);
-                g2[y][0] = tri_pack(g4.x, g4.y);
-                g2[y][1] = tri_pack(g4.z, g4.w);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int xr = lx + 8 * j;
-                const float4 e0 = tri_lds4(ey_t, xr, (y_base >> 2)), e1 = tri_lds4(ey_t, xr, (y_base >> 2) + 1);
-                const float4 f0 = tri_lds4(fy_t, xr, (y_base >> 2)), f1 = tri_lds4(fy_t, xr, (y_base >> 2) + 1);
-                const float4 ez4 = tri_lds4(ez_t, xr, zc), fz4 = tri_lds4(fz_t, xr, zc);
-                const float ey[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-                const float fy[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-                const unsigned long long ez2[2] = {tri_pack(ez4.x, ez4.y), tri_pack(ez4.z, ez4.w)};
-                const unsigned long long fz2[2] = {tri_pack(fz4.x, fz4.y), tri_pack(fz4.z, fz4.w)};
-#pragma unroll
-                for (int y = 0; y < 8; ++y) {
-                    const unsigned long long eb = tri_pack(ey[y], ey[y]);
-                    const unsigned long long fb = tri_pack(fy[y], fy[y]);
-#pragma unroll
-                    for (int zp = 0; zp < 2; ++zp) {
-                        // t = E^XY F^XZ + E^XZ F^XY, H += t G^YZ  (two Z at once)
-                        unsigned long long t = tri_mul2(eb, fz2[zp]);
-                        t = tri_fma2(ez2[zp], fb, t);
-                        acc[j][y][zp] = tri_fma2(t, g2[y][zp], acc[j][y][zp]);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tri_su32(&sm.empty[s]))
-                         : "memory");
-    }
-    __syncthreads();
-    if (*(volatile int*)&sm.fail) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
-        return;
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int X = X0 + lx + 8 * j;
-        if (X >= nX) continue;
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-            const int Y = Y0 + y_base + y;
-            if (Y >= P) continue;
-            const int Zb = Z0 + zc * 4;
-            float a[4];
-            tri_unpack(acc[j][y][0], a[0], a[1]);
-            tri_unpack(acc[j][y][1], a[2], a[3]);
-            float* h = H + ((long long)X * P + Y) * P + Zb;
-            if (Zb + 3 < P) {
-                float4 v = *reinterpret_cast<float4*>(h);
-                v.x += a[0]; v.y += a[1]; v.z += a[2]; v.w += a[3];
-                *reinterpret_cast<float4*>(h) = v;
-            } else {
-#pragma unroll
-                for (int z = 0; z < 4; ++z)
-                    if (Zb + z < P) h[z] += a[z];
-            }
-        }
-    }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 g_tri_encode = nullptr;
-std::once_flag g_tri_once;
-
-// Map of nI matrices of rows x P floats (rows are P-float lines).
-cudaError_t tri_map(CUtensorMap* m, const float* base, int rows, int P, int nI) {
-    std::call_once(g_tri_once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            g_tri_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    if (!g_tri_encode) return cudaErrorNotSupported;
-    cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)rows, (cuuint64_t)nI};
-    cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)rows * P * 4};
-    cuuint32_t box[3] = {(cuuint32_t)TT, (cuuint32_t)TT, (cuuint32_t)TI};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_tri_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box,
-                              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
 
 __device__ double block_sum(double v) {
     __shared__ double red[32];
@@ -934,24 +663,9 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx, T* 
 
 template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, int nI,
-                     cudaStream_t s, int* tri_err) {
+                     cudaStream_t s) {
     if (nX <= 0 || nI <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
-        if (P % 4 == 0 && ((uintptr_t)E % 16 == 0) && ((uintptr_t)F % 16 == 0) &&
-            ((uintptr_t)G % 16 == 0) && tri_err) {
-            CUtensorMap mE, mF, mG;
-            cudaError_t e = tri_map(&mE, E, nX, P, nI);
-            if (e == cudaSuccess) e = tri_map(&mF, F, nX, P, nI);
-            if (e == cudaSuccess) e = tri_map(&mG, G, P, P, nI);
-            if (e != cudaSuccess) return e;
-            const int smem = (int)sizeof(TriTmaSmem) + 1024;
-            e = smem_optin((const void*)k_triangle_f32_tma, smem);
-            if (e != cudaSuccess) return e;
-            dim3 grid(cdiv(P, TT), cdiv(P, TT), cdiv(nX, TT));
-            k_triangle_f32_tma<<<grid, 256, smem, s>>>(H, mE, mF, mG, P, nX, nI, tri_err);
-            count_launches(1);
-            return cudaGetLastError();
-        }
         const int smem = (int)(TSTAGES * sizeof(TriStage));
         cudaError_t e = smem_optin((const void*)k_triangle_f32, smem);
         if (e != cudaSuccess) return e;
@@ -1027,7 +741,7 @@ cudaError_t accumulate(double* acc, const T* part, long long n, double scale,
     template cudaError_t scale_rows<T>(const T*, int, int, const T*, int, int, T*,     \
                                        cudaStream_t);                                   \
     template cudaError_t triangle<T>(T*, const T*, const T*, const T*, int, int, int,  \
-                                     cudaStream_t, int*);                               \
+                                     cudaStream_t);                                     \
     template cudaError_t dot<T>(const T*, const T*, long long, double*, double*,       \
                                 cudaStream_t);                                          \
     template cudaError_t singles_energy<T>(const T*, const T*, const T*, int, int, int, \

@@ -78,11 +78,12 @@ cudaError_t scale_rows(const T* y, int R, int P, const T* w, int x0, int nx,
 
 // Alg. 6 line 11: H[X][Y][Z] += sum_I (E_I^XY F_I^XZ + E_I^XZ F_I^XY) G_I^YZ
 // for a block of nX rows X (X < nX <= P, Y, Z < P): H is nX x P x P, E and F
-// are nI x nX x P, G is nI x P x P.
-// tri_err (device int, may be null) receives 1 if a bounded wait expired.
+// are nI x nX x P, G is nI x P x P.  Float64: mirror (Y, Z) tiles on the
+// FP64 pipe; float32: 32^3 tiles through cp.async (the mixed path takes
+// triangle_pair when P is a multiple of 4).
 template <typename T>
 cudaError_t triangle(T* H, const T* E, const T* F, const T* G, int P, int nX, int nI,
-                     cudaStream_t s, int* tri_err = nullptr);
+                     cudaStream_t s);
 
 // Float64-accurate triangle on the FP32 pipe (float pairs, error-free
 // transformations; triangle_df.cu).  E4, F4: nI x ceil(nX/2) x P float4
@@ -100,7 +101,7 @@ cudaError_t triangle_df(double* H, const float4* E4, const float4* F4, const flo
 // multiple of 4 and at most kPairMaxP.  E2, F2: nI x ceil(nX/2) x P float2
 // {E^{2q,Y}, E^{2q+1,Y}} (16-byte aligned); G: nI x P x P; H: nX x P x P,
 // accumulated into.  err (device int) receives 1 if a bounded wait expired.
-constexpr int kPairMaxP = 6144;
+constexpr int kPairMaxP = 28000;
 bool triangle_pair_ok(int P);
 cudaError_t triangle_pair(float* H, const float2* E2, const float2* F2, const float* G, int P,
                           int nX, int nI, cudaStream_t s, int* err);

@@ -387,7 +387,12 @@ cudaError_t pair_rows(float* A, long long nslab, long long stride, int nX, int P
         return cudaErrorInvalidValue;
     const long long work = nslab * ((nX + 1) / 2);
     const unsigned grid = (unsigned)std::min<long long>(work, 152LL * 8);
-    k_pair_rows<<<grid, 256, 2 * P * sizeof(float), s>>>(A, nslab, stride, nX, P);
+    const int smem = 2 * P * (int)sizeof(float);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = smem_optin((const void*)k_pair_rows, smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_pair_rows<<<grid, 256, smem, s>>>(A, nslab, stride, nX, P);
     count_launches(1);
     return cudaGetLastError();
 }
