@@ -958,7 +958,10 @@ void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slic
 namespace {
 
 constexpr int FN = 64;                    // tile columns (B rows)
-constexpr int FA = 4;                     // A-slice ring depth
+#ifndef THC_F64_FA
+#define THC_F64_FA 4
+#endif
+constexpr int FA = THC_F64_FA;            // A-slice ring depth
 constexpr int kF64EpiWarps = 8;
 constexpr int kF64Threads = 64 + 32 * kF64EpiWarps;
 

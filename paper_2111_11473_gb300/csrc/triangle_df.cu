@@ -57,6 +57,17 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+// -a in both lanes: a sign-bit flip on the integer pipe (the FMA pipe is the
+// busy one here; -0 for a zero lane, which no later sum can tell from +0).
+__device__ __forceinline__ f2 neg2(f2 a) {
+#ifdef THC_DF_SUBNEG
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(0ull), "l"(a));
+    return d;
+#else
+    return a ^ 0x8000000080000000ull;
+#endif
+}
 // The rounded product fl(a b), written as fma(a, b, +0).  ptxas contracts a
 // packed mul.rn.f32x2 whose result feeds an add.rn.f32x2 into one fused
 // operation, which would round a b + c once where TwoSum needs fl(a b)
@@ -68,11 +79,10 @@ __device__ __forceinline__ f2 prod2(f2 a, f2 b) { return fma2(a, b, 0ull); }
 // up to the dropped low*low products and the roundings of the cross terms.
 __device__ __forceinline__ void df_dot2(f2 aH, f2 aL, f2 bH, f2 bL, f2 cH, f2 cL, f2 dH,
                                         f2 dL, f2& th, f2& tl) {
-    const f2 zero = 0ull;
     const f2 p1 = prod2(aH, bH);
-    const f2 e1 = fma2(aH, bH, sub2(zero, p1));   // aH bH - p1, exact
+    const f2 e1 = fma2(aH, bH, neg2(p1));   // aH bH - p1, exact
     const f2 p2 = prod2(cH, dH);
-    const f2 e2 = fma2(cH, dH, sub2(zero, p2));
+    const f2 e2 = fma2(cH, dH, neg2(p2));
     const f2 s = add2(p1, p2);                     // TwoSum(p1, p2)
     const f2 z = sub2(s, p1);
     const f2 es = add2(sub2(p1, sub2(s, z)), sub2(p2, z));
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(DTH, 1)
                         f2 th, tl;
                         df_dot2(ey[i].x, ey[i].y, fz[j].x, fz[j].y, ez[j].x, ez[j].y, fy[i].x,
                                 fy[i].y, th, tl);
-                        const f2 thn = sub2(0ull, th);
+                        const f2 thn = neg2(th);
                         df_acc(h1[xp][i][j], l1[xp][i][j], th, tl, thn, g1h[i][j], g1l[i][j]);
                         df_acc(h2[xp][i][j], l2[xp][i][j], th, tl, thn, g2h[i][j], g2l[i][j]);
                     }
