@@ -88,7 +88,8 @@ def _mixed_triangle_unpaired():
 # DRAM bytes (read + write) of one triangle launch at o=40, v=200, P=400,
 # G=1200, from one ncu capture of the kernel that runs at that precision
 # (None: not captured since the kernel last changed).
-TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": None, "mixed": None}
+TRIANGLE_TRAFFIC_BYTES = {"fp64": 97.58e9 + 0.52e9, "fp64tc": 36.653e9 + 0.517e9,
+                          "mixed": 12.702e9 + 0.249e9}
 
 
 def triangle_roofline(precision, flops, ms, launches, share):

@@ -285,16 +285,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t ah = smem_u32(sm.a_hi[s]), bh = smem_u32(sm.b_hi[s]);
-                    const uint32_t al = smem_u32(sm.a_lo[s]), bl = smem_u32(sm.b_lo[s]);
+                    // descriptors of the stage's tiles; a K sub-step of UK bf16
+                    // adds UK * 2 bytes (in 16-byte units) to the address field
+                    const uint64_t dah = smem_desc(smem_u32(sm.a_hi[s]));
+                    const uint64_t dbh = smem_desc(smem_u32(sm.b_hi[s]));
+                    const uint64_t dal = smem_desc(smem_u32(sm.a_lo[s]));
+                    const uint64_t dbl = smem_desc(smem_u32(sm.b_lo[s]));
+                    constexpr uint64_t kKStep = (uint64_t)(UK * 2) >> 4;
 #pragma unroll
                     for (int kk = 0; kk < BK / UK; ++kk) {
-                        const uint32_t off = kk * UK * 2;   // bytes along K inside the swizzle atom
                         const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(dst, smem_desc(ah + off), smem_desc(bh + off), idesc, acc0);
+                        const uint64_t o = kk * kKStep;
+                        mma_bf16(dst, dah + o, dbh + o, idesc, acc0);
                         if (args.nprod == 3) {
-                            mma_bf16(dst, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
-                            mma_bf16(dst, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+                            mma_bf16(dst, dah + o, dbl + o, idesc, 1u);
+                            mma_bf16(dst, dal + o, dbh + o, idesc, 1u);
                         }
                     }
                     mma_commit(&sm.empty[s]);
@@ -1093,12 +1098,23 @@ __global__ void __launch_bounds__(kF64Threads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer
+            // MMA issuer.  The loops over the 36 digit pairs are unrolled and
+            // the shared-memory descriptors are stepped by constants: the
+            // start-address field counts 16-byte units, A ring slots are
+            // BM * BK * 2 bytes apart, B slices FN * BK * 2, B buffers 8 B
+            // slices, and a K sub-step of UK bf16 moves UK * 2 bytes.  (The
+            // issuing thread was the limit with the descriptors rebuilt for
+            // every MMA: 128 x 64 x 16 MMAs leave it about 40 cycles each.)
             const uint32_t idesc = instr_desc(BM, FN);
+            const uint64_t a0 = smem_desc(smem_u32(sm.a[0]));
+            const uint64_t b0 = smem_desc(smem_u32(sm.b[0][0]));
+            constexpr uint64_t kAStep = (uint64_t)(BM * BK * 2) >> 4;
+            constexpr uint64_t kBSlice = (uint64_t)(FN * BK * 2) >> 4;
+            constexpr uint64_t kKStep = (uint64_t)(UK * 2) >> 4;
             long long bit = 0, ait = 0;
             // Per level q (bit q): usedm = a chunk has been started before
             // (its successor waits for the drain), parm = parity of the next
-            // lempty wait, inchunk = the current chunk has K steps already.
+            // lempty wait.
             unsigned usedm = 0, parm = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < args.ntiles && ok && !*fail; t += gridDim.x) {
@@ -1117,39 +1133,42 @@ __global__ void __launch_bounds__(kF64Threads, 1)
 #pragma unroll
                     for (int q = 0; q < kLevels; ++q)
                         if (cnt[q] > 0) startedm |= 1u << q;
-                    for (int ts = 1; ts <= kSlices && ok; ++ts) {
+                    const uint64_t bbase = b0 + (uint64_t)bs * (kSlices * kBSlice);
+#pragma unroll
+                    for (int ts = 1; ts <= kSlices; ++ts) {
                         const int as = (int)(ait % FA);
                         if (!mbar_wait_or_fail(&sm.afull[as], (uint32_t)((ait / FA) & 1), fail)) {
                             ok = false;
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                        const uint32_t aa = smem_u32(sm.a[as]);
+                        const uint64_t ad = a0 + (uint64_t)as * kAStep;
+#pragma unroll
                         for (int u = 1; u <= kSlices + 1 - ts; ++u) {
                             const int q = ts + u - 2;
                             const unsigned qb = 1u << q;
-                            const bool started = (startedm & qb) != 0;
-                            if (!started) {
+                            const uint32_t acc0 = (startedm >> q) & 1u;
+                            if (!acc0) {
                                 // a new chunk: the previous one has been drained
-                                if ((usedm & qb) &&
-                                    !mbar_wait_or_fail(&sm.lempty[q], (parm >> q) & 1u, fail)) {
-                                    ok = false;
-                                    break;
+                                if (usedm & qb) {
+                                    if (!mbar_wait_or_fail(&sm.lempty[q], (parm >> q) & 1u, fail)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    parm ^= qb;
                                 }
-                                if (usedm & qb) parm ^= qb;
                                 usedm |= qb;
                                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                             }
-                            const uint32_t bb = smem_u32(sm.b[bs][u - 1]);
+                            const uint64_t bd = bbase + (uint64_t)(u - 1) * kBSlice;
                             const uint32_t dst = tmem + (uint32_t)(q * FN);
 #pragma unroll
-                            for (int kk = 0; kk < BK / UK; ++kk) {
-                                const uint32_t off = kk * UK * 2;
-                                mma_bf16(dst, smem_desc(aa + off), smem_desc(bb + off), idesc,
-                                         (started || kk > 0) ? 1u : 0u);
-                            }
+                            for (int kk = 0; kk < BK / UK; ++kk)
+                                mma_bf16(dst, ad + kk * kKStep, bd + kk * kKStep, idesc,
+                                         kk > 0 ? 1u : acc0);
                             startedm |= qb;
                         }
+                        if (!ok) break;
                         mma_commit(&sm.aempty[as]);
                         ++ait;
                     }
