@@ -186,11 +186,13 @@ Err Engine<T>::mm(int M, int N, int Kd, View<T> A, View<T> B, T* C, long long ld
     } else {
         // float64 products by exact integer slices on the tensor cores, when
         // the estimated time beats the CUDA cores (1 TFLOP/s): 36 slice-pair
-        // products at about 1.2 PFLOP/s, 8 level outputs written and read
-        // back in float32, one float64 pass over C and about 14 launches.
+        // products at the 0.85 PFLOP/s of bf16 products the fused kernel
+        // reaches on large shapes, slicing (8 + 8 bytes read, 16 written per
+        // operand element), the float64 tile written once, 5 launches.
         const double out = (double)M * N * (reduce ? 1 : batch);
-        const double t_tc = 36.0 * fl / 1.2e15 + 8.0 * out * 8.0 / 5e12 + out * 16.0 / 5e12 +
-                            14.0 * 5e-6;
+        const double opnd = ((double)M + N) * Kd * batch;
+        const double t_tc = 36.0 * fl / 0.85e15 + opnd * 32.0 / 5e12 + out * 8.0 / 5e12 +
+                            5.0 * 5e-6;
         const bool use_tc = step_f64tc();
         if (use_tc && fl >= 3.0e7 && Kd >= 16 && t_tc < fl / 1.0e12) {
             cudaError_t e = gemm_f64_tc(g, f64ws, st);

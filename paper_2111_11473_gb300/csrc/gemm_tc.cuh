@@ -80,19 +80,21 @@ cudaError_t gemm_tc(const Gemm<float>& g, const TcWorkspace& ws, int nprod, cuda
 // Float64 products on the tensor cores: each operand row is cut into 8
 // slices of 7-bit integers below a per-row power of two, the 36 slice pairs
 // that matter are multiplied exactly (bf16 integer products, float32 sums of
-// at most 1024 terms) and combined in float64.  Returns
-// cudaErrorMemoryAllocation (without launching) if the workspace is too small.
+// at most 1024 terms) and combined in float64, all in one fused kernel per
+// product.  A product whose slices do not fit the workspace is cut into
+// pieces that do; cudaErrorMemoryAllocation (without launching) only if a
+// single 128 x 128 piece does not fit.
 struct F64TcWorkspace {
     __nv_bfloat16* slices = nullptr;   // operand slices
     size_t slice_elems = 0;
-    float* part = nullptr;             // float32 slice-pair products (exact integers)
+    float* part = nullptr;             // float64 split-K partials (counted in floats)
     size_t part_elems = 0;
     int* expo = nullptr;               // per-row binary exponents
     size_t expo_elems = 0;
     int* err = nullptr;                // bounded-wait expiry flag
 };
-// Workspace needed by one product (part: the float32 outputs of its 8
-// slice levels, combined in one float64 pass).
+// Workspace one product takes in one piece (part: room for its largest
+// split-K count).
 void gemm_f64_tc_sizes(int M, int N, int K, int batch, bool reduce, size_t* slice_elems,
                        size_t* part_elems, size_t* expo_elems);
 cudaError_t gemm_f64_tc(const Gemm<double>& g, const F64TcWorkspace& ws, cudaStream_t s);
