@@ -66,7 +66,8 @@ typedef enum {
  * with split (hi/lo) bf16 products and float32 accumulation, float32
  * CUDA-core triangle kernel; the sigma accumulation, energy, least squares
  * and DIIS stay float64.  FP64_TC: float64 storage and arithmetic as FP64,
- * but every product of at least 3e7 flops runs on the tensor cores as exact
+ * but the products of at least 3e7 flops (those a cost model of the two
+ * paths does not keep on the CUDA cores) run on the tensor cores as exact
  * integer products of 8 slices of 7 bits per operand row (scaled by a power
  * of two per row), combined in float64: each product term is within about
  * 1.2e-16 of its row and column scale, float64 rounding level; the triangle
