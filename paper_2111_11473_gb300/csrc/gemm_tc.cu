@@ -834,14 +834,12 @@ __global__ void __launch_bounds__(256) k_row_exp(const double* src, long long rs
     }
 }
 
-// bf16 bits of a small integer (|a| <= 127), exact.
-__device__ __forceinline__ unsigned short small_int_bf16(int a) {
-    const unsigned sign = a < 0 ? 0x8000u : 0u;
-    const unsigned m = (unsigned)(a < 0 ? -a : a);
-    if (m == 0) return (unsigned short)sign;
-    const int p = 31 - __clz(m);                       // leading bit, 0 .. 6
-    const unsigned frac = (m << (7 - p)) & 0x7fu;      // 7 bits after it
-    return (unsigned short)(sign | ((unsigned)(p + 127) << 7) | frac);
+// bf16 bits of the digit d (0 <= d <= 127) with sign bit sgn (0 or 0x8000;
+// +0 for d = 0): 2^23 + d is exact in float32, the subtraction leaves d, and
+// a float32 of at most 8 significant bits is its bf16 in the upper 16 bits.
+__device__ __forceinline__ unsigned short digit_bf16(unsigned d, unsigned sgn) {
+    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return (unsigned short)((__float_as_uint(f) >> 16) | (d ? sgn : 0u));
 }
 
 // Slices of one operand: row (bo, r) holds kSlices segments of Ktot
@@ -849,7 +847,9 @@ __device__ __forceinline__ unsigned short small_int_bf16(int a) {
 // the packed K-major layout of k_pack (zero in the padding).  x = m 2^E with
 // the 53-bit significand m; |x| 2^(56 - e) = m 2^(E - e + 56) truncated to an
 // integer V < 2^56 gives the slices as its 7-bit digits.
-__global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs, long long ks,
+// Five blocks of 256 threads per SM (at its natural 78 registers three fit,
+// and on GB300 that measured no faster).
+__global__ void __launch_bounds__(256, 5) k_slice64(const double* src, long long rs, long long ks,
                                                  long long bs, int R, int Kd, int nb, int Rp,
                                                  int Kp, int reduce, int reverse, const int* expo,
                                                  __nv_bfloat16* out) {
@@ -883,12 +883,15 @@ __global__ void __launch_bounds__(256) k_slice64(const double* src, long long rs
                     if (sh >= 0) V = mant << sh;          // sh <= 3: V < 2^56
                     else if (sh > -64) V = mant >> (-sh);
                 }
-                const bool neg = (bits >> 63) != 0;
+                const unsigned sgn = (bits >> 63) ? 0x8000u : 0u;
+                // digits 0-3 in the high 28 bits of V, 4-7 in the low 28
+                const unsigned vh = (unsigned)(V >> 28), vl = (unsigned)V & 0xfffffffu;
 #pragma unroll
                 for (int q = 0; q < kSlices; ++q) {
                     const int slice = reverse ? kSlices - 1 - q : q;      // 0-based digit
-                    const int dig = (int)((V >> (7 * (kSlices - 1 - slice))) & 0x7f);
-                    v[q].h[j] = small_int_bf16(neg ? -dig : dig);
+                    const unsigned dig =
+                        slice < 4 ? (vh >> (7 * (3 - slice))) & 0x7fu : (vl >> (7 * (7 - slice))) & 0x7fu;
+                    v[q].h[j] = digit_bf16(dig, sgn);
                 }
             }
             const long long row = ((long long)bo * Rp + r) * kSlices;
