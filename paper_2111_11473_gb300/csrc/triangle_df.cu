@@ -321,27 +321,66 @@ __global__ void __launch_bounds__(DTH, 1)
             }
 }
 
-__device__ __forceinline__ void split1(double d, float& h, float& l) {
+// {h, l} = {fl32(d), fl32(d - fl32(d))}.  The float64 form takes four
+// float64-pipe operations (1/64 of the float32 rate on GB300: it kept the
+// split kernels' float64 pipe 88 % busy), so for 2^-60 <= |d| < 2^60 the
+// split is done on the IEEE-754 fields with integer operations: h rounds the
+// 53-bit significand to 24 bits (nearest, ties to even); the signed
+// remainder, below 2^29 units of 2^(e - 1075), is rounded to float32 and
+// given its exponent.  Bit-identical to the float64 form (checked on the host
+// over 2e7 values, ties and carries included).  Other values (zero among
+// them) take the float64 form out of line, so that the common path carries
+// no predicated float64 operations.
+__device__ __noinline__ void split1_f64(double d, float& h, float& l) {
     h = __double2float_rn(d);
     l = __double2float_rn(d - (double)h);   // d - h is exact in float64
 }
 
+__device__ __forceinline__ bool split1_int(double d, float& h, float& l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 60 || e >= 1023 + 60) return false;
+    const unsigned long long m = (b & 0xfffffffffffffULL) | (1ULL << 52);
+    unsigned long long q = m >> 29;
+    const unsigned long long rem = m & ((1ULL << 29) - 1);
+    if (rem > (1ULL << 28) || (rem == (1ULL << 28) && (q & 1ULL))) ++q;
+    const long long rs = (long long)m - (long long)(q << 29);   // |rs| <= 2^28
+    int eh = e;
+    if (q >> 24) {
+        q >>= 1;
+        ++eh;
+    }
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    h = __uint_as_float(sgn | ((unsigned)(eh - 1023 + 127) << 23) | (unsigned)(q & 0x7fffffULL));
+    unsigned lb = __float_as_uint(__int2float_rn((int)rs));
+    if (rs != 0) lb += (unsigned)(e - 1075) << 23;
+    l = rs != 0 ? __uint_as_float(lb ^ sgn) : 0.f;
+    return true;
+}
+
+__device__ __forceinline__ void split1(double d, float& h, float& l) {
+    if (!split1_int(d, h, l)) split1_f64(d, h, l);
+}
+
+// One block per output row (I, q) at a time, threads along the P columns
+// (no 64-bit division per element).
 __global__ void k_split_pairs(const double* E, int nI, int nX, int P, float4* out) {
     const int nXp = (nX + 1) / 2;
-    const long long total = (long long)nI * nXp * P;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % P);
-        const long long r = idx / P;
-        const int q = (int)(r % nXp);
-        const long long I = r / nXp;
-        const int x = 2 * q;
-        const double d0 = E[(I * nX + x) * P + c];
-        const double d1 = x + 1 < nX ? E[(I * nX + x + 1) * P + c] : 0.0;
-        float h0, l0, h1, l1;
-        split1(d0, h0, l0);
-        split1(d1, h1, l1);
-        out[idx] = make_float4(h0, h1, l0, l1);
+    const long long rows = (long long)nI * nXp;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long long I = row / nXp;
+        const int x = 2 * (int)(row - I * nXp);
+        const double* e0 = E + (I * nX + x) * P;
+        float4* o = out + row * P;
+        const bool two = x + 1 < nX;
+        for (int c = threadIdx.x; c < P; c += blockDim.x) {
+            const double d0 = e0[c];
+            const double d1 = two ? e0[P + c] : 0.0;
+            float h0, l0, h1, l1;
+            split1(d0, h0, l0);
+            split1(d1, h1, l1);
+            o[c] = make_float4(h0, h1, l0, l1);
+        }
     }
 }
 
@@ -366,7 +405,9 @@ cudaError_t split_df_pairs(const double* E, int nI, int nX, int P, float4* out,
                            cudaStream_t s) {
     const long long n = (long long)nI * ((nX + 1) / 2) * P;
     if (n <= 0) return cudaSuccess;
-    k_split_pairs<<<grid_for(n), 256, 0, s>>>(E, nI, nX, P, out);
+    const long long rows = (long long)nI * ((nX + 1) / 2);
+    k_split_pairs<<<(unsigned)std::min<long long>(rows, 152LL * 16), 128, 0, s>>>(E, nI, nX, P,
+                                                                               out);
     count_launches(1);
     return cudaGetLastError();
 }
